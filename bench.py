@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 D-iteration.
+
+One step = one DI-SOP solve (Section 2.3) of X = P.X + B to ||F||_1 <= 1e-8 on the resident
+10M-node / ~141M-link synthetic web graph (FP32 fluid, FP64 history and residual, exact FP64
+refinement), B = (1-d)/N, d = 0.85. The metric is GTEPS = pushed links / solve time (the graph
+build is timed apart, like the paper's "Init"). Inputs (CSR ~1.8 GB) are larger than L2 and L2 is
+flushed between steps anyway.
+
+Extra legs in the same JSON line: time-to-residual of DI-SOP, DI-CYC and power iteration at
+d = 0.85 and DI-SOP at d = 0.95; graph build time; the roofline of the push kernel; the oracle
+timed on the host cores (`cpu_baseline`).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU: the solve does not shard here, so N ranks run N independent replicas ("weak"
+scaling); value = pushed links of all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "web_n10m"
+D = 0.85
+TOL = 1e-8
+L2_FLUSH_BYTES = 512 << 20
+MAX_SWEEPS = 20000
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--no-legs", action="store_true", help="skip the extra legs (DI-CYC, PI, d=0.95)")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return p.parse_args()
+
+
+def world():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle legs (the only place bench.py runs oracle/)
+# ------------------------------------------------------------------------------------------
+def oracle_sample(n, src, dst, d, max_cycles):
+    """The oracle's sequential DI-SOP on the same graph, bounded to `max_cycles` cycles from
+    F = B. Returns (pushed links, seconds, cycles)."""
+    import oracle
+    og = oracle.build(n, src, dst)
+    B = oracle.uniform_B(n, d)
+    t = time.perf_counter()
+    _, _, info, _ = oracle.di(og, B, d, TOL, oracle.SOP, max_cycles=max_cycles)
+    sec = time.perf_counter() - t
+    return info["pushed_edges"], sec, info["cycles"], og
+
+
+def run_reference(args):
+    rank, local_rank, ws = world()
+    if ws > 1 and rank != 0:
+        return
+    import workloads
+    cfg = workloads.WORKLOADS[WORKLOAD]
+    n, src, dst = workloads.generate(cfg["spec"])
+    import oracle
+    og = oracle.build(n, src, dst)
+    B = oracle.uniform_B(n, D)
+    # each step: one DI-SOP cycle of the oracle from F = B (a bounded sample of the solve)
+    times, pushed = [], []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        _, _, info, _ = oracle.di(og, B, D, TOL, oracle.SOP, max_cycles=1)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            times.append(dt)
+            pushed.append(info["pushed_edges"])
+    total = sum(times)
+    value = sum(pushed) / total / 1e9
+    line = {
+        "impl": "reference", "metric": "GTEPS (DI-SOP, N=10M, tol 1e-8)", "value": value, "unit": "GTEPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: N={n}, L={og.L}, d={D}", "step": "one oracle DI-SOP cycle from F=B"},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": "one sequential DI-SOP cycle per step on the full 10M-node graph"},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_1204_6255_gb300 as di
+    import workloads
+
+    rank, local_rank, ws = world()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    di.build()
+    di.load()
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    cfg = workloads.WORKLOADS[WORKLOAD]
+    n, src, dst = workloads.generate(cfg["spec"])
+
+    # graph build from a device edge list (the paper's "Init", timed apart)
+    src_d = torch.from_numpy(src).to(dev)
+    dst_d = torch.from_numpy(dst).to(dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g = di.di_graph_create(n, src_d, dst_d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    del src_d, dst_d
+    st = g.stats
+
+    B = torch.full((n,), (1.0 - D) / n, dtype=torch.float64, device=dev)
+    X = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(Bx=B, Xx=X, d=D, schedule=di.DI_SOP, **kw):
+        return di.di_solve_ex(g, Bx, d, TOL, schedule=schedule, fluid=di.DI_FLUID_F32, max_sweeps=MAX_SWEEPS,
+                              X_out=Xx, **kw)[1]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    sampler = ClockSampler(vis.split(",")[local_rank] if vis else local_rank)
+    sampler.start()
+    step_ms, infos = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)                      # evict the previous step's lines from L2
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        info = step()
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        infos.append(info)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+
+    total_ms = sum(step_ms)
+    pushed = sum(i["pushed_edges"] for i in infos)
+    launches = sum(i["kernel_launches"] for i in infos)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        p = torch.tensor([float(pushed), float(launches)], dtype=torch.float64, device=dev)
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+        total_ms, pushed, launches = float(t.item()), float(p[0].item()), int(p[1].item())
+    value = pushed / (total_ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers: B from pinned host memory, X back
+    Bh = torch.full((n,), (1.0 - D) / n, dtype=torch.float64).pin_memory()
+    Xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_ms, e2e_pushed = [], 0
+    for _ in range(max(1, min(args.steps, 5))):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        info = di.di_solve_ex(g, Bh, D, TOL, schedule=di.DI_SOP, fluid=di.DI_FLUID_F32, max_sweeps=MAX_SWEEPS,
+                              X_out=Xh)[1]
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+        e2e_pushed += info["pushed_edges"]
+    e2e_value = e2e_pushed / (sum(e2e_ms) * 1e-3) / 1e9 * ws
+
+    # per-kernel timing: one solve with CUDA events around every kernel launch
+    prof = step(profile=1)
+    push_ms = prof["push_ms"] / max(prof["push_launches"], 1)
+    push_bytes = (12.0 * prof["pushed_edges"] + 24.0 * prof["frontier_entries"]) / max(prof["push_launches"], 1)
+    peak, peak_kind = peaks()
+    achieved = push_bytes / (push_ms * 1e-3) / 1e9
+    kernel_total = prof["select_ms"] + prof["push_ms"] + prof["reduce_ms"] + prof["refine_ms"]
+
+    legs = {}
+    if not args.no_legs:
+        for name, kw in (("di_cyc", dict(schedule=di.DI_CYC)), ("di_sop_d095", dict(d=0.95, Bx=torch.full(
+                (n,), (1.0 - 0.95) / n, dtype=torch.float64, device=dev)))):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            inf = step(**kw)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            legs[name] = {"ms_to_residual": ms, "GTEPS": inf["pushed_edges"] / (ms * 1e-3) / 1e9,
+                          "sweeps": inf["sweeps"], "pushed_per_L": inf["pushed_edges"] / st["L"],
+                          "residual_l1": inf["residual_l1"]}
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, pinf = di.di_power_iter(g, B, D, TOL, max_iters=MAX_SWEEPS, X_out=X)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        legs["pi"] = {"ms_to_residual": ms, "GTEPS": pinf["pushed_edges"] / (ms * 1e-3) / 1e9,
+                      "iterations": pinf["sweeps"], "residual_l1": pinf["residual_l1"]}
+    legs["di_sop"] = {"ms_to_residual": statistics.median(step_ms), "sweeps": infos[-1]["sweeps"],
+                      "pushed_per_L": infos[-1]["pushed_edges"] / st["L"], "refine_rounds": infos[-1]["refine_rounds"],
+                      "residual_l1": infos[-1]["residual_l1"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cyc = 6
+        cp, csec, ccyc, _ = oracle_sample(n, src, dst, D, cyc)
+        cpu = {"value": cp / csec / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"first {ccyc} sequential DI-SOP cycles of the oracle on the same 10M-node graph "
+                         f"({cp} pushed links in {csec:.1f} s; oracle build excluded)"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": "GTEPS (DI-SOP, N=10M, tol 1e-8)",
+        "value": value,
+        "unit": "GTEPS",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: N={n}, L={st['L']}, d={D}, tol={TOL}, B=(1-d)/N",
+                   "fluid": "f32", "history": "f64", "residual": "f64 exact (refined)",
+                   "parallelism": f"replicas x{ws}", "l2": "flushed between steps (512 MB write)",
+                   "graph_build_ms": build_ms},
+        "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+                "ms_per_step": statistics.mean(e2e_ms)},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_push<float>", "peak_kind": peak_kind,
+                     "bytes_per_launch": push_bytes, "ms_per_launch": push_ms,
+                     "kernel_share": prof["push_ms"] / kernel_total if kernel_total else None},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "legs": legs,
+        "graph": {k: st[k] for k in ("n_nodes", "L", "D", "E", "O", "max_in", "max_out", "e_levels")},
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

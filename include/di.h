@@ -1,0 +1,193 @@
+/*
+ * di.h — C ABI of the GB300 (sm_103a) D-iteration library.
+ *
+ * The library solves X = P.X + B (paper: "Revisiting the D-iteration method: runtime
+ * comparison", Section 1) for a directed graph given as an edge list. P has d / out_j at (i, j)
+ * for every distinct link j -> i (Section 2.4: column j of P holds the out-links of j, row i
+ * the in-links of i); a dangling column (out_j = 0) is zero. B >= 0. With B = (1-d)/N this is
+ * the unnormalised PageRank equation; with B = (1-d)/|S| on a seed set S it is personalised
+ * PageRank.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers: every array argument may be host memory (pageable or pinned) or device memory
+ *     of the graph's GPU; the library asks the CUDA runtime which one it is. The caller owns
+ *     every array it passes and keeps it alive for the duration of the call.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     All device work of a call is ordered on that stream. Every call returns only after its
+ *     results are written (it synchronises the stream before returning).
+ *   - Errors: every call returns a di_status; DI_OK is 0. On error, di_last_error() returns a
+ *     human-readable message for the calling thread. No call aborts the process.
+ *   - Threads: calls on different graphs may run concurrently. Calls that use the same graph's
+ *     solve workspace (di_solve*, di_power_iter, di_solve_batch, di_ppr_batch) are serialised
+ *     by the graph; a call that finds the workspace busy returns DI_ERR_BUSY.
+ */
+#ifndef DI_GB300_H
+#define DI_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct di_graph di_graph;
+
+typedef enum {
+    DI_OK = 0,
+    DI_ERR_INVALID_ARG = 1,      /* bad size, d outside [0,1), tol <= 0, B < 0 or not finite */
+    DI_ERR_OUT_OF_RANGE_ID = 2,  /* an edge id outside [0, n_nodes) */
+    DI_ERR_OOM = 3,              /* device or host allocation failed */
+    DI_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+    DI_ERR_NOT_CONVERGED = 5,    /* the sweep cap was reached; outputs hold the current state */
+    DI_ERR_BUSY = 6,             /* the graph's workspace is in use by another thread */
+    DI_ERR_TIMEOUT = 7           /* a bounded wait ran out */
+} di_status;
+
+/* Node selection rule of a sweep (Section 2.3). */
+typedef enum {
+    DI_CYC = 0,   /* visit every node with F_i != 0 */
+    DI_SOP = 1    /* visit node i when |F_i| > (r / L) * out_i, r = ||F||_1 at the sweep start */
+} di_schedule;
+
+/* Storage of the fluid F. H, the residual and r are FP64 in both. */
+typedef enum {
+    DI_FLUID_F32 = 0,
+    DI_FLUID_F64 = 1
+} di_fluid;
+
+/* Graph statistics (Section 2.4 notation). */
+typedef struct {
+    int64_t n_nodes;
+    int64_t L;          /* distinct links, self-loops included */
+    int64_t D;          /* dangling nodes (out-degree 0) */
+    int64_t E;          /* recursively zero-in-degree nodes */
+    int64_t O;          /* loop nodes (p_ii != 0) */
+    int32_t max_in;
+    int32_t max_out;
+    int32_t e_levels;   /* 1 + largest peeling level in E (0 when E is empty) */
+    int32_t reserved;
+} di_graph_stats;
+
+/* Options of di_solve_ex / di_solve_batch / di_ppr_batch. Zero-initialise, then set fields;
+ * a zero field means "default". */
+typedef struct {
+    int32_t schedule;    /* di_schedule; default DI_CYC (0) */
+    int32_t fluid;       /* di_fluid; default DI_FLUID_F32 (0) */
+    int32_t max_sweeps;  /* cap on sweeps; <= 0: 100000; clamped to 1000000 */
+    int32_t refine;      /* 0: default (on for F32, off for F64); 1: on; -1: off. Refinement
+                            recomputes the exact FP64 residual F* = B + P.H - H and continues
+                            sweeping from it until ||F*||_1 <= tol (at most 4 rounds). */
+    int32_t host_loop;   /* 1: drive sweeps from the host (one sync per sweep) instead of a CUDA
+                            graph WHILE node; default 0 */
+    int32_t rhs_tile;    /* batched solves: RHS per tile (0: autotuned; else 1..64) */
+    int32_t profile;     /* 1: host-driven sweeps with CUDA events around every kernel launch;
+                            fills the per-kernel times of di_solve_info (slower: one sync per
+                            sweep) */
+    int32_t reserved;
+} di_solve_opts;
+
+/* Per-solve report. */
+typedef struct {
+    int32_t sweeps;          /* sweeps (or PI iterations) executed */
+    int32_t refine_rounds;   /* exact-residual recomputations */
+    int64_t pushed_edges;    /* sum of out_i over visited nodes (PI: L * iterations) */
+    int64_t visited_nodes;   /* node diffusions */
+    double residual_l1;      /* ||F||_1 at exit (after refinement: exact FP64 ||F*||_1);
+                                PI: ||X_k - X_(k-1)||_1 */
+    double dangling_mass_e;  /* e = sum of H over dangling nodes (Section 2.5 DI-CYC) */
+    double paper_error;      /* residual / (1 - d - d e), the paper's normalised error */
+    double ms;               /* device time of the solve (CUDA events), copies excluded */
+    int64_t kernel_launches; /* kernels of this library launched by the call */
+    int64_t frontier_entries;/* nodes handed to the push kernel (visited nodes with out-links) */
+    /* per-kernel device time and launch counts; filled only when opts.profile = 1
+       (PI: push_* is the pull kernel, select_* the heavy-row pre-pass) */
+    double select_ms, push_ms, reduce_ms, refine_ms;
+    int32_t select_launches, push_launches, reduce_launches, refine_launches;
+} di_solve_info;
+
+/* Which internal array di_graph_export copies. */
+typedef enum {
+    DI_ARR_ROWPTR_OUT = 0,   /* int64[n+1]: out-CSR row pointers (column view of P, l_out) */
+    DI_ARR_COL_OUT = 1,      /* int32[L]:   destinations, ascending within each row */
+    DI_ARR_ROWPTR_IN = 2,    /* int64[n+1]: in-CSR row pointers (row view of P, l_in) */
+    DI_ARR_COL_IN = 3,       /* int32[L]:   origins, ascending within each row */
+    DI_ARR_OUT_DEG = 4,      /* int32[n] */
+    DI_ARR_IN_DEG = 5,       /* int32[n] */
+    DI_ARR_LOOP = 6,         /* uint8[n]:   1 when the node links to itself */
+    DI_ARR_E_MASK = 7,       /* uint8[n]:   1 when the node is in E */
+    DI_ARR_E_LEVEL = 8       /* int32[n]:   peeling level in E, -1 outside E */
+} di_array;
+
+/*
+ * di_graph_create — iterator build ("Init", Section 2.1; Section 2.5 out[], in[], l_out,
+ * l_in; Section 2.4 L, D, E, O, max_in, max_out).
+ *   n_nodes   number of nodes, 1 .. 2^31-1.
+ *   src, dst  int32[n_edges]: link src[e] -> dst[e]. Host or device memory. Any order;
+ *             duplicates are dropped (a link counts once in L and in the degrees).
+ *   n_edges   0 .. 2^31-1.
+ *   out       receives a new graph handle owned by the caller (free with di_graph_destroy).
+ *             The handle owns its device arrays; they live on the device current at the call.
+ * Errors: DI_ERR_INVALID_ARG (sizes, NULL), DI_ERR_OUT_OF_RANGE_ID (the message names the first
+ * bad edge), DI_ERR_OOM, DI_ERR_CUDA. On error *out is set to NULL.
+ */
+di_status di_graph_create(int32_t n_nodes, const int32_t *src, const int32_t *dst, int64_t n_edges,
+                          void *stream, di_graph **out);
+
+/* Releases the graph and its device memory. NULL is ignored. */
+void di_graph_destroy(di_graph *g);
+
+/* Copies the statistics of Section 2.4 into *out. */
+di_status di_graph_stats_get(const di_graph *g, di_graph_stats *out);
+
+/*
+ * di_graph_export — copies one internal array (see di_array for type and length) into dst,
+ * host or device memory of at least `capacity_bytes`. Errors: DI_ERR_INVALID_ARG when `which`
+ * is unknown or the buffer is too small.
+ */
+di_status di_graph_export(const di_graph *g, int32_t which, void *dst, int64_t capacity_bytes,
+                          void *stream);
+
+/*
+ * di_solve — D-iteration (Section 2.3 DI-CYC / DI-SOP, Section 2.5): H = 0, F = B, then sweeps
+ * until ||F||_1 <= tol. A sweep takes r = ||F||_1, selects nodes by `schedule` (a DI-SOP sweep
+ * that selects nothing is followed by a DI-CYC sweep), and diffuses every selected node: H_i
+ * gains transit = F_i (F_i * out_i / (out_i - d) for a loop node), F_i becomes 0 and every
+ * out-neighbour j != i gains d * transit / out_i. Selected nodes diffuse concurrently, so the
+ * trajectory differs from the sequential one; the fixed point X = lim H does not.
+ *   B          double[n]: right-hand side, >= 0 and finite.
+ *   d          damping, 0 <= d < 1.   tol > 0: stop when ||F||_1 <= tol.
+ *   X_out      double[n]: receives H (the approximation of X; ||X - H||_1 <= residual/(1-d)).
+ *   residual_out (nullable) receives info.residual_l1.   info (nullable) receives the report.
+ * Uses FP32 fluid with refinement (see di_solve_opts); di_solve_ex takes explicit options.
+ * Errors: DI_ERR_INVALID_ARG, DI_ERR_NOT_CONVERGED (X_out and the residual still hold the
+ * current state), DI_ERR_BUSY, DI_ERR_OOM, DI_ERR_CUDA.
+ */
+di_status di_solve(di_graph *g, const double *B, double d, double tol, int32_t schedule,
+                   int32_t max_sweeps, double *X_out, double *residual_out, di_solve_info *info,
+                   void *stream);
+
+/* di_solve with explicit options (opts may be NULL for defaults). Same errors as di_solve. */
+di_status di_solve_ex(di_graph *g, const double *B, double d, double tol, const di_solve_opts *opts,
+                      double *X_out, double *residual_out, di_solve_info *info, void *stream);
+
+/*
+ * di_power_iter — power iteration PI (Section 2.3, Section 2.5 "PI": row vectors, i.e. a pull
+ * over the in-links), applied to X = P.X + B as a Jacobi iteration: X_0 = 0,
+ * X_(k+1) = B + P.X_k, stopping when ||X_(k+1) - X_k||_1 <= tol or after max_iters (<= 0:
+ * 100000) iterations. FP64 throughout. X_out double[n]; residual_out and info nullable.
+ * Errors as di_solve.
+ */
+di_status di_power_iter(di_graph *g, const double *B, double d, double tol, int32_t max_iters,
+                        double *X_out, double *residual_out, di_solve_info *info, void *stream);
+
+/* Thread-local message of the last failing call on this thread ("" when none). */
+const char *di_last_error(void);
+
+/* Library version string. */
+const char *di_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DI_GB300_H */

@@ -1,0 +1,252 @@
+"""GB300 (sm_103a) D-iteration: Python binding of the C ABI in include/di.h.
+
+The functions here carry the C names and only marshal arguments: every step of the graph build
+and of the solves runs in the CUDA library `_lib/libdi_gb300.so` (built from `csrc/` by
+`build()`). Arrays may be numpy arrays (host) or torch tensors (host or CUDA); pointers go to the
+library as they are, and CUDA work is ordered on torch's current stream when a CUDA tensor is
+involved. There is no CPU fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH, build as _build
+
+__all__ = [
+    "build", "load", "DiError", "Graph",
+    "DI_CYC", "DI_SOP", "DI_FLUID_F32", "DI_FLUID_F64",
+    "di_graph_create", "di_graph_destroy", "di_graph_stats_get", "di_graph_export",
+    "di_solve", "di_solve_ex", "di_power_iter", "di_last_error", "di_version",
+]
+
+DI_CYC, DI_SOP = 0, 1
+DI_FLUID_F32, DI_FLUID_F64 = 0, 1
+STATUS = {0: "DI_OK", 1: "DI_ERR_INVALID_ARG", 2: "DI_ERR_OUT_OF_RANGE_ID", 3: "DI_ERR_OOM", 4: "DI_ERR_CUDA",
+          5: "DI_ERR_NOT_CONVERGED", 6: "DI_ERR_BUSY", 7: "DI_ERR_TIMEOUT"}
+ARRAYS = {  # di_array id -> (numpy dtype, length kind)
+    "rowptr_out": (0, np.int64, "n+1"), "col_out": (1, np.int32, "L"), "rowptr_in": (2, np.int64, "n+1"),
+    "col_in": (3, np.int32, "L"), "out_deg": (4, np.int32, "n"), "in_deg": (5, np.int32, "n"),
+    "loop": (6, np.uint8, "n"), "e_mask": (7, np.uint8, "n"), "e_level": (8, np.int32, "n"),
+}
+
+
+class DiError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class GraphStats(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("L", ctypes.c_int64), ("D", ctypes.c_int64), ("E", ctypes.c_int64),
+                ("O", ctypes.c_int64), ("max_in", ctypes.c_int32), ("max_out", ctypes.c_int32),
+                ("e_levels", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("fluid", ctypes.c_int32), ("max_sweeps", ctypes.c_int32),
+                ("refine", ctypes.c_int32), ("host_loop", ctypes.c_int32), ("rhs_tile", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("refine_rounds", ctypes.c_int32), ("pushed_edges", ctypes.c_int64),
+                ("visited_nodes", ctypes.c_int64), ("residual_l1", ctypes.c_double),
+                ("dangling_mass_e", ctypes.c_double), ("paper_error", ctypes.c_double), ("ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64), ("frontier_entries", ctypes.c_int64),
+                ("select_ms", ctypes.c_double), ("push_ms", ctypes.c_double), ("reduce_ms", ctypes.c_double),
+                ("refine_ms", ctypes.c_double), ("select_launches", ctypes.c_int32),
+                ("push_launches", ctypes.c_int32), ("reduce_launches", ctypes.c_int32),
+                ("refine_launches", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library in-tree (nvcc, sm_103a)."""
+    return _build(force=force)
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        raise OSError(f"CUDA library {path} is missing: run paper_1204_6255_gb300.build() first")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    st = ctypes.c_int
+    lib.di_graph_create.restype = st
+    lib.di_graph_create.argtypes = [i32, vp, vp, i64, vp, ctypes.POINTER(vp)]
+    lib.di_graph_destroy.restype = None
+    lib.di_graph_destroy.argtypes = [vp]
+    lib.di_graph_stats_get.restype = st
+    lib.di_graph_stats_get.argtypes = [vp, ctypes.POINTER(GraphStats)]
+    lib.di_graph_export.restype = st
+    lib.di_graph_export.argtypes = [vp, i32, vp, i64, vp]
+    lib.di_solve.restype = st
+    lib.di_solve.argtypes = [vp, vp, dbl, dbl, i32, i32, vp, vp, ctypes.POINTER(SolveInfo), vp]
+    lib.di_solve_ex.restype = st
+    lib.di_solve_ex.argtypes = [vp, vp, dbl, dbl, ctypes.POINTER(SolveOpts), vp, vp, ctypes.POINTER(SolveInfo), vp]
+    lib.di_power_iter.restype = st
+    lib.di_power_iter.argtypes = [vp, vp, dbl, dbl, i32, vp, vp, ctypes.POINTER(SolveInfo), vp]
+    lib.di_last_error.restype = ctypes.c_char_p
+    lib.di_last_error.argtypes = []
+    lib.di_version.restype = ctypes.c_char_p
+    lib.di_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------------------------------------
+# marshalling helpers
+# ------------------------------------------------------------------------------------------
+def _is_torch(x) -> bool:
+    return hasattr(x, "data_ptr") and hasattr(x, "is_cuda")
+
+
+def _ptr(x, dtype):
+    """Raw pointer of a contiguous numpy array or torch tensor of the given numpy dtype."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        import torch
+        tmap = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64, np.uint8: torch.uint8}
+        if x.dtype != tmap[np.dtype(dtype).type] or not x.is_contiguous():
+            raise TypeError(f"expected a contiguous {np.dtype(dtype)} tensor, got {x.dtype}")
+        return x.data_ptr()
+    if not isinstance(x, np.ndarray) or x.dtype != np.dtype(dtype) or not x.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a contiguous numpy {np.dtype(dtype)} array")
+    return x.ctypes.data
+
+
+def _stream(*arrays):
+    for a in arrays:
+        if _is_torch(a) and a.is_cuda:
+            import torch
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
+def _check(status: int):
+    if status != 0:
+        raise DiError(status, load().di_last_error().decode())
+
+
+def _like(x, n: int, dtype):
+    if _is_torch(x):
+        import torch
+        return torch.empty(n, dtype=torch.float64, device=x.device)
+    return np.empty(n, dtype=dtype)
+
+
+# ------------------------------------------------------------------------------------------
+# C ABI, same names
+# ------------------------------------------------------------------------------------------
+class Graph:
+    """Owning wrapper of a di_graph handle."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = handle
+        self.n = n
+        self._stats = None
+
+    @property
+    def stats(self) -> dict:
+        if self._stats is None:
+            self._stats = di_graph_stats_get(self)
+        return self._stats
+
+    def close(self):
+        if self.handle:
+            load().di_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def di_graph_create(n_nodes: int, src, dst) -> Graph:
+    lib = load()
+    h = ctypes.c_void_p()
+    m = int(src.shape[0])
+    if int(dst.shape[0]) != m:
+        raise ValueError("src and dst differ in length")
+    _check(lib.di_graph_create(int(n_nodes), _ptr(src, np.int32), _ptr(dst, np.int32), m, _stream(src, dst),
+                               ctypes.byref(h)))
+    return Graph(h.value, int(n_nodes))
+
+
+def di_graph_destroy(g: Graph):
+    g.close()
+
+
+def di_graph_stats_get(g: Graph) -> dict:
+    s = GraphStats()
+    _check(load().di_graph_stats_get(g.handle, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in s._fields_ if k != "reserved"}
+
+
+def di_graph_export(g: Graph, which: str, out=None):
+    """Copy an internal array ("rowptr_out", "col_out", "rowptr_in", "col_in", "out_deg", "in_deg",
+    "loop", "e_mask", "e_level") into `out` (numpy or torch), or a new numpy array."""
+    code, dtype, kind = ARRAYS[which]
+    st = g.stats
+    length = {"n+1": g.n + 1, "L": st["L"], "n": g.n}[kind]
+    if out is None:
+        out = np.empty(length, dtype=dtype)
+    nbytes = out.numel() * out.element_size() if _is_torch(out) else out.nbytes
+    _check(load().di_graph_export(g.handle, code, _ptr(out, dtype), nbytes, _stream(out)))
+    return out
+
+
+def di_solve(g: Graph, B, d: float, tol: float, schedule: int = DI_SOP, max_sweeps: int = 0, X_out=None):
+    """D-iteration with default options (FP32 fluid + FP64 refinement). Returns (X, info)."""
+    X = X_out if X_out is not None else _like(B, g.n, np.float64)
+    info = SolveInfo()
+    res = ctypes.c_double()
+    _check(load().di_solve(g.handle, _ptr(B, np.float64), float(d), float(tol), int(schedule), int(max_sweeps),
+                           _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)))
+    return X, info.as_dict()
+
+
+def di_solve_ex(g: Graph, B, d: float, tol: float, schedule: int = DI_SOP, fluid: int = DI_FLUID_F32,
+                max_sweeps: int = 0, refine: int = 0, host_loop: int = 0, profile: int = 0, X_out=None):
+    """D-iteration with explicit options. Returns (X, info)."""
+    X = X_out if X_out is not None else _like(B, g.n, np.float64)
+    o = SolveOpts(int(schedule), int(fluid), int(max_sweeps), int(refine), int(host_loop), 0, int(profile), 0)
+    info = SolveInfo()
+    res = ctypes.c_double()
+    _check(load().di_solve_ex(g.handle, _ptr(B, np.float64), float(d), float(tol), ctypes.byref(o),
+                              _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)))
+    return X, info.as_dict()
+
+
+def di_power_iter(g: Graph, B, d: float, tol: float, max_iters: int = 0, X_out=None):
+    """Jacobi power iteration on X = P.X + B. Returns (X, info)."""
+    X = X_out if X_out is not None else _like(B, g.n, np.float64)
+    info = SolveInfo()
+    res = ctypes.c_double()
+    _check(load().di_power_iter(g.handle, _ptr(B, np.float64), float(d), float(tol), int(max_iters),
+                                _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)))
+    return X, info.as_dict()
+
+
+def di_last_error() -> str:
+    return load().di_last_error().decode()
+
+
+def di_version() -> str:
+    return load().di_version().decode()

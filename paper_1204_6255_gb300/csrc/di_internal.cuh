@@ -1,0 +1,247 @@
+// Internal declarations of the GB300 D-iteration library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "di.h"
+
+namespace di {
+
+// ------------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+void clear_error();
+
+struct Fail {
+    di_status status;
+};
+
+#define DI_CHECK_CUDA(expr)                                                                     \
+    do {                                                                                        \
+        cudaError_t _e = (expr);                                                                \
+        if (_e != cudaSuccess) {                                                                \
+            ::di::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__,   \
+                            __LINE__);                                                          \
+            throw ::di::Fail{_e == cudaErrorMemoryAllocation ? DI_ERR_OOM : DI_ERR_CUDA};       \
+        }                                                                                       \
+    } while (0)
+
+#define DI_REQUIRE(cond, status, ...)                                                           \
+    do {                                                                                        \
+        if (!(cond)) {                                                                          \
+            ::di::set_error(__VA_ARGS__);                                                       \
+            throw ::di::Fail{status};                                                           \
+        }                                                                                       \
+    } while (0)
+
+// Runs `body` and converts a thrown Fail into its status; also catches allocation failures.
+template <class F>
+di_status guarded(F &&body) {
+    clear_error();
+    try {
+        body();
+        return DI_OK;
+    } catch (const Fail &f) {
+        return f.status;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return DI_ERR_OOM;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// device memory owned by the library
+// ------------------------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // (Re)allocates to at least `n` bytes; contents are not preserved.
+    void ensure(size_t n) {
+        if (n <= bytes && p) return;
+        release();
+        size_t b = n ? n : 16;
+        DI_CHECK_CUDA(cudaMalloc(&p, b));
+        bytes = b;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+// True when `ptr` is device (or managed) memory.
+bool is_device_ptr(const void *ptr);
+
+// Copies `bytes` from src (host or device) into device buffer dst on `s`.
+void to_device(void *dst, const void *src, size_t bytes, cudaStream_t s);
+// Copies device src into dst (host or device) on `s`.
+void from_device(void *dst, const void *src, size_t bytes, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// launch geometry
+// ------------------------------------------------------------------------------------------
+struct DeviceInfo {
+    int device = 0;
+    int sms = 0;
+    int max_threads_per_sm = 0;
+    size_t l2_bytes = 0;
+};
+DeviceInfo query_device();
+
+// ------------------------------------------------------------------------------------------
+// solve control block (device resident; one per workspace)
+// ------------------------------------------------------------------------------------------
+struct SolveCtl {
+    // parameters written by the host before a launch
+    double d;
+    double tol;
+    double L;                 // links (DI-SOP threshold is (r / L) * out_i)
+    int32_t schedule;
+    int32_t max_sweeps;
+    // state
+    double r;                 // ||F||_1 after the latest reduction
+    double e;                 // dangling mass sum_{out=0} H
+    unsigned long long pushed;
+    unsigned long long visited;
+    int32_t sweeps;
+    int32_t force_cyc;        // next selection ignores the DI-SOP threshold
+    int32_t last_selected;    // nodes selected by the latest sweep, -1 before the first
+    int32_t front_count;      // light frontier entries written by the latest selection
+    int32_t heavy_count;      // heavy frontier entries written by the latest selection
+    int32_t batch_next;       // dynamic work counter of the push kernel
+    int32_t done;             // 1 when the stop test has fired
+    int32_t status;           // 0 ok; 1 bad right-hand side
+    uint32_t ticket;          // last-block-done counter of the reductions
+    int32_t body_runs;        // executions of the WHILE body (kernel-launch accounting)
+    unsigned long long front_total;  // frontier entries over all sweeps
+};
+
+// Fixed tuning of the single-RHS kernels.
+constexpr int kPushHeavy = 4096;    // out-degree above which a node's edges are split over warps
+constexpr int kPullHeavy = 8192;    // in-degree above which a row's edges are split over warps
+constexpr int kPullChunk = 4096;    // edges per heavy-row chunk of the pull
+constexpr int kReduceBlocks = 1024; // partial sums of the last-block-done reductions
+
+// Per-graph state for single-RHS solves and power iteration.
+struct Workspace {
+    int fluid = -1;                 // di_fluid the buffers were sized for
+    DevBuf F, H, B, front_id, front_s, heavy_id, heavy_s, partials, ctl, y0, y1;
+    cudaGraphExec_t sweep_exec = nullptr;   // reduce -> WHILE{select, push, reduce}
+    cudaGraphExec_t pi_exec = nullptr;      // pull -> WHILE{pull}
+    cudaStream_t capture_stream = nullptr;
+    SolveCtl *ctl_host = nullptr;           // pinned mirror for readback
+    void reset_graphs();
+    ~Workspace();
+};
+
+}  // namespace di
+
+struct di_graph {
+    int32_t n = 0;
+    int64_t L = 0;
+    int bits = 1;                  // bits per node id in packed keys
+    di::DeviceInfo dev;
+    di_graph_stats stats{};
+    di::DevBuf rp_out, col_out, rp_in, col_in;   // int64 / int32
+    di::DevBuf out_info;           // int32: out-degree | loop << 31
+    di::DevBuf out_deg, in_deg;    // int32
+    di::DevBuf loop;               // uint8
+    di::DevBuf e_mask;             // uint8
+    di::DevBuf e_level;            // int32
+    // heavy rows of the in-CSR (in-degree > kPullHeavy), for the pull kernels
+    int32_t n_heavy_in = 0;
+    int32_t n_heavy_in_chunks = 0;
+    di::DevBuf heavy_in_rows;      // int32[n_heavy_in], ascending
+    di::DevBuf heavy_in_chunk_off; // int32[n_heavy_in + 1]
+    di::DevBuf heavy_in_chunk_row; // int32[n_heavy_in_chunks]: heavy index of each chunk
+    di::DevBuf heavy_in_partial;   // double[n_heavy_in_chunks]
+    int64_t n_heavy_out = 0;       // nodes with out-degree > kPushHeavy
+    std::mutex mu;                 // serialises use of the workspaces
+    di::Workspace ws;
+};
+
+namespace di {
+// Solve entry used by the C ABI functions (di_solve.cu).
+di_status solve_single(di_graph *g, const double *B, double d, double tol, const di_solve_opts *opts,
+                       double *X_out, double *residual_out, di_solve_info *info, cudaStream_t s);
+di_status power_iter(di_graph *g, const double *B, double d, double tol, int32_t max_iters,
+                     double *X_out, double *residual_out, di_solve_info *info, cudaStream_t s);
+}  // namespace di
+
+// ------------------------------------------------------------------------------------------
+// small device helpers
+// ------------------------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace di {
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Inclusive prefix sum across the warp.
+template <class T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T u = __shfl_up_sync(kFull, v, o);
+        if (lane >= (unsigned)o) v += u;
+    }
+    return v;
+}
+
+// Block-wide sum; every thread receives the total. `scratch` holds one T per warp.
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T *scratch) {
+    const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane_id() == 0) scratch[warp] = v;
+    __syncthreads();
+    T t = 0;
+    for (int w = 0; w < nw; w++) t += scratch[w];
+    return t;
+}
+
+// Largest lane k with off_k <= q, for lane offsets that are non-decreasing across the warp.
+// Every lane of the warp must call it.
+__device__ __forceinline__ int warp_owner(int off, int q) {
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        int o = __shfl_sync(kFull, off, pos + s);
+        if (o <= q) pos += s;
+    }
+    return pos;
+}
+
+__device__ __forceinline__ void red_add(float *p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add(double *p, double v) { atomicAdd(p, v); }
+}  // namespace di
+#endif

@@ -1,0 +1,797 @@
+// Single right-hand-side D-iteration and power iteration on the GPU.
+//
+// A sweep (Section 2.3 DI-CYC / DI-SOP, Section 2.5) is three kernels:
+//   k_select  reads F and out[], picks the nodes of the sweep (DI-CYC: F_i != 0; DI-SOP:
+//             |F_i| > (r / L) * out_i with r = ||F||_1 taken at the sweep start), and performs the
+//             node part of every visit: F_i -> 0, transit (F_i * out_i / (out_i - d) for a loop
+//             node), H_i += transit, dangling mass e. Visited nodes with out-links are appended to
+//             the frontier with their per-link share d * transit / out_i.
+//   k_push    scatters each frontier entry's share onto its out-neighbours j != i with fire-and-
+//             forget atomic adds into F (the `l_out` loop of Section 2.5). Warps take batches of
+//             32 frontier entries and walk their concatenated out-links 32 at a time, so the col
+//             index loads of consecutive lanes are contiguous within each row; nodes with more
+//             than kPushHeavy links are spread over every warp of the grid.
+//   k_reduce  r = sum |F_i| in FP64 (warp shuffle, block, then the last block to finish sums
+//             the block partials in a fixed order), and the stop test r <= tol. It writes the
+//             WHILE-node condition, so the whole sweep loop runs from one CUDA graph launch.
+// All selected nodes diffuse concurrently; the result is a valid D-iteration in another
+// diffusion order, which reaches the same fixed point.
+//
+// Power iteration (Section 2.5 "PI", Jacobi on X = P.X + B) and the exact FP64 residual
+// F* = B + P.H - H both use k_pull: a warp takes 32 consecutive rows of the in-CSR, walks their
+// contiguous in-links 32 at a time and reduces per row with a segmented warp scan; rows with
+// more than kPullHeavy in-links are summed chunk-wise by k_pull_heavy first.
+#include <cmath>
+#include <cstring>
+
+#include "di_internal.cuh"
+
+namespace di {
+
+// ------------------------------------------------------------------------------------------
+// kernels
+// ------------------------------------------------------------------------------------------
+template <class T>
+__global__ void k_init(const double *B, int32_t n, T *F, double *H, SolveCtl *ctl) {
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double b = B[i];
+        if (!(b >= 0.0) || isinf(b)) bad = true;
+        F[i] = (T)b;
+        H[i] = 0.0;
+    }
+    if (bad) ctl->status = 1;
+}
+
+// Last-block-done FP64 sum of the per-block partials; returns true in the finishing block,
+// where `total` holds the grand total (thread 0 only needs it).
+__device__ __forceinline__ bool finish_sum(double s, double *partials, SolveCtl *ctl, double *scratch, double &total) {
+    __shared__ bool is_last;
+    s = block_sum(s, scratch);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = s;
+        __threadfence();
+        unsigned t = atomicAdd(&ctl->ticket, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc += __ldcg(&partials[b]);
+    total = block_sum(acc, scratch);
+    return true;
+}
+
+// r = ||F||_1, stop test, and bookkeeping for the next selection.
+template <class T>
+__global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl, cudaGraphConditionalHandle h,
+                         int set_cond) {
+    __shared__ double scratch[32];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += fabs((double)F[i]);
+    double tot;
+    if (!finish_sum(s, partials, ctl, scratch, tot)) return;
+    if (threadIdx.x == 0) {
+        ctl->ticket = 0;
+        ctl->r = tot;
+        int sel = ctl->last_selected;
+        ctl->force_cyc = (sel == 0 && tot > 0.0) ? 1 : 0;   // a DI-SOP sweep found no node
+        ctl->last_selected = 0;
+        ctl->front_total += (unsigned long long)(ctl->front_count + ctl->heavy_count);
+        ctl->front_count = 0;
+        ctl->heavy_count = 0;
+        ctl->batch_next = 0;
+        if (set_cond) ctl->body_runs++;
+        bool cont = ctl->status == 0 && tot > ctl->tol && ctl->sweeps < ctl->max_sweeps;
+        ctl->done = cont ? 0 : 1;
+        if (set_cond) cudaGraphSetConditional(h, cont ? 1u : 0u);
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_select(T *F, double *H, const int32_t *out_info, int32_t n, SolveCtl *ctl,
+                                                int32_t *front_id, T *front_s, int32_t *heavy_id, T *heavy_s) {
+    __shared__ double scratch[32];
+    __shared__ unsigned long long scratch_u[32];
+    if (ctl->done) return;
+    const double r = ctl->r, d = ctl->d;
+    const bool cyc = ctl->schedule == DI_CYC || ctl->force_cyc;
+    const double thr = ctl->L > 0.0 ? r / ctl->L : 0.0;
+    const unsigned lane = lane_id(), lt = lanemask_lt();
+    double e_loc = 0.0;
+    unsigned long long pushed = 0, visited = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        bool light = false, heavy = false;
+        double share = 0.0;
+        if (i < n) {
+            const T f = F[i];
+            const int32_t info = out_info[i];
+            const int32_t o = info & 0x7fffffff;
+            const bool lp = info < 0;
+            const double af = fabs((double)f);
+            const bool sel = cyc ? (f != (T)0) : (af > thr * (double)o);
+            if (sel) {
+                F[i] = (T)0;
+                const double t = lp ? (double)f * (double)o / ((double)o - d) : (double)f;
+                H[i] += t;
+                visited++;
+                pushed += (unsigned long long)o;
+                if (o == 0) {
+                    e_loc += t;
+                } else {
+                    share = t * d / (double)o;
+                    if (o > kPushHeavy) heavy = true;
+                    else if (o - (lp ? 1 : 0) > 0) light = true;
+                }
+            }
+        }
+        const unsigned bl = __ballot_sync(kFull, light);
+        if (bl) {
+            const int leader = __ffs(bl) - 1;
+            int p0 = 0;
+            if ((int)lane == leader) p0 = atomicAdd(&ctl->front_count, __popc(bl));
+            p0 = __shfl_sync(kFull, p0, leader);
+            if (light) {
+                const int p = p0 + __popc(bl & lt);
+                front_id[p] = (int32_t)i;
+                front_s[p] = (T)share;
+            }
+        }
+        const unsigned bh = __ballot_sync(kFull, heavy);
+        if (bh) {
+            const int leader = __ffs(bh) - 1;
+            int p0 = 0;
+            if ((int)lane == leader) p0 = atomicAdd(&ctl->heavy_count, __popc(bh));
+            p0 = __shfl_sync(kFull, p0, leader);
+            if (heavy) {
+                const int p = p0 + __popc(bh & lt);
+                heavy_id[p] = (int32_t)i;
+                heavy_s[p] = (T)share;
+            }
+        }
+    }
+    e_loc = block_sum(e_loc, scratch);
+    pushed = block_sum(pushed, scratch_u);
+    visited = block_sum(visited, scratch_u);
+    if (threadIdx.x == 0) {
+        if (e_loc != 0.0) atomicAdd(&ctl->e, e_loc);
+        if (pushed) atomicAdd(&ctl->pushed, pushed);
+        if (visited) {
+            atomicAdd(&ctl->visited, visited);
+            atomicAdd(&ctl->last_selected, (int)visited);
+        }
+        if (blockIdx.x == 0) atomicAdd(&ctl->sweeps, 1);
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_id, const T *__restrict__ front_s,
+                                              const int32_t *__restrict__ heavy_id, const T *__restrict__ heavy_s,
+                                              const int64_t *__restrict__ rp_out, const int32_t *__restrict__ col_out,
+                                              T *F, SolveCtl *ctl) {
+    if (ctl->done) return;
+    const int lane = (int)lane_id();
+    const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+
+    // nodes with more than kPushHeavy links: their edges in chunks over all warps
+    const int hc = ctl->heavy_count;
+    constexpr int kChunk = 1024;
+    for (int h = 0; h < hc; h++) {
+        const int32_t u = heavy_id[h];
+        const T s = heavy_s[h];
+        const int64_t b = rp_out[u], e = rp_out[u + 1];
+        const int64_t nch = (e - b + kChunk - 1) / kChunk;
+        for (int64_t c = gwarp; c < nch; c += nwarps) {
+            const int64_t cb = b + c * kChunk, ce = min(cb + kChunk, e);
+            for (int64_t k = cb + lane; k < ce; k += 32) {
+                const int32_t j = col_out[k];
+                if (j != u) red_add(&F[j], s);
+            }
+        }
+    }
+
+    // light nodes: batches of 32 frontier entries; warps claim `grab` entries at a time
+    const int count = ctl->front_count;
+    const int grab = (count >= (int)(nwarps * 32 * 8)) ? 128 : 32;
+    for (;;) {
+        int c0 = 0;
+        if (lane == 0) c0 = atomicAdd(&ctl->batch_next, grab);
+        c0 = __shfl_sync(kFull, c0, 0);
+        if (c0 >= count) break;
+        const int cend = min(c0 + grab, count);
+        for (int b0 = c0; b0 < cend; b0 += 32) {
+            const int idx = b0 + lane;
+            int32_t u = -1;
+            T s = (T)0;
+            int64_t beg = 0;
+            int deg = 0;
+            if (idx < cend) {
+                u = front_id[idx];
+                s = front_s[idx];
+                beg = rp_out[u];
+                deg = (int)(rp_out[u + 1] - beg);
+            }
+            const int inc = warp_inclusive_scan(deg);
+            const int off = inc - deg;
+            const int total = __shfl_sync(kFull, inc, 31);
+            for (int q0 = 0; q0 < total; q0 += 32) {
+                const int q = q0 + lane;
+                const int ow = warp_owner(off, q);
+                const int64_t ob = __shfl_sync(kFull, beg, ow);
+                const int oo = __shfl_sync(kFull, off, ow);
+                const int32_t ou = __shfl_sync(kFull, u, ow);
+                const T os = __shfl_sync(kFull, s, ow);
+                if (q < total) {
+                    const int32_t j = col_out[ob + (q - oo)];
+                    if (j != ou) red_add(&F[j], os);
+                }
+            }
+        }
+    }
+}
+
+// y[j] = d * v[j] / out_j (0 for a dangling node)
+__global__ void k_scale(const double *v, const int32_t *out_info, int32_t n, double d, double *y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = out_info[i] & 0x7fffffff;
+        y[i] = o ? d * v[i] / (double)o : 0.0;
+    }
+}
+
+// partial[c] = sum of y over the in-links of heavy-row chunk c
+__global__ void k_pull_heavy(const int64_t *rp_in, const int32_t *col_in, const int32_t *heavy_rows,
+                             const int32_t *chunk_off, const int32_t *chunk_row, int32_t n_chunks,
+                             const double *y0, const double *y1, const SolveCtl *ctl, int alternate,
+                             double *partial) {
+    const double *y = (alternate && (ctl->sweeps & 1)) ? y1 : y0;
+    const int lane = (int)lane_id();
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += nwarps) {
+        const int32_t h = chunk_row[c];
+        const int32_t row = heavy_rows[h];
+        const int64_t b = rp_in[row] + (int64_t)(c - chunk_off[h]) * kPullChunk;
+        const int64_t e = min(b + (int64_t)kPullChunk, rp_in[row + 1]);
+        double s = 0.0;
+        for (int64_t k = b + lane; k < e; k += 32) s += y[col_in[k]];
+        s = warp_sum(s);
+        if (lane == 0) partial[c] = s;
+    }
+}
+
+enum { PULL_PI = 0, PULL_RESID = 1 };
+
+// Row sums acc_i = sum_{j in in(i)} y_j for 32 consecutive rows per warp, then the epilogue:
+//   PULL_PI:    X'_i = B_i + acc_i, delta_i = |X'_i - X_i|, X_i = X'_i, y'_i = d X'_i / out_i;
+//               sum delta -> ctl->r, iteration count and WHILE condition.
+//   PULL_RESID: F*_i = B_i + acc_i - H_i -> F_i (as T); sum |F*| -> ctl->r.
+template <int MODE, class T>
+__global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in, const int32_t *__restrict__ col_in,
+                                              const double *y0, double *y1, int32_t n, const int32_t *heavy_rows,
+                                              const int32_t *heavy_chunk_off, const double *heavy_partial,
+                                              int32_t n_heavy, const double *__restrict__ B, double *X, T *F,
+                                              const int32_t *__restrict__ out_info, double *partials, SolveCtl *ctl,
+                                              cudaGraphConditionalHandle hcond, int set_cond) {
+    __shared__ double acc_s[8][32];
+    __shared__ double scratch[32];
+    const int lane = (int)lane_id(), warp = threadIdx.x >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double d = ctl->d;
+    const bool odd = (MODE == PULL_PI) && (ctl->sweeps & 1);
+    const double *y_in = odd ? y1 : y0;
+    double *y_out = odd ? const_cast<double *>(y0) : y1;
+    double sum = 0.0;
+    // every warp runs the same number of row groups so the block stays converged
+    const int64_t groups = ((int64_t)n + 31) >> 5;
+    const int64_t rounds = (groups + nwarps - 1) / nwarps;
+    for (int64_t rd = 0; rd < rounds; rd++) {
+        const int64_t grp = rd * nwarps + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+        const int64_t row = grp * 32 + lane;
+        const bool valid = row < n;
+        int64_t beg = 0;
+        int deg = 0;
+        bool heavy = false;
+        if (valid) {
+            beg = rp_in[row];
+            const int64_t dd = rp_in[row + 1] - beg;
+            heavy = dd > kPullHeavy;
+            deg = heavy ? 0 : (int)dd;
+        }
+        acc_s[warp][lane] = 0.0;
+        __syncwarp();
+        const int inc = warp_inclusive_scan(deg);
+        const int off = inc - deg;
+        const int total = __shfl_sync(kFull, inc, 31);
+        for (int q0 = 0; q0 < total; q0 += 32) {
+            const int q = q0 + lane;
+            const int ow = warp_owner(off, q);
+            const int64_t ob = __shfl_sync(kFull, beg, ow);
+            const int oo = __shfl_sync(kFull, off, ow);
+            const bool act = q < total;
+            double v = act ? y_in[col_in[ob + (q - oo)]] : 0.0;
+            const int own = act ? ow : 32;
+            // segmented inclusive scan; owners are non-decreasing across lanes
+#pragma unroll
+            for (int s = 1; s < 32; s <<= 1) {
+                const double vv = __shfl_up_sync(kFull, v, s);
+                const int o2 = __shfl_up_sync(kFull, own, s);
+                if (lane >= s && o2 == own) v += vv;
+            }
+            const int next_own = __shfl_down_sync(kFull, own, 1);
+            if (act && (lane == 31 || next_own != own)) acc_s[warp][own] += v;
+            __syncwarp();
+        }
+        double a = acc_s[warp][lane];
+        __syncwarp();
+        if (heavy) {
+            int lo = 0, hi = n_heavy - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (heavy_rows[mid] < row) lo = mid + 1; else hi = mid;
+            }
+            a = 0.0;
+            for (int c = heavy_chunk_off[lo]; c < heavy_chunk_off[lo + 1]; c++) a += heavy_partial[c];
+        }
+        if (valid) {
+            if (MODE == PULL_PI) {
+                const double xn = B[row] + a;
+                sum += fabs(xn - X[row]);
+                X[row] = xn;
+                const int32_t o = out_info[row] & 0x7fffffff;
+                y_out[row] = o ? d * xn / (double)o : 0.0;
+            } else {
+                const double fs = B[row] + a - X[row];
+                F[row] = (T)fs;
+                sum += fabs(fs);
+            }
+        }
+    }
+    double tot;
+    if (!finish_sum(sum, partials, ctl, scratch, tot)) return;
+    if (threadIdx.x == 0) {
+        ctl->ticket = 0;
+        ctl->r = tot;
+        if (MODE == PULL_PI) {
+            const int it = ctl->sweeps + 1;
+            ctl->sweeps = it;
+            if (set_cond) ctl->body_runs++;
+            const bool cont = tot > ctl->tol && it < ctl->max_sweeps;
+            ctl->done = cont ? 0 : 1;
+            if (set_cond) cudaGraphSetConditional(hcond, cont ? 1u : 0u);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+Workspace::~Workspace() {
+    reset_graphs();
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+    if (ctl_host) cudaFreeHost(ctl_host);
+}
+
+void Workspace::reset_graphs() {
+    if (sweep_exec) cudaGraphExecDestroy(sweep_exec);
+    if (pi_exec) cudaGraphExecDestroy(pi_exec);
+    sweep_exec = nullptr;
+    pi_exec = nullptr;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) DI_CHECK_CUDA(cudaSetDevice(dev));
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+struct Launch {
+    int sel_blocks, red_blocks, push_blocks, pull_blocks, ew_blocks;
+};
+
+// Counts the kernels a call launches from the host and, in profile mode, brackets each launch
+// with CUDA events on the launching stream (synchronising after it) to time it alone.
+enum { KC_SELECT = 0, KC_PUSH = 1, KC_REDUCE = 2, KC_REFINE = 3 };
+struct KernelClock {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    double ms[4] = {0, 0, 0, 0};
+    int count[4] = {0, 0, 0, 0};
+    int64_t host_launches = 0;
+    KernelClock(bool profile, cudaStream_t st) : on(profile), s(st) {
+        if (on) {
+            DI_CHECK_CUDA(cudaEventCreate(&a));
+            DI_CHECK_CUDA(cudaEventCreate(&b));
+        }
+    }
+    ~KernelClock() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    template <class F>
+    void run(int slot, int launches, F &&launch) {
+        host_launches += launches;
+        if (!on) {
+            launch();
+            return;
+        }
+        DI_CHECK_CUDA(cudaEventRecord(a, s));
+        launch();
+        DI_CHECK_CUDA(cudaEventRecord(b, s));
+        DI_CHECK_CUDA(cudaEventSynchronize(b));
+        float t = 0.f;
+        DI_CHECK_CUDA(cudaEventElapsedTime(&t, a, b));
+        ms[slot] += t;
+        count[slot] += 1;
+    }
+};
+
+template <class T>
+static Launch launch_shape(const di_graph *g) {
+    Launch l;
+    const int sms = g->dev.sms;
+    int occ = 0;
+    DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push<T>, 256, 0));
+    l.push_blocks = sms * (occ > 0 ? occ : 1);
+    DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pull<PULL_PI, T>, 256, 0));
+    l.pull_blocks = sms * (occ > 0 ? occ : 1);
+    const int64_t n = g->n;
+    auto cap = [&](int64_t want, int64_t lim) { return (int)(want < 1 ? 1 : (want < lim ? want : lim)); };
+    l.sel_blocks = cap((n + 255) / 256, (int64_t)sms * 8);
+    l.red_blocks = cap((n + 255) / 256, (int64_t)(kReduceBlocks < sms * 4 ? kReduceBlocks : sms * 4));
+    l.ew_blocks = cap((n + 255) / 256, (int64_t)sms * 8);
+    // a pull block never needs more row groups than exist
+    l.pull_blocks = cap(((n + 31) / 32 + 7) / 8, l.pull_blocks);
+    if (l.pull_blocks > kReduceBlocks) l.pull_blocks = kReduceBlocks;
+    return l;
+}
+
+template <class T>
+static void ensure_workspace(di_graph *g) {
+    Workspace &ws = g->ws;
+    const int fl = sizeof(T) == 4 ? DI_FLUID_F32 : DI_FLUID_F64;
+    if (ws.fluid == fl) return;
+    ws.reset_graphs();
+    const size_t n = (size_t)g->n;
+    ws.F.ensure(sizeof(T) * n);
+    ws.H.ensure(sizeof(double) * n);
+    ws.B.ensure(sizeof(double) * n);
+    ws.front_id.ensure(sizeof(int32_t) * n);
+    ws.front_s.ensure(sizeof(T) * n);
+    ws.heavy_id.ensure(sizeof(int32_t) * (size_t)(g->n_heavy_out + 1));
+    ws.heavy_s.ensure(sizeof(T) * (size_t)(g->n_heavy_out + 1));
+    ws.partials.ensure(sizeof(double) * kReduceBlocks);
+    ws.ctl.ensure(sizeof(SolveCtl));
+    ws.y0.ensure(sizeof(double) * n);
+    ws.y1.ensure(sizeof(double) * n);
+    if (!ws.capture_stream) DI_CHECK_CUDA(cudaStreamCreateWithFlags(&ws.capture_stream, cudaStreamNonBlocking));
+    if (!ws.ctl_host) DI_CHECK_CUDA(cudaMallocHost(&ws.ctl_host, sizeof(SolveCtl)));
+    ws.fluid = fl;
+}
+
+template <class T>
+static void launch_sweep_body(di_graph *g, const Launch &l, cudaStream_t s, cudaGraphConditionalHandle h, int set_cond,
+                              KernelClock *kc) {
+    Workspace &ws = g->ws;
+    SolveCtl *ctl = ws.ctl.as<SolveCtl>();
+    KernelClock none(false, s);
+    KernelClock &c = kc ? *kc : none;
+    c.run(KC_SELECT, 1, [&] {
+        k_select<T><<<l.sel_blocks, 256, 0, s>>>(ws.F.as<T>(), ws.H.as<double>(), g->out_info.as<int32_t>(), g->n, ctl,
+                                                  ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
+                                                  ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>());
+    });
+    c.run(KC_PUSH, 1, [&] {
+        k_push<T><<<l.push_blocks, 256, 0, s>>>(ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
+                                                ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(), g->rp_out.as<int64_t>(),
+                                                g->col_out.as<int32_t>(), ws.F.as<T>(), ctl);
+    });
+    c.run(KC_REDUCE, 1, [&] {
+        k_reduce<T><<<l.red_blocks, 256, 0, s>>>(ws.F.as<T>(), g->n, ws.partials.as<double>(), ctl, h, set_cond);
+    });
+}
+
+// Graph: WHILE(cond, default 1 at every launch) { select; push; reduce -> cond }.
+template <class T>
+static void build_sweep_graph(di_graph *g, const Launch &l) {
+    Workspace &ws = g->ws;
+    cudaGraph_t graph;
+    DI_CHECK_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    DI_CHECK_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    DI_CHECK_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    DI_CHECK_CUDA(cudaStreamBeginCaptureToGraph(ws.capture_stream, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal));
+    launch_sweep_body<T>(g, l, ws.capture_stream, h, 1, nullptr);
+    cudaGraph_t captured;
+    DI_CHECK_CUDA(cudaStreamEndCapture(ws.capture_stream, &captured));
+    DI_CHECK_CUDA(cudaGraphInstantiate(&ws.sweep_exec, graph, 0));
+    DI_CHECK_CUDA(cudaGraphDestroy(graph));
+}
+
+template <class T>
+static void launch_pi_body(di_graph *g, const Launch &l, cudaStream_t s, cudaGraphConditionalHandle h, int set_cond) {
+    Workspace &ws = g->ws;
+    SolveCtl *ctl = ws.ctl.as<SolveCtl>();
+    if (g->n_heavy_in_chunks > 0) {
+        int blocks = (int)((g->n_heavy_in_chunks + 7) / 8);
+        if (blocks > g->dev.sms * 8) blocks = g->dev.sms * 8;
+        k_pull_heavy<<<blocks, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(),
+                                            g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(),
+                                            g->heavy_in_chunk_row.as<int32_t>(), g->n_heavy_in_chunks,
+                                            ws.y0.as<double>(), ws.y1.as<double>(), ctl, 1,
+                                            g->heavy_in_partial.as<double>());
+    }
+    k_pull<PULL_PI, T><<<l.pull_blocks, 256, 0, s>>>(
+        g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<double>(), ws.y1.as<double>(), g->n,
+        g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<double>(),
+        g->n_heavy_in, ws.B.as<double>(), ws.H.as<double>(), (T *)nullptr, g->out_info.as<int32_t>(),
+        ws.partials.as<double>(), ctl, h, set_cond);
+}
+
+template <class T>
+static void build_pi_graph(di_graph *g, const Launch &l) {
+    Workspace &ws = g->ws;
+    cudaGraph_t graph;
+    DI_CHECK_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    DI_CHECK_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    DI_CHECK_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    DI_CHECK_CUDA(cudaStreamBeginCaptureToGraph(ws.capture_stream, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal));
+    launch_pi_body<T>(g, l, ws.capture_stream, h, 1);
+    cudaGraph_t captured;
+    DI_CHECK_CUDA(cudaStreamEndCapture(ws.capture_stream, &captured));
+    DI_CHECK_CUDA(cudaGraphInstantiate(&ws.pi_exec, graph, 0));
+    DI_CHECK_CUDA(cudaGraphDestroy(graph));
+}
+
+// F <- B + P.H - H (as T), ctl->r <- ||F*||_1 (exact FP64 residual of the history H).
+// Launches 2 or 3 kernels.
+template <class T>
+static void launch_refine(di_graph *g, const Launch &l, double d, cudaStream_t s) {
+    Workspace &ws = g->ws;
+    SolveCtl *ctl = ws.ctl.as<SolveCtl>();
+    k_scale<<<l.ew_blocks, 256, 0, s>>>(ws.H.as<double>(), g->out_info.as<int32_t>(), g->n, d, ws.y0.as<double>());
+    if (g->n_heavy_in_chunks > 0) {
+        int blocks = (int)((g->n_heavy_in_chunks + 7) / 8);
+        if (blocks > g->dev.sms * 8) blocks = g->dev.sms * 8;
+        k_pull_heavy<<<blocks, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(),
+                                            g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(),
+                                            g->heavy_in_chunk_row.as<int32_t>(), g->n_heavy_in_chunks,
+                                            ws.y0.as<double>(), ws.y1.as<double>(), ctl, 0,
+                                            g->heavy_in_partial.as<double>());
+    }
+    k_pull<PULL_RESID, T><<<l.pull_blocks, 256, 0, s>>>(
+        g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<double>(), ws.y1.as<double>(), g->n,
+        g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<double>(),
+        g->n_heavy_in, ws.B.as<double>(), ws.H.as<double>(), ws.F.as<T>(), g->out_info.as<int32_t>(),
+        ws.partials.as<double>(), ctl, cudaGraphConditionalHandle(0), 0);
+    DI_CHECK_CUDA(cudaGetLastError());
+}
+
+static void write_ctl(di_graph *g, double d, double tol, int schedule, int max_sweeps, cudaStream_t s) {
+    SolveCtl &c = *g->ws.ctl_host;
+    memset(&c, 0, sizeof(c));
+    c.d = d;
+    c.tol = tol;
+    c.L = (double)g->L;
+    c.schedule = schedule;
+    c.max_sweeps = max_sweeps;
+    c.last_selected = -1;
+    DI_CHECK_CUDA(cudaMemcpyAsync(g->ws.ctl.p, &c, sizeof(SolveCtl), cudaMemcpyHostToDevice, s));
+}
+
+static void read_ctl(di_graph *g, cudaStream_t s) {
+    DI_CHECK_CUDA(cudaMemcpyAsync(g->ws.ctl_host, g->ws.ctl.p, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
+    DI_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+static void check_common(di_graph *g, const double *B, double d, double tol, const double *X_out) {
+    DI_REQUIRE(g != nullptr, DI_ERR_INVALID_ARG, "graph is NULL");
+    DI_REQUIRE(B != nullptr && X_out != nullptr, DI_ERR_INVALID_ARG, "B or X_out is NULL");
+    DI_REQUIRE(d >= 0.0 && d < 1.0, DI_ERR_INVALID_ARG, "d must be in [0, 1) (got %g)", d);
+    DI_REQUIRE(tol > 0.0 && std::isfinite(tol), DI_ERR_INVALID_ARG, "tol must be positive and finite (got %g)", tol);
+}
+
+template <class T>
+static void solve_impl(di_graph *g, const double *B, double d, double tol, int schedule, int max_sweeps, int refine,
+                       int host_loop, int profile, double *X_out, double *residual_out, di_solve_info *info,
+                       cudaStream_t s) {
+    ensure_workspace<T>(g);
+    Workspace &ws = g->ws;
+    const Launch l = launch_shape<T>(g);
+    SolveCtl *ctl = ws.ctl.as<SolveCtl>();
+    to_device(ws.B.p, B, sizeof(double) * (size_t)g->n, s);
+    write_ctl(g, d, tol, schedule, max_sweeps, s);
+    if (profile) host_loop = 1;
+    KernelClock kc(profile != 0, s);
+    cudaEvent_t e0, e1;
+    DI_CHECK_CUDA(cudaEventCreate(&e0));
+    DI_CHECK_CUDA(cudaEventCreate(&e1));
+    int rounds = 0;
+    try {
+        DI_CHECK_CUDA(cudaEventRecord(e0, s));
+        kc.run(KC_REFINE, 1, [&] {
+            k_init<T><<<l.ew_blocks, 256, 0, s>>>(ws.B.as<double>(), g->n, ws.F.as<T>(), ws.H.as<double>(), ctl);
+        });
+        auto run_sweeps = [&]() {
+            kc.run(KC_REDUCE, 1, [&] {
+                k_reduce<T><<<l.red_blocks, 256, 0, s>>>(ws.F.as<T>(), g->n, ws.partials.as<double>(), ctl,
+                                                         cudaGraphConditionalHandle(0), 0);
+            });
+            DI_CHECK_CUDA(cudaGetLastError());
+            if (host_loop) {
+                for (;;) {
+                    read_ctl(g, s);
+                    if (ws.ctl_host->done) break;
+                    launch_sweep_body<T>(g, l, s, cudaGraphConditionalHandle(0), 0, &kc);
+                    DI_CHECK_CUDA(cudaGetLastError());
+                }
+            } else {
+                if (!ws.sweep_exec) build_sweep_graph<T>(g, l);
+                DI_CHECK_CUDA(cudaGraphLaunch(ws.sweep_exec, s));
+            }
+        };
+        run_sweeps();
+        // every refinement round ends on an exact residual, so the reported one is exact
+        while (refine) {
+            kc.run(KC_REFINE, g->n_heavy_in_chunks > 0 ? 3 : 2, [&] { launch_refine<T>(g, l, d, s); });
+            read_ctl(g, s);
+            rounds++;
+            if (ws.ctl_host->status || ws.ctl_host->r <= tol || ws.ctl_host->sweeps >= max_sweeps || rounds >= 4) break;
+            run_sweeps();
+        }
+        DI_CHECK_CUDA(cudaEventRecord(e1, s));
+        from_device(X_out, ws.H.p, sizeof(double) * (size_t)g->n, s);
+        read_ctl(g, s);
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const SolveCtl &c = *ws.ctl_host;
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->sweeps = c.sweeps;
+        info->refine_rounds = rounds;
+        info->pushed_edges = (int64_t)c.pushed;
+        info->visited_nodes = (int64_t)c.visited;
+        info->residual_l1 = c.r;
+        info->dangling_mass_e = c.e;
+        info->paper_error = c.r / (1.0 - d - d * c.e);
+        info->ms = ms;
+        info->kernel_launches = kc.host_launches + 3 * (int64_t)c.body_runs;
+        info->frontier_entries = (int64_t)c.front_total;
+        info->select_ms = kc.ms[KC_SELECT];
+        info->push_ms = kc.ms[KC_PUSH];
+        info->reduce_ms = kc.ms[KC_REDUCE];
+        info->refine_ms = kc.ms[KC_REFINE];
+        info->select_launches = kc.count[KC_SELECT];
+        info->push_launches = kc.count[KC_PUSH];
+        info->reduce_launches = kc.count[KC_REDUCE];
+        info->refine_launches = kc.count[KC_REFINE];
+    }
+    if (residual_out) *residual_out = c.r;
+    DI_REQUIRE(c.status == 0, DI_ERR_INVALID_ARG, "B has a negative or non-finite entry");
+    DI_REQUIRE(c.r <= tol, DI_ERR_NOT_CONVERGED, "not converged after %d sweeps: ||F||_1 = %g > tol = %g", c.sweeps,
+               c.r, tol);
+}
+
+di_status solve_single(di_graph *g, const double *B, double d, double tol, const di_solve_opts *opts, double *X_out,
+                       double *residual_out, di_solve_info *info, cudaStream_t s) {
+    return guarded([&] {
+        check_common(g, B, d, tol, X_out);
+        di_solve_opts o;
+        memset(&o, 0, sizeof(o));
+        if (opts) o = *opts;
+        DI_REQUIRE(o.schedule == DI_CYC || o.schedule == DI_SOP, DI_ERR_INVALID_ARG, "unknown schedule %d", o.schedule);
+        DI_REQUIRE(o.fluid == DI_FLUID_F32 || o.fluid == DI_FLUID_F64, DI_ERR_INVALID_ARG, "unknown fluid %d", o.fluid);
+        int max_sweeps = o.max_sweeps <= 0 ? 100000 : (o.max_sweeps > 1000000 ? 1000000 : o.max_sweeps);
+        int refine = o.refine == 0 ? (o.fluid == DI_FLUID_F32) : (o.refine > 0);
+        std::unique_lock<std::mutex> lk(g->mu, std::try_to_lock);
+        DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
+        DeviceGuard dg(g->dev.device);
+        if (o.fluid == DI_FLUID_F32)
+            solve_impl<float>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile, X_out,
+                              residual_out, info, s);
+        else
+            solve_impl<double>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile, X_out,
+                               residual_out, info, s);
+    });
+}
+
+di_status power_iter(di_graph *g, const double *B, double d, double tol, int32_t max_iters, double *X_out,
+                     double *residual_out, di_solve_info *info, cudaStream_t s) {
+    return guarded([&] {
+        check_common(g, B, d, tol, X_out);
+        int mi = max_iters <= 0 ? 100000 : (max_iters > 1000000 ? 1000000 : max_iters);
+        std::unique_lock<std::mutex> lk(g->mu, std::try_to_lock);
+        DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
+        DeviceGuard dg(g->dev.device);
+        using T = float;   // PI is FP64 throughout; the fluid buffers are unused
+        ensure_workspace<T>(g);
+        Workspace &ws = g->ws;
+        const Launch l = launch_shape<T>(g);
+        to_device(ws.B.p, B, sizeof(double) * (size_t)g->n, s);
+        write_ctl(g, d, tol, DI_CYC, mi, s);
+        // X_0 = 0 (kept in H), y_0 = 0
+        DI_CHECK_CUDA(cudaMemsetAsync(ws.H.p, 0, sizeof(double) * (size_t)g->n, s));
+        DI_CHECK_CUDA(cudaMemsetAsync(ws.y0.p, 0, sizeof(double) * (size_t)g->n, s));
+        cudaEvent_t e0, e1;
+        DI_CHECK_CUDA(cudaEventCreate(&e0));
+        DI_CHECK_CUDA(cudaEventCreate(&e1));
+        DI_CHECK_CUDA(cudaEventRecord(e0, s));
+        if (!ws.pi_exec) build_pi_graph<T>(g, l);
+        DI_CHECK_CUDA(cudaGraphLaunch(ws.pi_exec, s));
+        DI_CHECK_CUDA(cudaEventRecord(e1, s));
+        from_device(X_out, ws.H.p, sizeof(double) * (size_t)g->n, s);
+        read_ctl(g, s);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        const SolveCtl &c = *ws.ctl_host;
+        if (info) {
+            memset(info, 0, sizeof(*info));
+            info->sweeps = c.sweeps;
+            info->pushed_edges = (int64_t)c.sweeps * g->L;
+            info->visited_nodes = (int64_t)c.sweeps * g->n;
+            info->residual_l1 = c.r;
+            info->ms = ms;
+            info->kernel_launches = (int64_t)c.body_runs * (g->n_heavy_in_chunks > 0 ? 2 : 1);
+        }
+        if (residual_out) *residual_out = c.r;
+        DI_REQUIRE(c.r <= tol, DI_ERR_NOT_CONVERGED, "PI not converged after %d iterations: %g > %g", c.sweeps, c.r,
+                   tol);
+    });
+}
+
+}  // namespace di
+
+extern "C" {
+
+di_status di_solve(di_graph *g, const double *B, double d, double tol, int32_t schedule, int32_t max_sweeps,
+                   double *X_out, double *residual_out, di_solve_info *info, void *stream) {
+    di_solve_opts o;
+    memset(&o, 0, sizeof(o));
+    o.schedule = schedule;
+    o.max_sweeps = max_sweeps;
+    return di::solve_single(g, B, d, tol, &o, X_out, residual_out, info, (cudaStream_t)stream);
+}
+
+di_status di_solve_ex(di_graph *g, const double *B, double d, double tol, const di_solve_opts *opts, double *X_out,
+                      double *residual_out, di_solve_info *info, void *stream) {
+    return di::solve_single(g, B, d, tol, opts, X_out, residual_out, info, (cudaStream_t)stream);
+}
+
+di_status di_power_iter(di_graph *g, const double *B, double d, double tol, int32_t max_iters, double *X_out,
+                        double *residual_out, di_solve_info *info, void *stream) {
+    return di::power_iter(g, B, d, tol, max_iters, X_out, residual_out, info, (cudaStream_t)stream);
+}
+
+}  // extern "C"

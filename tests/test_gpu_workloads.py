@@ -1,0 +1,73 @@
+"""Parity on the full-size synthetic workloads, in the launch configuration the benchmark times.
+
+  pa_n10k : N=10k preferential-attachment graph, FP64 fluid, tol 1e-10: DI-CYC, DI-SOP and PI
+            against the oracle's fixed point.
+  web_n1m : N=1M web-like graph, FP32 fluid + FP64 refinement, tol 1e-8: DI-SOP, DI-CYC and PI.
+  web_n10m: N=10M, ~141M links: bit-exact graph build; DI-SOP at d=0.85 against the oracle's
+            DI-SOP fixed point; d=0.95 certified by the oracle's exact residual of the GPU
+            history (||X - H||_1 <= ||B + P.H - H||_1 / (1 - d), a bound that holds at any size).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1204_6255_gb300 as di
+import workloads
+from gpu_util import assert_build_matches_oracle, lib, rel_l1
+
+pytestmark = pytest.mark.gpu
+TOL_X = 1e-6
+
+
+def _setup(name):
+    cfg = workloads.WORKLOADS[name]
+    n, src, dst = workloads.generate(cfg["spec"])
+    lib()
+    return cfg, n, src, dst, di.di_graph_create(n, src, dst), oracle.build(n, src, dst)
+
+
+def test_pa_n10k_fp64():
+    cfg, n, src, dst, g, og = _setup("pa_n10k")
+    d, tol = cfg["d"], cfg["tol"]
+    B = oracle.uniform_B(n, d)
+    ref, _, _, ok = oracle.di(og, B, d, 1e-16, oracle.SOP)
+    assert ok
+    for sched in (di.DI_CYC, di.DI_SOP):
+        X, info = di.di_solve_ex(g, B, d, tol, schedule=sched, fluid=di.DI_FLUID_F64)
+        assert rel_l1(X, ref) <= TOL_X and info["residual_l1"] <= tol
+    X, info = di.di_power_iter(g, B, d, tol)
+    assert rel_l1(X, ref) <= TOL_X
+
+
+def test_web_n1m_fp32_fluid():
+    cfg, n, src, dst, g, og = _setup("web_n1m")
+    assert_build_matches_oracle(g, og)
+    d, tol = cfg["d"], cfg["tol"]
+    B = oracle.uniform_B(n, d)
+    ref, _, oinfo, ok = oracle.di(og, B, d, 1e-13, oracle.SOP)
+    assert ok
+    for sched in (di.DI_SOP, di.DI_CYC):
+        X, info = di.di_solve_ex(g, B, d, tol, schedule=sched, fluid=di.DI_FLUID_F32)
+        assert info["residual_l1"] <= tol
+        assert rel_l1(X, ref) <= TOL_X
+    X, info = di.di_power_iter(g, B, d, tol)
+    assert rel_l1(X, ref) <= TOL_X
+
+
+def test_web_n10m_full_size():
+    cfg, n, src, dst, g, og = _setup("web_n10m")
+    assert_build_matches_oracle(g, og)
+    tol = cfg["tol"]
+    d = 0.85
+    B = oracle.uniform_B(n, d)
+    X, info = di.di_solve_ex(g, B, d, tol, schedule=di.DI_SOP, fluid=di.DI_FLUID_F32, max_sweeps=20000)
+    assert info["residual_l1"] <= tol
+    ref, _, _, ok = oracle.di(og, B, d, 1e-11, oracle.SOP)
+    assert ok and rel_l1(X, ref) <= TOL_X
+    # d = 0.95: certify with the oracle's exact residual of the GPU history
+    d = 0.95
+    B = oracle.uniform_B(n, d)
+    X, info = di.di_solve_ex(g, B, d, tol, schedule=di.DI_SOP, fluid=di.DI_FLUID_F32, max_sweeps=20000)
+    _, res = oracle.residual(og, B, d, X)
+    assert res <= 1.01 * tol
+    assert res / (1 - d) <= TOL_X * np.abs(X).sum()
