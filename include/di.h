@@ -103,6 +103,8 @@ typedef struct {
        (PI: push_* is the pull kernel, select_* the heavy-row pre-pass) */
     double select_ms, push_ms, reduce_ms, refine_ms;
     int32_t select_launches, push_launches, reduce_launches, refine_launches;
+    int32_t rhs_tile;        /* batched solves: columns per tile that were used */
+    int32_t reserved;
 } di_solve_info;
 
 /* Which internal array di_graph_export copies. */
@@ -179,6 +181,40 @@ di_status di_solve_ex(di_graph *g, const double *B, double d, double tol, const 
  */
 di_status di_power_iter(di_graph *g, const double *B, double d, double tol, int32_t max_iters,
                         double *X_out, double *residual_out, di_solve_info *info, void *stream);
+
+/*
+ * di_solve_batch — k independent D-iterations on one graph in one multi-RHS sweep loop: every
+ * column r solves X_r = P.X_r + B_r and stops at its own tolerance tol[r]. Each column keeps its
+ * own selection rule (Section 2.3; DI-SOP: |F_ir| > (r_r / L) * out_i); a node's out-links are
+ * walked once per sweep for all the columns that selected it.
+ *   B      double[k * n]: column r at B + r * n (host or device), >= 0 and finite.
+ *   tol    double[k] (host or device), each > 0.
+ *   opts   schedule, max_sweeps, refine (as di_solve_ex; fluid must be DI_FLUID_F32), rhs_tile
+ *          (columns per tile: 4, 8, 16 or 32; 0 = autotuned once per graph and cached).
+ *   X_out  double[k * n], same layout as B.   res_out (nullable) double[k]: final ||F_r||_1
+ *          (exact FP64 residual of H_r when refinement is on).
+ *   info   (nullable) aggregate report: sweeps summed over tiles, pushed_edges counted once per
+ *          node visit (a visit serves every selected column), rhs_tile = tile width used.
+ * The fluid is FP32, node-major within each tile; H is FP64.
+ * Errors as di_solve; DI_ERR_NOT_CONVERGED when any column missed its tolerance (X_out and
+ * res_out still hold every column's current state).
+ */
+di_status di_solve_batch(di_graph *g, int32_t k, const double *B, double d, const double *tol,
+                         const di_solve_opts *opts, double *X_out, double *res_out,
+                         di_solve_info *info, void *stream);
+
+/*
+ * di_ppr_batch — di_solve_batch with personalised right-hand sides given as seed sets
+ * (personalised PageRank): column r has B_r = (1 - d) / |S_r| on every seed of
+ * S_r = seeds[seed_offsets[r] .. seed_offsets[r+1]); a seed listed twice receives two shares.
+ *   seed_offsets int64[k+1], ascending, seed_offsets[0] = 0, no empty set; seeds int32 ids.
+ *   Both host or device.
+ * Errors as di_solve_batch; DI_ERR_OUT_OF_RANGE_ID for a seed outside [0, n),
+ * DI_ERR_INVALID_ARG for an empty set or bad offsets.
+ */
+di_status di_ppr_batch(di_graph *g, int32_t k, const int64_t *seed_offsets, const int32_t *seeds,
+                       double d, const double *tol, const di_solve_opts *opts, double *X_out,
+                       double *res_out, di_solve_info *info, void *stream);
 
 /* Thread-local message of the last failing call on this thread ("" when none). */
 const char *di_last_error(void);

@@ -19,7 +19,7 @@ __all__ = [
     "build", "load", "DiError", "Graph",
     "DI_CYC", "DI_SOP", "DI_FLUID_F32", "DI_FLUID_F64",
     "di_graph_create", "di_graph_destroy", "di_graph_stats_get", "di_graph_export",
-    "di_solve", "di_solve_ex", "di_power_iter", "di_last_error", "di_version",
+    "di_solve", "di_solve_ex", "di_power_iter", "di_solve_batch", "di_ppr_batch", "di_last_error", "di_version",
 ]
 
 DI_CYC, DI_SOP = 0, 1
@@ -60,7 +60,7 @@ class SolveInfo(ctypes.Structure):
                 ("select_ms", ctypes.c_double), ("push_ms", ctypes.c_double), ("reduce_ms", ctypes.c_double),
                 ("refine_ms", ctypes.c_double), ("select_launches", ctypes.c_int32),
                 ("push_launches", ctypes.c_int32), ("reduce_launches", ctypes.c_int32),
-                ("refine_launches", ctypes.c_int32)]
+                ("refine_launches", ctypes.c_int32), ("rhs_tile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -99,6 +99,11 @@ def load(path: str | None = None):
     lib.di_solve_ex.argtypes = [vp, vp, dbl, dbl, ctypes.POINTER(SolveOpts), vp, vp, ctypes.POINTER(SolveInfo), vp]
     lib.di_power_iter.restype = st
     lib.di_power_iter.argtypes = [vp, vp, dbl, dbl, i32, vp, vp, ctypes.POINTER(SolveInfo), vp]
+    lib.di_solve_batch.restype = st
+    lib.di_solve_batch.argtypes = [vp, i32, vp, dbl, vp, ctypes.POINTER(SolveOpts), vp, vp, ctypes.POINTER(SolveInfo), vp]
+    lib.di_ppr_batch.restype = st
+    lib.di_ppr_batch.argtypes = [vp, i32, vp, vp, dbl, vp, ctypes.POINTER(SolveOpts), vp, vp,
+                                 ctypes.POINTER(SolveInfo), vp]
     lib.di_last_error.restype = ctypes.c_char_p
     lib.di_last_error.argtypes = []
     lib.di_version.restype = ctypes.c_char_p
@@ -242,6 +247,43 @@ def di_power_iter(g: Graph, B, d: float, tol: float, max_iters: int = 0, X_out=N
     _check(load().di_power_iter(g.handle, _ptr(B, np.float64), float(d), float(tol), int(max_iters),
                                 _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)))
     return X, info.as_dict()
+
+
+def _tol_array(tol, k, like):
+    if np.isscalar(tol):
+        return np.full(k, float(tol), dtype=np.float64)
+    return tol
+
+
+def di_solve_batch(g: Graph, B, d: float, tol, schedule: int = DI_SOP, max_sweeps: int = 0, rhs_tile: int = 0,
+                   refine: int = 0, X_out=None, res_out=None):
+    """k right-hand sides at once; B has shape (k, n) (row r is the right-hand side of column r).
+    tol is a scalar or k values. Returns (X (k, n), residuals (k,), info)."""
+    k = int(B.shape[0])
+    tol = _tol_array(tol, k, B)
+    X = X_out if X_out is not None else (_like(B, k * g.n, np.float64).reshape(k, g.n))
+    res = res_out if res_out is not None else np.empty(k, dtype=np.float64)
+    o = SolveOpts(int(schedule), DI_FLUID_F32, int(max_sweeps), int(refine), 0, int(rhs_tile), 0, 0)
+    info = SolveInfo()
+    _check(load().di_solve_batch(g.handle, k, _ptr(B, np.float64), float(d), _ptr(tol, np.float64), ctypes.byref(o),
+                                 _ptr(X, np.float64), _ptr(res, np.float64), ctypes.byref(info), _stream(B, X)))
+    return X, res, info.as_dict()
+
+
+def di_ppr_batch(g: Graph, seed_offsets, seeds, d: float, tol, schedule: int = DI_SOP, max_sweeps: int = 0,
+                 rhs_tile: int = 0, refine: int = 0, X_out=None, res_out=None):
+    """Personalised PageRank for k seed sets (seed_offsets int64[k+1], seeds int32): column r has
+    B_r = (1-d)/|S_r| on its seeds. Returns (X (k, n), residuals (k,), info)."""
+    k = int(seed_offsets.shape[0]) - 1
+    tol = _tol_array(tol, k, seeds)
+    X = X_out if X_out is not None else (_like(seeds, k * g.n, np.float64).reshape(k, g.n))
+    res = res_out if res_out is not None else np.empty(k, dtype=np.float64)
+    o = SolveOpts(int(schedule), DI_FLUID_F32, int(max_sweeps), int(refine), 0, int(rhs_tile), 0, 0)
+    info = SolveInfo()
+    _check(load().di_ppr_batch(g.handle, k, _ptr(seed_offsets, np.int64), _ptr(seeds, np.int32), float(d),
+                               _ptr(tol, np.float64), ctypes.byref(o), _ptr(X, np.float64), _ptr(res, np.float64),
+                               ctypes.byref(info), _stream(seeds, X)))
+    return X, res, info.as_dict()
 
 
 def di_last_error() -> str:

@@ -1,0 +1,19 @@
+// Batched (multi-RHS) workspace of a graph (di_batch.cu).
+#pragma once
+
+#include "di_internal.cuh"
+
+namespace di {
+
+struct BatchWorkspace {
+    int T_alloc = 0;                 // widest tile the buffers hold
+    int tuned_T = 0;                 // autotuned tile width (0 = not tuned yet)
+    double probe_rate[4] = {0, 0, 0, 0};   // column-link updates per second of each width
+    DevBuf F, H, Bn, front_id, front_s, heavy_partial, partials, ctl, stage;
+    cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};   // per tile width
+    cudaStream_t capture_stream = nullptr;
+    void *ctl_host = nullptr;
+    ~BatchWorkspace();
+};
+
+}  // namespace di

@@ -620,7 +620,7 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
         g->heavy_in_rows.ensure(sizeof(int32_t) * (size_t)(tot[0] + 1));
         g->heavy_in_chunk_off.ensure(sizeof(int32_t) * (size_t)(tot[0] + 1));
         g->heavy_in_chunk_row.ensure(sizeof(int32_t) * (size_t)(tot[1] + 1));
-        g->heavy_in_partial.ensure(sizeof(double) * (size_t)(tot[1] + 1));
+        g->heavy_in_partial.ensure(sizeof(float) * 2 * (size_t)(tot[1] + 1));
         if (tot[0] > 0) {
             k_heavy_in_lists<<<grid_for(n, 256, dev), 256, 0, s>>>(
                 flag.as<uint32_t>(), fpos.as<uint32_t>(), cpos.as<uint32_t>(), n, g->heavy_in_rows.as<int32_t>(),

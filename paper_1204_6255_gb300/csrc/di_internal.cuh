@@ -139,7 +139,8 @@ constexpr int kReduceBlocks = 1024; // partial sums of the last-block-done reduc
 // Per-graph state for single-RHS solves and power iteration.
 struct Workspace {
     int fluid = -1;                 // di_fluid the buffers were sized for
-    DevBuf F, H, B, front_id, front_s, heavy_id, heavy_s, partials, ctl, y0, y1;
+    DevBuf F, H, B, front_id, front_s, front_beg, front_deg, heavy_id, heavy_s, partials, ctl, y0, y1;
+    DevBuf Bdf, cdf, Xdf;           // power iteration in double-float: B, d/out, X
     cudaGraphExec_t sweep_exec = nullptr;   // reduce -> WHILE{select, push, reduce}
     cudaGraphExec_t pi_exec = nullptr;      // pull -> WHILE{pull}
     cudaStream_t capture_stream = nullptr;
@@ -147,6 +148,24 @@ struct Workspace {
     void reset_graphs();
     ~Workspace();
 };
+
+// Makes the graph's device current for the lifetime of the guard.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            DI_CHECK_CUDA(cudaSetDevice(dev));
+        } else {
+            prev = -1;
+        }
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+struct BatchWorkspace;
+void destroy_batch_workspace(BatchWorkspace *);
 
 }  // namespace di
 
@@ -168,10 +187,12 @@ struct di_graph {
     di::DevBuf heavy_in_rows;      // int32[n_heavy_in], ascending
     di::DevBuf heavy_in_chunk_off; // int32[n_heavy_in + 1]
     di::DevBuf heavy_in_chunk_row; // int32[n_heavy_in_chunks]: heavy index of each chunk
-    di::DevBuf heavy_in_partial;   // double[n_heavy_in_chunks]
+    di::DevBuf heavy_in_partial;   // float2[n_heavy_in_chunks] (double-float partial sums)
     int64_t n_heavy_out = 0;       // nodes with out-degree > kPushHeavy
     std::mutex mu;                 // serialises use of the workspaces
     di::Workspace ws;
+    di::BatchWorkspace *bws = nullptr;   // batched solves (created on first use)
+    ~di_graph() { if (bws) di::destroy_batch_workspace(bws); }
 };
 
 namespace di {

@@ -63,14 +63,35 @@ __device__ __forceinline__ bool finish_sum(double s, double *partials, SolveCtl 
     return true;
 }
 
+// This thread's share of sum |F_i| (grid-stride). FP32 fluid is summed in FP32 runs of 16
+// entries that are then added in FP64 (FP64 throughput on this part is a small fraction of FP32).
+__device__ __forceinline__ double abs_sum(const float *F, int32_t n) {
+    double s = 0.0;
+    float run = 0.f;
+    int k = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        run += fabsf(__ldcg(F + i));
+        if (++k == 16) {
+            s += (double)run;
+            run = 0.f;
+            k = 0;
+        }
+    }
+    return s + (double)run;
+}
+__device__ __forceinline__ double abs_sum(const double *F, int32_t n) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += fabs(__ldcg(F + i));
+    return s;
+}
+
 // r = ||F||_1, stop test, and bookkeeping for the next selection.
 template <class T>
 __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl, cudaGraphConditionalHandle h,
                          int set_cond) {
     __shared__ double scratch[32];
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s += fabs((double)F[i]);
+    const double s = abs_sum(F, n);
     double tot;
     if (!finish_sum(s, partials, ctl, scratch, tot)) return;
     if (threadIdx.x == 0) {
@@ -90,69 +111,160 @@ __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl,
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// cache-policy helpers: F (the scatter target) should stay in L2 while everything else streams
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void red_keep(float *p, float v, uint64_t pol) {
+    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void red_keep(double *p, double v, uint64_t pol) {
+    asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ float ld_keep(const float *p, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_keep(const double *p, uint64_t pol) {
+    double v;
+    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_keep(float *p, float v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep(double *p, double v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+
+// Node part of a visit: transit (loop closed form) and the per-link share d * transit / out.
+// FP32 fluid: the arithmetic stays in FP32 (this part's FP64 rate is a small fraction of its
+// FP32 rate); the transit is widened to FP64 only to be added to H.
+__device__ __forceinline__ void visit_math(float f, int32_t o, bool lp, double d, float d_f, double &t, float &share) {
+    const float of = (float)o;
+    const float tf = lp ? f * of / (of - d_f) : f;
+    t = (double)tf;
+    share = o ? tf * d_f / of : 0.f;
+}
+__device__ __forceinline__ void visit_math(double f, int32_t o, bool lp, double d, float, double &t, double &share) {
+    t = lp ? f * (double)o / ((double)o - d) : f;
+    share = o ? t * d / (double)o : 0.0;
+}
+__device__ __forceinline__ bool selects(float f, int32_t o, bool cyc, double, float thr_f) {
+    return cyc ? (f != 0.f) : (fabsf(f) > thr_f * (float)o);
+}
+__device__ __forceinline__ bool selects(double f, int32_t o, bool cyc, double thr, float) {
+    return cyc ? (f != 0.0) : (fabs(f) > thr * (double)o);
+}
+
+// Nodes are visited in chunks of kSelChunk consecutive ids per block iteration; the frontier
+// entries of a chunk are compacted with one atomic per chunk, so the frontier is id-sorted
+// within each chunk (the push then walks neighbouring rows together). Every entry carries its
+// row start and degree, so the push needs no dependent row-pointer gather.
+constexpr int kSelItems = 8;
+constexpr int kSelChunk = 256 * kSelItems;
+
 template <class T>
-__global__ void __launch_bounds__(256) k_select(T *F, double *H, const int32_t *out_info, int32_t n, SolveCtl *ctl,
-                                                int32_t *front_id, T *front_s, int32_t *heavy_id, T *heavy_s) {
+__global__ void __launch_bounds__(256) k_select(T *F, double *H, const int32_t *out_info, const int64_t *rp_out,
+                                                int32_t n, SolveCtl *ctl, int32_t *front_id, T *front_s,
+                                                int64_t *front_beg, int32_t *front_deg, int32_t *heavy_id,
+                                                T *heavy_s) {
     __shared__ double scratch[32];
     __shared__ unsigned long long scratch_u[32];
+    __shared__ int wcount[kSelItems][8];
+    __shared__ int chunk_base;
     if (ctl->done) return;
     const double r = ctl->r, d = ctl->d;
     const bool cyc = ctl->schedule == DI_CYC || ctl->force_cyc;
     const double thr = ctl->L > 0.0 ? r / ctl->L : 0.0;
+    const float thr_f = (float)thr, d_f = (float)d;
+    const uint64_t keep = policy_evict_last();
     const unsigned lane = lane_id(), lt = lanemask_lt();
+    const int warp = threadIdx.x >> 5;
+    float e_run = 0.f;   // dangling mass of this thread, widened at the end
     double e_loc = 0.0;
     unsigned long long pushed = 0, visited = 0;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        bool light = false, heavy = false;
-        double share = 0.0;
-        if (i < n) {
-            const T f = F[i];
-            const int32_t info = out_info[i];
-            const int32_t o = info & 0x7fffffff;
-            const bool lp = info < 0;
-            const double af = fabs((double)f);
-            const bool sel = cyc ? (f != (T)0) : (af > thr * (double)o);
-            if (sel) {
-                F[i] = (T)0;
-                const double t = lp ? (double)f * (double)o / ((double)o - d) : (double)f;
-                H[i] += t;
-                visited++;
-                pushed += (unsigned long long)o;
-                if (o == 0) {
-                    e_loc += t;
-                } else {
-                    share = t * d / (double)o;
-                    if (o > kPushHeavy) heavy = true;
-                    else if (o - (lp ? 1 : 0) > 0) light = true;
+    for (int64_t base = (int64_t)blockIdx.x * kSelChunk; base < n; base += (int64_t)gridDim.x * kSelChunk) {
+        unsigned ballots[kSelItems];
+        T shares[kSelItems];
+        int32_t degs[kSelItems];
+#pragma unroll
+        for (int j = 0; j < kSelItems; j++) {
+            const int64_t i = base + j * 256 + threadIdx.x;
+            bool light = false, heavy = false;
+            T share = (T)0;
+            int32_t o = 0;
+            if (i < n) {
+                const T f = ld_keep(F + i, keep);
+                const int32_t info = __ldcs(out_info + i);
+                o = info & 0x7fffffff;
+                const bool lp = info < 0;
+                if (selects(f, o, cyc, thr, thr_f)) {
+                    st_keep(F + i, (T)0, keep);
+                    double t;
+                    visit_math(f, o, lp, d, d_f, t, share);
+                    __stcs(H + i, __ldcs(H + i) + t);
+                    visited++;
+                    pushed += (unsigned long long)o;
+                    if (o == 0) {
+                        if (sizeof(T) == 4) e_run += (float)t; else e_loc += t;
+                    } else if (o > kPushHeavy) {
+                        heavy = true;
+                    } else if (o - (lp ? 1 : 0) > 0) {
+                        light = true;
+                    }
+                }
+            }
+            shares[j] = share;
+            degs[j] = o;
+            ballots[j] = __ballot_sync(kFull, light);
+            if (lane == 0) wcount[j][warp] = __popc(ballots[j]);
+            // heavy nodes are rare: one atomic per warp that has any
+            const unsigned bh = __ballot_sync(kFull, heavy);
+            if (bh) {
+                const int leader = __ffs(bh) - 1;
+                int p0 = 0;
+                if ((int)lane == leader) p0 = atomicAdd(&ctl->heavy_count, __popc(bh));
+                p0 = __shfl_sync(kFull, p0, leader);
+                if (heavy) {
+                    const int p = p0 + __popc(bh & lt);
+                    heavy_id[p] = (int32_t)i;
+                    heavy_s[p] = share;
                 }
             }
         }
-        const unsigned bl = __ballot_sync(kFull, light);
-        if (bl) {
-            const int leader = __ffs(bl) - 1;
-            int p0 = 0;
-            if ((int)lane == leader) p0 = atomicAdd(&ctl->front_count, __popc(bl));
-            p0 = __shfl_sync(kFull, p0, leader);
-            if (light) {
-                const int p = p0 + __popc(bl & lt);
-                front_id[p] = (int32_t)i;
-                front_s[p] = (T)share;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int j = 0; j < kSelItems; j++)
+                for (int w = 0; w < 8; w++) {
+                    const int c = wcount[j][w];
+                    wcount[j][w] = run;
+                    run += c;
+                }
+            chunk_base = run ? atomicAdd(&ctl->front_count, run) : 0;
+        }
+        __syncthreads();
+        const int cb = chunk_base;
+#pragma unroll
+        for (int j = 0; j < kSelItems; j++) {
+            if (ballots[j] & (1u << lane)) {
+                const int p = cb + wcount[j][warp] + __popc(ballots[j] & lt);
+                const int64_t i = base + j * 256 + threadIdx.x;
+                __stcs(front_id + p, (int32_t)i);
+                __stcs(front_s + p, shares[j]);
+                __stcs(front_beg + p, (long long)__ldcs(rp_out + i));
+                __stcs(front_deg + p, degs[j]);
             }
         }
-        const unsigned bh = __ballot_sync(kFull, heavy);
-        if (bh) {
-            const int leader = __ffs(bh) - 1;
-            int p0 = 0;
-            if ((int)lane == leader) p0 = atomicAdd(&ctl->heavy_count, __popc(bh));
-            p0 = __shfl_sync(kFull, p0, leader);
-            if (heavy) {
-                const int p = p0 + __popc(bh & lt);
-                heavy_id[p] = (int32_t)i;
-                heavy_s[p] = (T)share;
-            }
-        }
+        __syncthreads();
     }
+    e_loc += (double)e_run;
     e_loc = block_sum(e_loc, scratch);
     pushed = block_sum(pushed, scratch_u);
     visited = block_sum(visited, scratch_u);
@@ -167,87 +279,150 @@ __global__ void __launch_bounds__(256) k_select(T *F, double *H, const int32_t *
     }
 }
 
+// Push, one warp per batch of 32 frontier entries (no block barriers): the warp scans the
+// entries' degrees, then each lane takes kPushVT contiguous links of the batch's concatenated
+// links per round, finds their owner once (binary search over the warp's 33 offsets in shared
+// memory) and keeps kPushVT independent index loads in flight before its atomic adds.
+constexpr int kPushVT = 8;
+
 template <class T>
 __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_id, const T *__restrict__ front_s,
+                                              const int64_t *__restrict__ front_beg,
+                                              const int32_t *__restrict__ front_deg,
                                               const int32_t *__restrict__ heavy_id, const T *__restrict__ heavy_s,
                                               const int64_t *__restrict__ rp_out, const int32_t *__restrict__ col_out,
                                               T *F, SolveCtl *ctl) {
+    __shared__ int s_off[8][33];
+    __shared__ int64_t s_beg[8][32];
+    __shared__ int32_t s_u[8][32];
+    __shared__ T s_s[8][32];
     if (ctl->done) return;
-    const int lane = (int)lane_id();
-    const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t pol = policy_evict_last();
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
 
-    // nodes with more than kPushHeavy links: their edges in chunks over all warps
+    // nodes with more than kPushHeavy links: their links in chunks over all warps
     const int hc = ctl->heavy_count;
     constexpr int kChunk = 1024;
     for (int h = 0; h < hc; h++) {
         const int32_t u = heavy_id[h];
-        const T s = heavy_s[h];
+        const T sh = heavy_s[h];
         const int64_t b = rp_out[u], e = rp_out[u + 1];
         const int64_t nch = (e - b + kChunk - 1) / kChunk;
         for (int64_t c = gwarp; c < nch; c += nwarps) {
             const int64_t cb = b + c * kChunk, ce = min(cb + kChunk, e);
             for (int64_t k = cb + lane; k < ce; k += 32) {
-                const int32_t j = col_out[k];
-                if (j != u) red_add(&F[j], s);
+                const int32_t j = __ldcs(col_out + k);
+                if (j != u) red_keep(&F[j], sh, pol);
             }
         }
     }
 
-    // light nodes: batches of 32 frontier entries; warps claim `grab` entries at a time
     const int count = ctl->front_count;
-    const int grab = (count >= (int)(nwarps * 32 * 8)) ? 128 : 32;
-    for (;;) {
-        int c0 = 0;
-        if (lane == 0) c0 = atomicAdd(&ctl->batch_next, grab);
-        c0 = __shfl_sync(kFull, c0, 0);
-        if (c0 >= count) break;
-        const int cend = min(c0 + grab, count);
-        for (int b0 = c0; b0 < cend; b0 += 32) {
-            const int idx = b0 + lane;
-            int32_t u = -1;
-            T s = (T)0;
-            int64_t beg = 0;
-            int deg = 0;
-            if (idx < cend) {
-                u = front_id[idx];
-                s = front_s[idx];
-                beg = rp_out[u];
-                deg = (int)(rp_out[u + 1] - beg);
+    for (int64_t b0 = gwarp * 32; b0 < count; b0 += nwarps * 32) {
+        const int64_t idx = b0 + lane;
+        int deg = 0;
+        if (idx < count) {
+            deg = __ldcs(front_deg + idx);
+            s_u[w][lane] = __ldcs(front_id + idx);
+            s_s[w][lane] = __ldcs(front_s + idx);
+            s_beg[w][lane] = (int64_t)__ldcs(front_beg + idx);
+        }
+        const int inc = warp_inclusive_scan(deg);
+        const int total = __shfl_sync(kFull, inc, 31);
+        s_off[w][lane] = inc - deg;
+        if (lane == 31) s_off[w][32] = total;
+        __syncwarp();
+        for (int e0 = lane * kPushVT; e0 < total; e0 += 32 * kPushVT) {
+            int lo = 0, hi = 31;   // last entry k with s_off[k] <= e0
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[w][mid] <= e0) lo = mid; else hi = mid - 1;
             }
-            const int inc = warp_inclusive_scan(deg);
-            const int off = inc - deg;
-            const int total = __shfl_sync(kFull, inc, 31);
-            for (int q0 = 0; q0 < total; q0 += 32) {
-                const int q = q0 + lane;
-                const int ow = warp_owner(off, q);
-                const int64_t ob = __shfl_sync(kFull, beg, ow);
-                const int oo = __shfl_sync(kFull, off, ow);
-                const int32_t ou = __shfl_sync(kFull, u, ow);
-                const T os = __shfl_sync(kFull, s, ow);
-                if (q < total) {
-                    const int32_t j = col_out[ob + (q - oo)];
-                    if (j != ou) red_add(&F[j], os);
+            int k = lo;
+            int next = s_off[w][k + 1];
+            int32_t j[kPushVT];
+            int own[kPushVT];
+#pragma unroll
+            for (int v = 0; v < kPushVT; v++) {
+                const int e = e0 + v;
+                own[v] = -1;
+                if (e < total) {
+                    while (next <= e) next = s_off[w][++k + 1];
+                    own[v] = k;
+                    j[v] = __ldcs(col_out + s_beg[w][k] + (e - s_off[w][k]));
                 }
             }
+#pragma unroll
+            for (int v = 0; v < kPushVT; v++)
+                if (own[v] >= 0 && j[v] != s_u[w][own[v]]) red_keep(&F[j[v]], s_s[w][own[v]], pol);
         }
+        __syncwarp();
     }
 }
 
-// y[j] = d * v[j] / out_j (0 for a dangling node)
-__global__ void k_scale(const double *v, const int32_t *out_info, int32_t n, double d, double *y) {
+// ------------------------------------------------------------------------------------------
+// double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32 numbers (about 44
+// significant bits). Sums use Knuth's error-free two-sum, products an FMA-based exact product
+// (Dekker's double-length arithmetic); both renormalise with a fast two-sum. The pull kernels
+// accumulate this way instead of in FP64, whose throughput on this part is a small fraction of
+// the FP32 rate.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    float e = (a.x - (s - bb)) + (b.x - bb);
+    e += a.y + b.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float hi = p + e;
+    return make_float2(hi, e - (hi - p));
+}
+__device__ __forceinline__ float2 df_from(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+__device__ __forceinline__ double df_to(float2 a) { return (double)a.x + (double)a.y; }
+
+// y[j] = d * v[j] / out_j (0 for a dangling node), as double-float (refinement: v = H)
+__global__ void k_scale(const double *v, const int32_t *out_info, int32_t n, double d, float2 *y) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t o = out_info[i] & 0x7fffffff;
-        y[i] = o ? d * v[i] / (double)o : 0.0;
+        y[i] = df_from(o ? d * v[i] / (double)o : 0.0);
     }
+}
+
+// Power-iteration set-up: c[j] = d / out_j (0 if dangling), B and X_0 = 0 as double-float, y_0 = 0.
+__global__ void k_pi_init(const double *B, const int32_t *out_info, int32_t n, double d, float2 *Bdf, float2 *c,
+                          float2 *X, float2 *y0) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = out_info[i] & 0x7fffffff;
+        c[i] = df_from(o ? d / (double)o : 0.0);
+        Bdf[i] = df_from(B[i]);
+        X[i] = make_float2(0.f, 0.f);
+        y0[i] = make_float2(0.f, 0.f);
+    }
+}
+
+__global__ void k_df_to_double(const float2 *X, int32_t n, double *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = df_to(X[i]);
 }
 
 // partial[c] = sum of y over the in-links of heavy-row chunk c
 __global__ void k_pull_heavy(const int64_t *rp_in, const int32_t *col_in, const int32_t *heavy_rows,
                              const int32_t *chunk_off, const int32_t *chunk_row, int32_t n_chunks,
-                             const double *y0, const double *y1, const SolveCtl *ctl, int alternate,
-                             double *partial) {
-    const double *y = (alternate && (ctl->sweeps & 1)) ? y1 : y0;
+                             const float2 *y0, const float2 *y1, const SolveCtl *ctl, int alternate,
+                             float2 *partial) {
+    const float2 *y = (alternate && (ctl->sweeps & 1)) ? y1 : y0;
     const int lane = (int)lane_id();
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += nwarps) {
@@ -255,35 +430,44 @@ __global__ void k_pull_heavy(const int64_t *rp_in, const int32_t *col_in, const 
         const int32_t row = heavy_rows[h];
         const int64_t b = rp_in[row] + (int64_t)(c - chunk_off[h]) * kPullChunk;
         const int64_t e = min(b + (int64_t)kPullChunk, rp_in[row + 1]);
-        double s = 0.0;
-        for (int64_t k = b + lane; k < e; k += 32) s += y[col_in[k]];
-        s = warp_sum(s);
+        float2 s = make_float2(0.f, 0.f);
+        for (int64_t k = b + lane; k < e; k += 32) s = df_add(s, y[__ldcs(col_in + k)]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float2 t;
+            t.x = __shfl_xor_sync(kFull, s.x, o);
+            t.y = __shfl_xor_sync(kFull, s.y, o);
+            s = df_add(s, t);
+        }
         if (lane == 0) partial[c] = s;
     }
 }
 
 enum { PULL_PI = 0, PULL_RESID = 1 };
 
-// Row sums acc_i = sum_{j in in(i)} y_j for 32 consecutive rows per warp, then the epilogue:
-//   PULL_PI:    X'_i = B_i + acc_i, delta_i = |X'_i - X_i|, X_i = X'_i, y'_i = d X'_i / out_i;
-//               sum delta -> ctl->r, iteration count and WHILE condition.
-//   PULL_RESID: F*_i = B_i + acc_i - H_i -> F_i (as T); sum |F*| -> ctl->r.
+// Row sums acc_i = sum_{j in in(i)} y_j (double-float) for 32 consecutive rows per warp, then:
+//   PULL_PI:    X'_i = B_i + acc_i, delta_i = |X'_i - X_i|, X_i = X'_i, y'_i = X'_i * c_i with
+//               c_i = d / out_i (all double-float); sum delta -> ctl->r, iteration count and the
+//               WHILE condition.
+//   PULL_RESID: F*_i = B_i + acc_i - H_i (FP64) -> F_i (as T); sum |F*| -> ctl->r.
 template <int MODE, class T>
 __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in, const int32_t *__restrict__ col_in,
-                                              const double *y0, double *y1, int32_t n, const int32_t *heavy_rows,
-                                              const int32_t *heavy_chunk_off, const double *heavy_partial,
-                                              int32_t n_heavy, const double *__restrict__ B, double *X, T *F,
-                                              const int32_t *__restrict__ out_info, double *partials, SolveCtl *ctl,
+                                              const float2 *y0, float2 *y1, int32_t n, const int32_t *heavy_rows,
+                                              const int32_t *heavy_chunk_off, const float2 *heavy_partial,
+                                              int32_t n_heavy, const double *__restrict__ B,
+                                              const float2 *__restrict__ Bdf, const float2 *__restrict__ cdf,
+                                              float2 *Xdf, const double *H, T *F, double *partials, SolveCtl *ctl,
                                               cudaGraphConditionalHandle hcond, int set_cond) {
-    __shared__ double acc_s[8][32];
+    __shared__ float2 acc_s[8][32];
     __shared__ double scratch[32];
     const int lane = (int)lane_id(), warp = threadIdx.x >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const double d = ctl->d;
     const bool odd = (MODE == PULL_PI) && (ctl->sweeps & 1);
-    const double *y_in = odd ? y1 : y0;
-    double *y_out = odd ? const_cast<double *>(y0) : y1;
+    const float2 *y_in = odd ? y1 : y0;
+    float2 *y_out = odd ? const_cast<float2 *>(y0) : y1;
     double sum = 0.0;
+    float run = 0.f;
+    int runs = 0;
     // every warp runs the same number of row groups so the block stays converged
     const int64_t groups = ((int64_t)n + 31) >> 5;
     const int64_t rounds = (groups + nwarps - 1) / nwarps;
@@ -300,7 +484,7 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
             heavy = dd > kPullHeavy;
             deg = heavy ? 0 : (int)dd;
         }
-        acc_s[warp][lane] = 0.0;
+        acc_s[warp][lane] = make_float2(0.f, 0.f);
         __syncwarp();
         const int inc = warp_inclusive_scan(deg);
         const int off = inc - deg;
@@ -311,20 +495,22 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
             const int64_t ob = __shfl_sync(kFull, beg, ow);
             const int oo = __shfl_sync(kFull, off, ow);
             const bool act = q < total;
-            double v = act ? y_in[col_in[ob + (q - oo)]] : 0.0;
+            float2 v = act ? y_in[__ldcs(col_in + ob + (q - oo))] : make_float2(0.f, 0.f);
             const int own = act ? ow : 32;
             // segmented inclusive scan; owners are non-decreasing across lanes
 #pragma unroll
             for (int s = 1; s < 32; s <<= 1) {
-                const double vv = __shfl_up_sync(kFull, v, s);
+                float2 vv;
+                vv.x = __shfl_up_sync(kFull, v.x, s);
+                vv.y = __shfl_up_sync(kFull, v.y, s);
                 const int o2 = __shfl_up_sync(kFull, own, s);
-                if (lane >= s && o2 == own) v += vv;
+                if (lane >= s && o2 == own) v = df_add(v, vv);
             }
             const int next_own = __shfl_down_sync(kFull, own, 1);
-            if (act && (lane == 31 || next_own != own)) acc_s[warp][own] += v;
+            if (act && (lane == 31 || next_own != own)) acc_s[warp][own] = df_add(acc_s[warp][own], v);
             __syncwarp();
         }
-        double a = acc_s[warp][lane];
+        float2 a = acc_s[warp][lane];
         __syncwarp();
         if (heavy) {
             int lo = 0, hi = n_heavy - 1;
@@ -332,23 +518,29 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
                 const int mid = (lo + hi) >> 1;
                 if (heavy_rows[mid] < row) lo = mid + 1; else hi = mid;
             }
-            a = 0.0;
-            for (int c = heavy_chunk_off[lo]; c < heavy_chunk_off[lo + 1]; c++) a += heavy_partial[c];
+            a = make_float2(0.f, 0.f);
+            for (int c = heavy_chunk_off[lo]; c < heavy_chunk_off[lo + 1]; c++) a = df_add(a, heavy_partial[c]);
         }
         if (valid) {
             if (MODE == PULL_PI) {
-                const double xn = B[row] + a;
-                sum += fabs(xn - X[row]);
-                X[row] = xn;
-                const int32_t o = out_info[row] & 0x7fffffff;
-                y_out[row] = o ? d * xn / (double)o : 0.0;
+                const float2 xn = df_add(Bdf[row], a);
+                const float2 dx = df_add(xn, df_neg(Xdf[row]));
+                run += fabsf(dx.x + dx.y);
+                Xdf[row] = xn;
+                y_out[row] = df_mul(xn, cdf[row]);
             } else {
-                const double fs = B[row] + a - X[row];
+                const double fs = B[row] + df_to(a) - H[row];
                 F[row] = (T)fs;
                 sum += fabs(fs);
             }
+            if (++runs == 16) {
+                sum += (double)run;
+                run = 0.f;
+                runs = 0;
+            }
         }
     }
+    sum += (double)run;
     double tot;
     if (!finish_sum(sum, partials, ctl, scratch, tot)) return;
     if (threadIdx.x == 0) {
@@ -380,17 +572,6 @@ void Workspace::reset_graphs() {
     sweep_exec = nullptr;
     pi_exec = nullptr;
 }
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) DI_CHECK_CUDA(cudaSetDevice(dev));
-        else prev = -1;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 struct Launch {
     int sel_blocks, red_blocks, push_blocks, pull_blocks, ew_blocks;
@@ -445,7 +626,7 @@ static Launch launch_shape(const di_graph *g) {
     l.pull_blocks = sms * (occ > 0 ? occ : 1);
     const int64_t n = g->n;
     auto cap = [&](int64_t want, int64_t lim) { return (int)(want < 1 ? 1 : (want < lim ? want : lim)); };
-    l.sel_blocks = cap((n + 255) / 256, (int64_t)sms * 8);
+    l.sel_blocks = cap((n + kSelChunk - 1) / kSelChunk, (int64_t)sms * 8);
     l.red_blocks = cap((n + 255) / 256, (int64_t)(kReduceBlocks < sms * 4 ? kReduceBlocks : sms * 4));
     l.ew_blocks = cap((n + 255) / 256, (int64_t)sms * 8);
     // a pull block never needs more row groups than exist
@@ -466,12 +647,17 @@ static void ensure_workspace(di_graph *g) {
     ws.B.ensure(sizeof(double) * n);
     ws.front_id.ensure(sizeof(int32_t) * n);
     ws.front_s.ensure(sizeof(T) * n);
+    ws.front_beg.ensure(sizeof(int64_t) * n);
+    ws.front_deg.ensure(sizeof(int32_t) * n);
     ws.heavy_id.ensure(sizeof(int32_t) * (size_t)(g->n_heavy_out + 1));
     ws.heavy_s.ensure(sizeof(T) * (size_t)(g->n_heavy_out + 1));
     ws.partials.ensure(sizeof(double) * kReduceBlocks);
     ws.ctl.ensure(sizeof(SolveCtl));
-    ws.y0.ensure(sizeof(double) * n);
-    ws.y1.ensure(sizeof(double) * n);
+    ws.y0.ensure(sizeof(float2) * n);
+    ws.y1.ensure(sizeof(float2) * n);
+    ws.Bdf.ensure(sizeof(float2) * n);
+    ws.cdf.ensure(sizeof(float2) * n);
+    ws.Xdf.ensure(sizeof(float2) * n);
     if (!ws.capture_stream) DI_CHECK_CUDA(cudaStreamCreateWithFlags(&ws.capture_stream, cudaStreamNonBlocking));
     if (!ws.ctl_host) DI_CHECK_CUDA(cudaMallocHost(&ws.ctl_host, sizeof(SolveCtl)));
     ws.fluid = fl;
@@ -485,12 +671,15 @@ static void launch_sweep_body(di_graph *g, const Launch &l, cudaStream_t s, cuda
     KernelClock none(false, s);
     KernelClock &c = kc ? *kc : none;
     c.run(KC_SELECT, 1, [&] {
-        k_select<T><<<l.sel_blocks, 256, 0, s>>>(ws.F.as<T>(), ws.H.as<double>(), g->out_info.as<int32_t>(), g->n, ctl,
-                                                  ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
-                                                  ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>());
+        k_select<T><<<l.sel_blocks, 256, 0, s>>>(ws.F.as<T>(), ws.H.as<double>(), g->out_info.as<int32_t>(),
+                                                  g->rp_out.as<int64_t>(), g->n, ctl, ws.front_id.as<int32_t>(),
+                                                  ws.front_s.as<T>(), ws.front_beg.as<int64_t>(),
+                                                  ws.front_deg.as<int32_t>(), ws.heavy_id.as<int32_t>(),
+                                                  ws.heavy_s.as<T>());
     });
     c.run(KC_PUSH, 1, [&] {
         k_push<T><<<l.push_blocks, 256, 0, s>>>(ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
+                                                ws.front_beg.as<int64_t>(), ws.front_deg.as<int32_t>(),
                                                 ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(), g->rp_out.as<int64_t>(),
                                                 g->col_out.as<int32_t>(), ws.F.as<T>(), ctl);
     });
@@ -533,14 +722,14 @@ static void launch_pi_body(di_graph *g, const Launch &l, cudaStream_t s, cudaGra
         k_pull_heavy<<<blocks, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(),
                                             g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(),
                                             g->heavy_in_chunk_row.as<int32_t>(), g->n_heavy_in_chunks,
-                                            ws.y0.as<double>(), ws.y1.as<double>(), ctl, 1,
-                                            g->heavy_in_partial.as<double>());
+                                            ws.y0.as<float2>(), ws.y1.as<float2>(), ctl, 1,
+                                            g->heavy_in_partial.as<float2>());
     }
     k_pull<PULL_PI, T><<<l.pull_blocks, 256, 0, s>>>(
-        g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<double>(), ws.y1.as<double>(), g->n,
-        g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<double>(),
-        g->n_heavy_in, ws.B.as<double>(), ws.H.as<double>(), (T *)nullptr, g->out_info.as<int32_t>(),
-        ws.partials.as<double>(), ctl, h, set_cond);
+        g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<float2>(), ws.y1.as<float2>(), g->n,
+        g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<float2>(),
+        g->n_heavy_in, ws.B.as<double>(), ws.Bdf.as<float2>(), ws.cdf.as<float2>(), ws.Xdf.as<float2>(),
+        ws.H.as<double>(), (T *)nullptr, ws.partials.as<double>(), ctl, h, set_cond);
 }
 
 template <class T>
@@ -566,27 +755,27 @@ static void build_pi_graph(di_graph *g, const Launch &l) {
     DI_CHECK_CUDA(cudaGraphDestroy(graph));
 }
 
-// F <- B + P.H - H (as T), ctl->r <- ||F*||_1 (exact FP64 residual of the history H).
-// Launches 2 or 3 kernels.
+// F <- B + P.H - H (as T), ctl->r <- ||F*||_1 (exact residual of the history H: FP64 H and
+// B, double-float link sums). Launches 2 or 3 kernels.
 template <class T>
 static void launch_refine(di_graph *g, const Launch &l, double d, cudaStream_t s) {
     Workspace &ws = g->ws;
     SolveCtl *ctl = ws.ctl.as<SolveCtl>();
-    k_scale<<<l.ew_blocks, 256, 0, s>>>(ws.H.as<double>(), g->out_info.as<int32_t>(), g->n, d, ws.y0.as<double>());
+    k_scale<<<l.ew_blocks, 256, 0, s>>>(ws.H.as<double>(), g->out_info.as<int32_t>(), g->n, d, ws.y0.as<float2>());
     if (g->n_heavy_in_chunks > 0) {
         int blocks = (int)((g->n_heavy_in_chunks + 7) / 8);
         if (blocks > g->dev.sms * 8) blocks = g->dev.sms * 8;
         k_pull_heavy<<<blocks, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(),
                                             g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(),
                                             g->heavy_in_chunk_row.as<int32_t>(), g->n_heavy_in_chunks,
-                                            ws.y0.as<double>(), ws.y1.as<double>(), ctl, 0,
-                                            g->heavy_in_partial.as<double>());
+                                            ws.y0.as<float2>(), ws.y1.as<float2>(), ctl, 0,
+                                            g->heavy_in_partial.as<float2>());
     }
     k_pull<PULL_RESID, T><<<l.pull_blocks, 256, 0, s>>>(
-        g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<double>(), ws.y1.as<double>(), g->n,
-        g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<double>(),
-        g->n_heavy_in, ws.B.as<double>(), ws.H.as<double>(), ws.F.as<T>(), g->out_info.as<int32_t>(),
-        ws.partials.as<double>(), ctl, cudaGraphConditionalHandle(0), 0);
+        g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<float2>(), ws.y1.as<float2>(), g->n,
+        g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<float2>(),
+        g->n_heavy_in, ws.B.as<double>(), ws.Bdf.as<float2>(), ws.cdf.as<float2>(), ws.Xdf.as<float2>(),
+        ws.H.as<double>(), ws.F.as<T>(), ws.partials.as<double>(), ctl, cudaGraphConditionalHandle(0), 0);
     DI_CHECK_CUDA(cudaGetLastError());
 }
 
@@ -660,6 +849,9 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
             read_ctl(g, s);
             rounds++;
             if (ws.ctl_host->status || ws.ctl_host->r <= tol || ws.ctl_host->sweeps >= max_sweeps || rounds >= 4) break;
+            // continuation sweeps aim at half the tolerance, so the next exact residual lands below it
+            const double half = 0.5 * tol;
+            DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->tol, &half, sizeof(double), cudaMemcpyHostToDevice, s));
             run_sweeps();
         }
         DI_CHECK_CUDA(cudaEventRecord(e1, s));
@@ -739,15 +931,18 @@ di_status power_iter(di_graph *g, const double *B, double d, double tol, int32_t
         const Launch l = launch_shape<T>(g);
         to_device(ws.B.p, B, sizeof(double) * (size_t)g->n, s);
         write_ctl(g, d, tol, DI_CYC, mi, s);
-        // X_0 = 0 (kept in H), y_0 = 0
-        DI_CHECK_CUDA(cudaMemsetAsync(ws.H.p, 0, sizeof(double) * (size_t)g->n, s));
-        DI_CHECK_CUDA(cudaMemsetAsync(ws.y0.p, 0, sizeof(double) * (size_t)g->n, s));
         cudaEvent_t e0, e1;
         DI_CHECK_CUDA(cudaEventCreate(&e0));
         DI_CHECK_CUDA(cudaEventCreate(&e1));
         DI_CHECK_CUDA(cudaEventRecord(e0, s));
+        // c = d / out, B and X_0 = 0 in double-float, y_0 = 0
+        k_pi_init<<<l.ew_blocks, 256, 0, s>>>(ws.B.as<double>(), g->out_info.as<int32_t>(), g->n, d,
+                                              ws.Bdf.as<float2>(), ws.cdf.as<float2>(), ws.Xdf.as<float2>(),
+                                              ws.y0.as<float2>());
         if (!ws.pi_exec) build_pi_graph<T>(g, l);
         DI_CHECK_CUDA(cudaGraphLaunch(ws.pi_exec, s));
+        k_df_to_double<<<l.ew_blocks, 256, 0, s>>>(ws.Xdf.as<float2>(), g->n, ws.H.as<double>());
+        DI_CHECK_CUDA(cudaGetLastError());
         DI_CHECK_CUDA(cudaEventRecord(e1, s));
         from_device(X_out, ws.H.p, sizeof(double) * (size_t)g->n, s);
         read_ctl(g, s);
@@ -763,7 +958,7 @@ di_status power_iter(di_graph *g, const double *B, double d, double tol, int32_t
             info->visited_nodes = (int64_t)c.sweeps * g->n;
             info->residual_l1 = c.r;
             info->ms = ms;
-            info->kernel_launches = (int64_t)c.body_runs * (g->n_heavy_in_chunks > 0 ? 2 : 1);
+            info->kernel_launches = 2 + (int64_t)c.body_runs * (g->n_heavy_in_chunks > 0 ? 2 : 1);
         }
         if (residual_out) *residual_out = c.r;
         DI_REQUIRE(c.r <= tol, DI_ERR_NOT_CONVERGED, "PI not converged after %d iterations: %g > %g", c.sweeps, c.r,
