@@ -34,10 +34,14 @@ ARRAYS = {  # di_array id -> (numpy dtype, length kind)
 
 
 class DiError(RuntimeError):
-    def __init__(self, status: int, message: str):
+    """A non-zero di_status. `info` holds the call's report when it has one (a solve that hit its
+    sweep cap still reports its state, and its outputs hold the current history)."""
+
+    def __init__(self, status: int, message: str, info: dict | None = None):
         super().__init__(f"{STATUS.get(status, status)}: {message}")
         self.status = status
         self.message = message
+        self.info = info
 
 
 class GraphStats(ctypes.Structure):
@@ -142,9 +146,9 @@ def _stream(*arrays):
     return None
 
 
-def _check(status: int):
+def _check(status: int, info=None):
     if status != 0:
-        raise DiError(status, load().di_last_error().decode())
+        raise DiError(status, load().di_last_error().decode(), info.as_dict() if info is not None else None)
 
 
 def _like(x, n: int, dtype):
@@ -223,7 +227,7 @@ def di_solve(g: Graph, B, d: float, tol: float, schedule: int = DI_SOP, max_swee
     info = SolveInfo()
     res = ctypes.c_double()
     _check(load().di_solve(g.handle, _ptr(B, np.float64), float(d), float(tol), int(schedule), int(max_sweeps),
-                           _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)))
+                           _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)), info)
     return X, info.as_dict()
 
 
@@ -235,7 +239,7 @@ def di_solve_ex(g: Graph, B, d: float, tol: float, schedule: int = DI_SOP, fluid
     info = SolveInfo()
     res = ctypes.c_double()
     _check(load().di_solve_ex(g.handle, _ptr(B, np.float64), float(d), float(tol), ctypes.byref(o),
-                              _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)))
+                              _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)), info)
     return X, info.as_dict()
 
 
@@ -245,7 +249,7 @@ def di_power_iter(g: Graph, B, d: float, tol: float, max_iters: int = 0, X_out=N
     info = SolveInfo()
     res = ctypes.c_double()
     _check(load().di_power_iter(g.handle, _ptr(B, np.float64), float(d), float(tol), int(max_iters),
-                                _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)))
+                                _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)), info)
     return X, info.as_dict()
 
 
@@ -266,7 +270,8 @@ def di_solve_batch(g: Graph, B, d: float, tol, schedule: int = DI_SOP, max_sweep
     o = SolveOpts(int(schedule), DI_FLUID_F32, int(max_sweeps), int(refine), 0, int(rhs_tile), 0, 0)
     info = SolveInfo()
     _check(load().di_solve_batch(g.handle, k, _ptr(B, np.float64), float(d), _ptr(tol, np.float64), ctypes.byref(o),
-                                 _ptr(X, np.float64), _ptr(res, np.float64), ctypes.byref(info), _stream(B, X)))
+                                 _ptr(X, np.float64), _ptr(res, np.float64), ctypes.byref(info), _stream(B, X)),
+           info)
     return X, res, info.as_dict()
 
 
@@ -282,7 +287,7 @@ def di_ppr_batch(g: Graph, seed_offsets, seeds, d: float, tol, schedule: int = D
     info = SolveInfo()
     _check(load().di_ppr_batch(g.handle, k, _ptr(seed_offsets, np.int64), _ptr(seeds, np.int32), float(d),
                                _ptr(tol, np.float64), ctypes.byref(o), _ptr(X, np.float64), _ptr(res, np.float64),
-                               ctypes.byref(info), _stream(seeds, X)))
+                               ctypes.byref(info), _stream(seeds, X)), info)
     return X, res, info.as_dict()
 
 

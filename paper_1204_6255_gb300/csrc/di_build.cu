@@ -440,6 +440,32 @@ __global__ void k_count_heavy_out(const int32_t *out_deg, int32_t n, unsigned lo
     if (lane_id() == 0 && c) atomicAdd(cnt, c);
 }
 
+// Hub table: the nodes of highest in-degree, by open hashing into kHubSlots slots; a slot keeps
+// the candidate with the larger in-degree (packed in-degree << 32 | id, atomicMax).
+__global__ void k_indeg_hist(const int32_t *in_deg, int32_t n, unsigned long long *hist) {
+    __shared__ unsigned int h[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = in_deg[v];
+        if (d > 0) atomicAdd(&h[31 - __clz(d)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], (unsigned long long)h[threadIdx.x]);
+}
+
+__global__ void k_hub_insert(const int32_t *in_deg, int32_t n, int32_t min_deg, unsigned long long *slots) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = in_deg[v];
+        if (d >= min_deg) atomicMax(&slots[hub_slot((int32_t)v)], ((unsigned long long)(uint32_t)d << 32) | (uint32_t)v);
+    }
+}
+
+__global__ void k_hub_finalize(const unsigned long long *slots, int32_t *ids) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kHubSlots) ids[i] = slots[i] ? (int32_t)(uint32_t)(slots[i] & 0xffffffffu) : -1;
+}
+
 static int ceil_log2(int64_t x) {
     int b = 0;
     while ((int64_t(1) << b) < x) b++;
@@ -560,6 +586,30 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
     unsigned long long *heavy_out_cnt = reinterpret_cast<unsigned long long *>(misc.as<char>() + 192);
     k_count_heavy_out<<<grid_for(n, 256, dev), 256, 0, s>>>(g->out_deg.as<int32_t>(), n, heavy_out_cnt);
     DI_CHECK_CUDA(cudaGetLastError());
+
+    // hub table (highest in-degree nodes) for the push kernels' shared-memory hub cache
+    {
+        DevBuf hist, slots;
+        hist.ensure(sizeof(unsigned long long) * 32);
+        DI_CHECK_CUDA(cudaMemsetAsync(hist.p, 0, sizeof(unsigned long long) * 32, s));
+        k_indeg_hist<<<grid_for(n, 256, dev), 256, 0, s>>>(g->in_deg.as<int32_t>(), n, hist.as<unsigned long long>());
+        unsigned long long hh[32];
+        DI_CHECK_CUDA(cudaMemcpyAsync(hh, hist.p, sizeof(hh), cudaMemcpyDeviceToHost, s));
+        DI_CHECK_CUDA(cudaStreamSynchronize(s));
+        // smallest power-of-two in-degree bound that leaves at most 2 * kHubSlots candidates
+        int b = 31;
+        unsigned long long above = 0;
+        while (b > 6 && above + hh[b - 1] <= 2ull * kHubSlots) above += hh[--b];
+        const int32_t min_deg = (int32_t)1 << b;
+        slots.ensure(sizeof(unsigned long long) * kHubSlots);
+        DI_CHECK_CUDA(cudaMemsetAsync(slots.p, 0, sizeof(unsigned long long) * kHubSlots, s));
+        k_hub_insert<<<grid_for(n, 256, dev), 256, 0, s>>>(g->in_deg.as<int32_t>(), n, min_deg,
+                                                         slots.as<unsigned long long>());
+        g->hub_ids.ensure(sizeof(int32_t) * kHubSlots);
+        k_hub_finalize<<<(kHubSlots + 255) / 256, 256, 0, s>>>(slots.as<unsigned long long>(), g->hub_ids.as<int32_t>());
+        DI_CHECK_CUDA(cudaGetLastError());
+        DI_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
 
     // E by peeling
     g->e_mask.ensure((size_t)n);

@@ -127,6 +127,8 @@ struct SolveCtl {
     int32_t status;           // 0 ok; 1 bad right-hand side
     uint32_t ticket;          // last-block-done counter of the reductions
     int32_t body_runs;        // executions of the WHILE body (kernel-launch accounting)
+    int32_t chunk_count;      // frontier segments (one per select chunk with entries)
+    int32_t chunk_next;       // dynamic work counter over the segments
     unsigned long long front_total;  // frontier entries over all sweeps
 };
 
@@ -135,11 +137,12 @@ constexpr int kPushHeavy = 4096;    // out-degree above which a node's edges are
 constexpr int kPullHeavy = 8192;    // in-degree above which a row's edges are split over warps
 constexpr int kPullChunk = 4096;    // edges per heavy-row chunk of the pull
 constexpr int kReduceBlocks = 1024; // partial sums of the last-block-done reductions
+constexpr int kHubSlots = 2048;     // shared-memory hub cache of the push kernels
 
 // Per-graph state for single-RHS solves and power iteration.
 struct Workspace {
     int fluid = -1;                 // di_fluid the buffers were sized for
-    DevBuf F, H, B, front_id, front_s, front_beg, front_deg, heavy_id, heavy_s, partials, ctl, y0, y1;
+    DevBuf F, H, B, front_id, front_s, front_beg, front_deg, heavy_id, heavy_s, partials, ctl, y0, y1, chunks;
     DevBuf Bdf, cdf, Xdf;           // power iteration in double-float: B, d/out, X
     cudaGraphExec_t sweep_exec = nullptr;   // reduce -> WHILE{select, push, reduce}
     cudaGraphExec_t pi_exec = nullptr;      // pull -> WHILE{pull}
@@ -189,6 +192,7 @@ struct di_graph {
     di::DevBuf heavy_in_chunk_row; // int32[n_heavy_in_chunks]: heavy index of each chunk
     di::DevBuf heavy_in_partial;   // float2[n_heavy_in_chunks] (double-float partial sums)
     int64_t n_heavy_out = 0;       // nodes with out-degree > kPushHeavy
+    di::DevBuf hub_ids;            // int32[kHubSlots]: hub node per hash slot, -1 when empty
     std::mutex mu;                 // serialises use of the workspaces
     di::Workspace ws;
     di::BatchWorkspace *bws = nullptr;   // batched solves (created on first use)
@@ -249,6 +253,9 @@ __device__ __forceinline__ T block_sum(T v, T *scratch) {
     for (int w = 0; w < nw; w++) t += scratch[w];
     return t;
 }
+
+// Hash slot of a node in the hub table.
+__device__ __forceinline__ int hub_slot(int32_t v) { return (int)(((uint32_t)v * 0x9E3779B1u) >> 21); }
 
 // Largest lane k with off_k <= q, for lane offsets that are non-decreasing across the warp.
 // Every lane of the warp must call it.

@@ -66,18 +66,29 @@ __device__ __forceinline__ bool finish_sum(double s, double *partials, SolveCtl 
 // This thread's share of sum |F_i| (grid-stride). FP32 fluid is summed in FP32 runs of 16
 // entries that are then added in FP64 (FP64 throughput on this part is a small fraction of FP32).
 __device__ __forceinline__ double abs_sum(const float *F, int32_t n) {
+    // four float4 loads in flight per thread and step; the 16-entry FP32 run is then widened
+    const int64_t n4 = n >> 2;
+    const float4 *F4 = reinterpret_cast<const float4 *>(F);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double s = 0.0;
-    float run = 0.f;
-    int k = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        run += fabsf(__ldcg(F + i));
-        if (++k == 16) {
-            s += (double)run;
-            run = 0.f;
-            k = 0;
-        }
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; q + 3 * stride < n4; q += 4 * stride) {
+        float4 a = __ldcg(F4 + q), b = __ldcg(F4 + q + stride), c = __ldcg(F4 + q + 2 * stride),
+               d = __ldcg(F4 + q + 3 * stride);
+        const float run = ((fabsf(a.x) + fabsf(a.y)) + (fabsf(a.z) + fabsf(a.w))) +
+                          ((fabsf(b.x) + fabsf(b.y)) + (fabsf(b.z) + fabsf(b.w))) +
+                          ((fabsf(c.x) + fabsf(c.y)) + (fabsf(c.z) + fabsf(c.w))) +
+                          ((fabsf(d.x) + fabsf(d.y)) + (fabsf(d.z) + fabsf(d.w)));
+        s += (double)run;
     }
-    return s + (double)run;
+    for (; q < n4; q += stride) {
+        const float4 a = __ldcg(F4 + q);
+        s += (double)((fabsf(a.x) + fabsf(a.y)) + (fabsf(a.z) + fabsf(a.w)));
+    }
+    // tail entries n4*4 .. n-1
+    const int64_t t = (n4 << 2) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) s += (double)fabsf(__ldcg(F + t));
+    return s;
 }
 __device__ __forceinline__ double abs_sum(const double *F, int32_t n) {
     double s = 0.0;
@@ -104,6 +115,8 @@ __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl,
         ctl->front_count = 0;
         ctl->heavy_count = 0;
         ctl->batch_next = 0;
+        ctl->chunk_count = 0;
+        ctl->chunk_next = 0;
         if (set_cond) ctl->body_runs++;
         bool cont = ctl->status == 0 && tot > ctl->tol && ctl->sweeps < ctl->max_sweeps;
         ctl->done = cont ? 0 : 1;
@@ -118,6 +131,21 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
     uint64_t pol;
     asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     return pol;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t *p, uint64_t pol) {
+    int32_t v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void red_keep_v4(float *p, float4 v, uint64_t pol) {
+    asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(pol)
+                 : "memory");
 }
 __device__ __forceinline__ void red_keep(float *p, float v, uint64_t pol) {
     asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
@@ -173,7 +201,7 @@ template <class T>
 __global__ void __launch_bounds__(256) k_select(T *F, double *H, const int32_t *out_info, const int64_t *rp_out,
                                                 int32_t n, SolveCtl *ctl, int32_t *front_id, T *front_s,
                                                 int64_t *front_beg, int32_t *front_deg, int32_t *heavy_id,
-                                                T *heavy_s) {
+                                                T *heavy_s, int4 *chunks) {
     __shared__ double scratch[32];
     __shared__ unsigned long long scratch_u[32];
     __shared__ int wcount[kSelItems][8];
@@ -248,6 +276,7 @@ __global__ void __launch_bounds__(256) k_select(T *F, double *H, const int32_t *
                     run += c;
                 }
             chunk_base = run ? atomicAdd(&ctl->front_count, run) : 0;
+            if (run) chunks[atomicAdd(&ctl->chunk_count, 1)] = make_int4((int)base, chunk_base, run, 0);
         }
         __syncthreads();
         const int cb = chunk_base;
@@ -360,6 +389,157 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
         }
         __syncwarp();
     }
+}
+
+// Push with a shared-memory window (FP32 fluid). The select emits the frontier as id-sorted
+// segments of kSelChunk consecutive source nodes; a block takes one segment at a time and adds
+// every link whose target lies within kHalo ids of the segment (host locality: most web links
+// stay near their source) into a window of kWin floats in shared memory, sending only the other
+// links straight to F. The window then goes to F with one four-float atomic per non-zero group,
+// so a dense segment issues a fraction of the global atomics of a link-by-link push.
+constexpr int kHalo = 1024;
+constexpr int kWin = kSelChunk + 2 * kHalo;     // 4096 floats, 16 KB
+constexpr int kWinMinEntries = 24;              // sparser segments push link by link
+
+__global__ void __launch_bounds__(256, 4) k_push_win(const int32_t *__restrict__ front_id, const float *__restrict__ front_s,
+                                                  const int64_t *__restrict__ front_beg,
+                                                  const int32_t *__restrict__ front_deg,
+                                                  const int32_t *__restrict__ heavy_id, const float *__restrict__ heavy_s,
+                                                  const int64_t *__restrict__ rp_out,
+                                                  const int32_t *__restrict__ col_out, const int4 *__restrict__ chunks,
+                                                  const int32_t *__restrict__ hub_ids, float *F, SolveCtl *ctl) {
+    __shared__ __align__(16) float s_win[kWin];
+    __shared__ int32_t s_hub[kHubSlots];     // hub node of each slot (-1: none)
+    __shared__ float s_hacc[kHubSlots];      // this block's pending additions to the hubs
+    __shared__ int s_off[8][33];
+    __shared__ int64_t s_beg[8][32];
+    __shared__ int32_t s_u[8][32];
+    __shared__ float s_s[8][32];
+    __shared__ int s_chunk, s_batch;
+    if (ctl->done) return;
+    const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int q = tid; q < kHubSlots; q += 256) {
+        s_hub[q] = hub_ids[q];
+        s_hacc[q] = 0.f;
+    }
+    __syncthreads();
+    // a link to a far target: hubs (high in-degree nodes) collect in shared memory, the rest
+    // goes to F directly
+    auto far_add = [&](int32_t j, float v) {
+        const int slot = hub_slot(j);
+        if (s_hub[slot] == j) atomicAdd(&s_hacc[slot], v);
+        else red_keep(&F[j], v, keep);
+    };
+
+    // nodes with more than kPushHeavy links: their links in chunks over all warps
+    const int hc = ctl->heavy_count;
+    constexpr int kChunk = 1024;
+    for (int h = 0; h < hc; h++) {
+        const int32_t u = heavy_id[h];
+        const float sh = heavy_s[h];
+        const int64_t b = rp_out[u], e = rp_out[u + 1];
+        const int64_t nch = (e - b + kChunk - 1) / kChunk;
+        for (int64_t c = gwarp; c < nch; c += nwarps) {
+            const int64_t cb = b + c * kChunk, ce = min(cb + kChunk, e);
+            for (int64_t k = cb + lane; k < ce; k += 32) {
+                const int32_t j = ld_stream(col_out + k, stream);
+                if (j != u) far_add(j, sh);
+            }
+        }
+    }
+
+    const int nchunks = ctl->chunk_count;
+    for (;;) {
+        if (tid == 0) {
+            s_chunk = atomicAdd(&ctl->chunk_next, 1);
+            s_batch = 0;
+        }
+        __syncthreads();
+        const int ci = s_chunk;
+        if (ci >= nchunks) break;
+        const int4 ch = chunks[ci];
+        const int cstart = ch.y, clen = ch.z;
+        const bool use_win = clen >= kWinMinEntries;
+        const int lo = max(0, ch.x - kHalo) & ~3;
+        if (use_win) {
+            for (int q = tid; q < kWin / 4; q += 256) reinterpret_cast<float4 *>(s_win)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncthreads();
+        }
+        for (;;) {
+            // warps claim 32-entry batches of the segment
+            int b0 = 0;
+            if (lane == 0) b0 = atomicAdd(&s_batch, 32);
+            b0 = __shfl_sync(kFull, b0, 0);
+            if (b0 >= clen) break;
+            const int idx = cstart + b0 + lane;
+            int deg = 0;
+            if (b0 + lane < clen) {
+                deg = __ldcs(front_deg + idx);
+                s_u[w][lane] = __ldcs(front_id + idx);
+                s_s[w][lane] = __ldcs(front_s + idx);
+                s_beg[w][lane] = (int64_t)__ldcs(front_beg + idx);
+            }
+            const int inc = warp_inclusive_scan(deg);
+            const int total = __shfl_sync(kFull, inc, 31);
+            s_off[w][lane] = inc - deg;
+            if (lane == 31) s_off[w][32] = total;
+            __syncwarp();
+            for (int e0 = lane * kPushVT; e0 < total; e0 += 32 * kPushVT) {
+                int k = 0;   // last entry with s_off[k] <= e0
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (s_off[w][k + step] <= e0) k += step;
+                // the owner's row in registers; every entry has at least one link, so moving
+                // to the next link crosses at most one entry boundary
+                int off_k = s_off[w][k], next = s_off[w][k + 1];
+                int64_t row = s_beg[w][k] - off_k;
+                int32_t u = s_u[w][k];
+                float sv = s_s[w][k];
+                int32_t j[kPushVT], uu[kPushVT];
+                float ss[kPushVT];
+#pragma unroll
+                for (int v = 0; v < kPushVT; v++) {
+                    const int e = e0 + v;
+                    j[v] = -1;
+                    if (e < total) {
+                        if (e >= next) {
+                            ++k;
+                            off_k = next;
+                            next = s_off[w][k + 1];
+                            row = s_beg[w][k] - off_k;
+                            u = s_u[w][k];
+                            sv = s_s[w][k];
+                        }
+                        j[v] = ld_stream(col_out + row + e, stream);
+                        uu[v] = u;
+                        ss[v] = sv;
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < kPushVT; v++) {
+                    if (j[v] < 0 || j[v] == uu[v]) continue;
+                    const unsigned off = (unsigned)(j[v] - lo);
+                    if (use_win && off < (unsigned)kWin) atomicAdd(&s_win[off], ss[v]);
+                    else far_add(j[v], ss[v]);
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        if (use_win) {
+            for (int q = tid; q < kWin / 4; q += 256) {
+                const float4 v = reinterpret_cast<const float4 *>(s_win)[q];
+                if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) red_keep_v4(F + lo + 4 * q, v, keep);
+            }
+            __syncthreads();
+        }
+    }
+    // one atomic per hub that received something from this block
+    for (int q = tid; q < kHubSlots; q += 256)
+        if (s_hacc[q] != 0.f) red_keep(&F[s_hub[q]], s_hacc[q], keep);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -574,7 +754,7 @@ void Workspace::reset_graphs() {
 }
 
 struct Launch {
-    int sel_blocks, red_blocks, push_blocks, pull_blocks, ew_blocks;
+    int sel_blocks, red_blocks, push_blocks, win_blocks, pull_blocks, ew_blocks;
 };
 
 // Counts the kernels a call launches from the host and, in profile mode, brackets each launch
@@ -622,6 +802,8 @@ static Launch launch_shape(const di_graph *g) {
     int occ = 0;
     DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push<T>, 256, 0));
     l.push_blocks = sms * (occ > 0 ? occ : 1);
+    DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_win, 256, 0));
+    l.win_blocks = sms * (occ > 0 ? occ : 1);
     DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pull<PULL_PI, T>, 256, 0));
     l.pull_blocks = sms * (occ > 0 ? occ : 1);
     const int64_t n = g->n;
@@ -642,7 +824,8 @@ static void ensure_workspace(di_graph *g) {
     if (ws.fluid == fl) return;
     ws.reset_graphs();
     const size_t n = (size_t)g->n;
-    ws.F.ensure(sizeof(T) * n);
+    ws.F.ensure(sizeof(T) * (n + 8));   // padded: window flushes write four floats at a time
+    ws.chunks.ensure(sizeof(int4) * (n / kSelChunk + 2));
     ws.H.ensure(sizeof(double) * n);
     ws.B.ensure(sizeof(double) * n);
     ws.front_id.ensure(sizeof(int32_t) * n);
@@ -675,13 +858,21 @@ static void launch_sweep_body(di_graph *g, const Launch &l, cudaStream_t s, cuda
                                                   g->rp_out.as<int64_t>(), g->n, ctl, ws.front_id.as<int32_t>(),
                                                   ws.front_s.as<T>(), ws.front_beg.as<int64_t>(),
                                                   ws.front_deg.as<int32_t>(), ws.heavy_id.as<int32_t>(),
-                                                  ws.heavy_s.as<T>());
+                                                  ws.heavy_s.as<T>(), ws.chunks.as<int4>());
     });
     c.run(KC_PUSH, 1, [&] {
-        k_push<T><<<l.push_blocks, 256, 0, s>>>(ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
-                                                ws.front_beg.as<int64_t>(), ws.front_deg.as<int32_t>(),
-                                                ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(), g->rp_out.as<int64_t>(),
-                                                g->col_out.as<int32_t>(), ws.F.as<T>(), ctl);
+        if (sizeof(T) == 4) {
+            k_push_win<<<l.win_blocks, 256, 0, s>>>(
+                ws.front_id.as<int32_t>(), ws.front_s.as<float>(), ws.front_beg.as<int64_t>(),
+                ws.front_deg.as<int32_t>(), ws.heavy_id.as<int32_t>(), ws.heavy_s.as<float>(), g->rp_out.as<int64_t>(),
+                g->col_out.as<int32_t>(), ws.chunks.as<int4>(), g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl);
+        } else {
+            k_push<T><<<l.push_blocks, 256, 0, s>>>(ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
+                                                    ws.front_beg.as<int64_t>(), ws.front_deg.as<int32_t>(),
+                                                    ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(),
+                                                    g->rp_out.as<int64_t>(), g->col_out.as<int32_t>(), ws.F.as<T>(),
+                                                    ctl);
+        }
     });
     c.run(KC_REDUCE, 1, [&] {
         k_reduce<T><<<l.red_blocks, 256, 0, s>>>(ws.F.as<T>(), g->n, ws.partials.as<double>(), ctl, h, set_cond);
