@@ -216,6 +216,29 @@ di_status di_ppr_batch(di_graph *g, int32_t k, const int64_t *seed_offsets, cons
                        double d, const double *tol, const di_solve_opts *opts, double *X_out,
                        double *res_out, di_solve_info *info, void *stream);
 
+/*
+ * di_residual_noalloc — the exact residual F* = B + P.H - H of a history H and its norm
+ * ||F*||_1 (by the identity X = H + (I - P)^-1 F*, ||X - H||_1 <= ||F*||_1 / (1 - d)), computed
+ * without allocating any memory. The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc, such as code that records its work into a CUDA graph by
+ * stream capture, or hosts whose own pool owns all device memory. Its scratch is a static device
+ * array of about 8 MB that every GPU which loads this library holds until the process exits.
+ *   n          1 .. 1048576 nodes (the size the static scratch holds); larger n is rejected with
+ *              DI_ERR_INVALID_ARG.
+ *   rp_in, col_in  int64[n+1], int32[L]: rows of P (in-links), as di_graph_export returns them.
+ *   out_deg    int32[n]: out-degrees.   B, H: double[n].   0 <= d < 1.
+ *   Fstar_out  double[n] or NULL: receives F*.   norm_out: one double, receives ||F*||_1.
+ * Every array must be device memory of the current device; the caller owns all of them. The call
+ * only enqueues work on `stream` (no synchronisation, no allocation); results are ready when
+ * the stream reaches that point. The first call on a device looks up the scratch array's device
+ * address, so make it before any stream capture. Every call shares the one scratch array: calls
+ * whose work can overlap on the GPU (different streams without ordering) race and must not be
+ * issued. Errors: DI_ERR_INVALID_ARG (size, d, NULL or host pointer), DI_ERR_CUDA.
+ */
+di_status di_residual_noalloc(int32_t n, const int64_t *rp_in, const int32_t *col_in,
+                              const int32_t *out_deg, const double *B, double d, const double *H,
+                              double *Fstar_out, double *norm_out, void *stream);
+
 /* Thread-local message of the last failing call on this thread ("" when none). */
 const char *di_last_error(void);
 

@@ -19,7 +19,8 @@ __all__ = [
     "build", "load", "DiError", "Graph",
     "DI_CYC", "DI_SOP", "DI_FLUID_F32", "DI_FLUID_F64",
     "di_graph_create", "di_graph_destroy", "di_graph_stats_get", "di_graph_export",
-    "di_solve", "di_solve_ex", "di_power_iter", "di_solve_batch", "di_ppr_batch", "di_last_error", "di_version",
+    "di_solve", "di_solve_ex", "di_power_iter", "di_solve_batch", "di_ppr_batch", "di_residual_noalloc",
+    "di_last_error", "di_version",
 ]
 
 DI_CYC, DI_SOP = 0, 1
@@ -108,6 +109,8 @@ def load(path: str | None = None):
     lib.di_ppr_batch.restype = st
     lib.di_ppr_batch.argtypes = [vp, i32, vp, vp, dbl, vp, ctypes.POINTER(SolveOpts), vp, vp,
                                  ctypes.POINTER(SolveInfo), vp]
+    lib.di_residual_noalloc.restype = st
+    lib.di_residual_noalloc.argtypes = [i32, vp, vp, vp, vp, dbl, vp, vp, vp, vp]
     lib.di_last_error.restype = ctypes.c_char_p
     lib.di_last_error.argtypes = []
     lib.di_version.restype = ctypes.c_char_p
@@ -289,6 +292,16 @@ def di_ppr_batch(g: Graph, seed_offsets, seeds, d: float, tol, schedule: int = D
                                _ptr(tol, np.float64), ctypes.byref(o), _ptr(X, np.float64), _ptr(res, np.float64),
                                ctypes.byref(info), _stream(seeds, X)), info)
     return X, res, info.as_dict()
+
+
+def di_residual_noalloc(n: int, rp_in, col_in, out_deg, B, d: float, H, norm_out, Fstar_out=None):
+    """Exact residual F* = B + P.H - H and ||F*||_1 (into the one-element CUDA tensor norm_out)
+    with no allocation: every argument is a CUDA tensor the caller owns. Only enqueues work on
+    torch's current stream."""
+    _check(load().di_residual_noalloc(int(n), _ptr(rp_in, np.int64), _ptr(col_in, np.int32), _ptr(out_deg, np.int32),
+                                      _ptr(B, np.float64), float(d), _ptr(H, np.float64),
+                                      _ptr(Fstar_out, np.float64), _ptr(norm_out, np.float64), _stream(H, B)))
+    return norm_out
 
 
 def di_last_error() -> str:
