@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     p.add_argument("--no-legs", action="store_true", help="skip the extra legs (DI-CYC, PI, d=0.95)")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--one-solve", action="store_true",
+                   help="build the graph, run one DI-SOP solve and exit (the command the ncu captures profile)")
     return p.parse_args()
 
 
@@ -104,6 +106,30 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
                 "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+PUSH_SRC = os.path.join(ROOT, "paper_1204_6255_gb300", "csrc", "di_solve.cu")
+PUSH_PROFILE = os.path.join(ROOT, "profiles", "k_push_win_web_n10m.md")
+
+
+def push_traffic():
+    """DRAM bytes per push launch from the committed ncu summary, or None when the kernel source
+    changed since that capture (the summary records the source's sha256)."""
+    import hashlib
+    if not os.path.exists(PUSH_PROFILE):
+        return None, None
+    sha = hashlib.sha256(open(PUSH_SRC, "rb").read()).hexdigest()
+    fields = {}
+    for line in open(PUSH_PROFILE):
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("source_sha256") != sha:
+        return None, "stale: kernel source changed since the capture"
+    try:
+        return float(fields["dram_bytes_per_launch"]), PUSH_PROFILE
+    except (KeyError, ValueError):
+        return None, None
 
 
 def peaks():
@@ -207,6 +233,13 @@ def run_gpu(args):
         return di.di_solve_ex(g, Bx, d, TOL, schedule=schedule, fluid=di.DI_FLUID_F32, max_sweeps=MAX_SWEEPS,
                               X_out=Xx, **kw)[1]
 
+    if args.one_solve:
+        info = step()
+        torch.cuda.synchronize()
+        print(json.dumps({"one_solve": {k: info[k] for k in ("sweeps", "pushed_edges", "frontier_entries",
+                                                             "kernel_launches", "ms")}}))
+        return
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -266,6 +299,7 @@ def run_gpu(args):
     peak, peak_kind = peaks()
     achieved = push_bytes / (push_ms * 1e-3) / 1e9
     kernel_total = prof["select_ms"] + prof["push_ms"] + prof["reduce_ms"] + prof["refine_ms"]
+    traffic, traffic_src = push_traffic()
 
     legs = {}
     if not args.no_legs:
@@ -327,7 +361,7 @@ def run_gpu(args):
                 "ms_per_step": statistics.mean(e2e_ms)},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_push<float>", "peak_kind": peak_kind,
+                     "traffic": traffic, "traffic_source": traffic_src, "kernel": "k_push_win", "peak_kind": peak_kind,
                      "bytes_per_launch": push_bytes, "ms_per_launch": push_ms,
                      "kernel_share": prof["push_ms"] / kernel_total if kernel_total else None},
         "cpu_baseline": cpu,

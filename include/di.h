@@ -216,6 +216,66 @@ di_status di_ppr_batch(di_graph *g, int32_t k, const int64_t *seed_offsets, cons
                        double d, const double *tol, const di_solve_opts *opts, double *X_out,
                        double *res_out, di_solve_info *info, void *stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Serving: personalised-PageRank requests over resident graphs, continuously batched.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct di_server di_server;
+
+typedef struct {
+    double d;                    /* damping of every request; 0 means 0.85 */
+    int32_t slots;               /* request slots per graph (columns of its tile): 4, 8, 16 or 32;
+                                    0 means 32 */
+    int32_t sweeps_per_step;     /* sweeps between two admission / retirement points; 0 means 4 */
+    int32_t max_request_sweeps;  /* a request still above its tolerance after this many sweeps
+                                    ends with DI_ERR_NOT_CONVERGED; 0 means 100000 */
+    int32_t reserved;
+    int64_t mem_budget;          /* device bytes for request state over all graphs (24 bytes per
+                                    node and slot); slots halve until it fits; 0 means no limit */
+} di_server_opts;
+
+typedef struct {
+    int32_t status;              /* di_status of the request */
+    int32_t sweeps;              /* sweeps its slot took part in */
+    int32_t graph, slot;
+    double residual_l1;          /* final ||F||_1 of its column (exact FP64 when tol < 1e-6) */
+    double queue_ms;             /* submit -> admitted into a slot */
+    double service_ms;           /* admitted -> history copied out */
+    double total_ms;             /* submit -> done */
+} di_request_info;
+
+/*
+ * di_server_create — starts one worker (host thread + CUDA stream + a tile of request slots) per
+ * resident graph. Every request is the personalised PageRank X = P.X + B with
+ * B = (1 - d) / |S| on its seed set S (Section 1 problem, Section 2.3 DI-SOP sweeps, per-column
+ * selection and retirement as in di_solve_batch). Requests that arrive while others are on the
+ * GPU are admitted between sweep steps as slots free up, so their work overlaps; the workers of
+ * different graphs run concurrently. The graphs must outlive the server.
+ * Errors: DI_ERR_INVALID_ARG, DI_ERR_OOM (mem_budget below 4 slots per graph), DI_ERR_CUDA.
+ */
+di_status di_server_create(di_graph *const *graphs, int32_t n_graphs, const di_server_opts *opts,
+                           di_server **out);
+
+/*
+ * di_server_submit — queues a request on graph `graph` with seed ids seeds[0 .. n_seeds) (host
+ * memory, copied; a seed listed twice gets two shares) and tolerance tol on ||F||_1. Returns at
+ * once with *request_id. Errors: DI_ERR_INVALID_ARG, DI_ERR_OUT_OF_RANGE_ID (a seed), DI_ERR_CUDA
+ * (the graph's worker stopped).
+ */
+di_status di_server_submit(di_server *srv, int32_t graph, const int32_t *seeds, int32_t n_seeds,
+                           double tol, int64_t *request_id);
+
+/*
+ * di_server_wait — waits at most timeout_ms for a request. When it is done, copies its history H
+ * (the approximation of X, n doubles) into X_out (host or device memory; NULL skips the copy),
+ * fills *info (nullable), forgets the request and returns its status. DI_ERR_TIMEOUT leaves the
+ * request pending (wait again later).
+ */
+di_status di_server_wait(di_server *srv, int64_t request_id, double *X_out, di_request_info *info,
+                         int32_t timeout_ms);
+
+/* Stops the workers (requests not finished end with DI_ERR_BUSY) and frees the server. */
+void di_server_destroy(di_server *srv);
+
 /*
  * di_residual_noalloc — the exact residual F* = B + P.H - H of a history H and its norm
  * ||F*||_1 (by the identity X = H + (I - P)^-1 F*, ||X - H||_1 <= ||F*||_1 / (1 - d)), computed

@@ -20,6 +20,7 @@ __all__ = [
     "DI_CYC", "DI_SOP", "DI_FLUID_F32", "DI_FLUID_F64",
     "di_graph_create", "di_graph_destroy", "di_graph_stats_get", "di_graph_export",
     "di_solve", "di_solve_ex", "di_power_iter", "di_solve_batch", "di_ppr_batch", "di_residual_noalloc",
+    "di_server_create", "di_server_submit", "di_server_wait", "di_server_destroy", "Server",
     "di_last_error", "di_version",
 ]
 
@@ -55,6 +56,20 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("fluid", ctypes.c_int32), ("max_sweeps", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("host_loop", ctypes.c_int32), ("rhs_tile", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_double), ("slots", ctypes.c_int32), ("sweeps_per_step", ctypes.c_int32),
+                ("max_request_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mem_budget", ctypes.c_int64)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("slot", ctypes.c_int32), ("residual_l1", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("service_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class SolveInfo(ctypes.Structure):
@@ -109,6 +124,14 @@ def load(path: str | None = None):
     lib.di_ppr_batch.restype = st
     lib.di_ppr_batch.argtypes = [vp, i32, vp, vp, dbl, vp, ctypes.POINTER(SolveOpts), vp, vp,
                                  ctypes.POINTER(SolveInfo), vp]
+    lib.di_server_create.restype = st
+    lib.di_server_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+    lib.di_server_submit.restype = st
+    lib.di_server_submit.argtypes = [vp, i32, vp, i32, dbl, ctypes.POINTER(ctypes.c_int64)]
+    lib.di_server_wait.restype = st
+    lib.di_server_wait.argtypes = [vp, ctypes.c_int64, vp, ctypes.POINTER(RequestInfo), i32]
+    lib.di_server_destroy.restype = None
+    lib.di_server_destroy.argtypes = [vp]
     lib.di_residual_noalloc.restype = st
     lib.di_residual_noalloc.argtypes = [i32, vp, vp, vp, vp, dbl, vp, vp, vp, vp]
     lib.di_last_error.restype = ctypes.c_char_p
@@ -302,6 +325,57 @@ def di_residual_noalloc(n: int, rp_in, col_in, out_deg, B, d: float, H, norm_out
                                       _ptr(B, np.float64), float(d), _ptr(H, np.float64),
                                       _ptr(Fstar_out, np.float64), _ptr(norm_out, np.float64), _stream(H, B)))
     return norm_out
+
+
+class Server:
+    """Owning wrapper of a di_server handle (keeps its graphs alive)."""
+
+    def __init__(self, handle: int, graphs):
+        self.handle = handle
+        self.graphs = list(graphs)
+
+    def close(self):
+        if self.handle:
+            load().di_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def di_server_create(graphs, d: float = 0.85, slots: int = 0, sweeps_per_step: int = 0, max_request_sweeps: int = 0,
+                     mem_budget: int = 0) -> Server:
+    lib = load()
+    arr = (ctypes.c_void_p * len(graphs))(*[g.handle for g in graphs])
+    o = ServerOpts(float(d), int(slots), int(sweeps_per_step), int(max_request_sweeps), 0, int(mem_budget))
+    h = ctypes.c_void_p()
+    _check(lib.di_server_create(arr, len(graphs), ctypes.byref(o), ctypes.byref(h)))
+    return Server(h.value, graphs)
+
+
+def di_server_submit(srv: Server, graph: int, seeds, tol: float) -> int:
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    rid = ctypes.c_int64()
+    _check(load().di_server_submit(srv.handle, int(graph), seeds.ctypes.data, int(seeds.shape[0]), float(tol),
+                                   ctypes.byref(rid)))
+    return rid.value
+
+
+def di_server_wait(srv: Server, request_id: int, X_out=None, timeout_ms: int = 60000):
+    """Waits for a request; returns (X or None, info). Raises DiError (status 7) on timeout."""
+    info = RequestInfo()
+    st = load().di_server_wait(srv.handle, int(request_id), _ptr(X_out, np.float64), ctypes.byref(info),
+                               int(timeout_ms))
+    if st != 0:
+        raise DiError(st, load().di_last_error().decode(), info.as_dict())
+    return X_out, info.as_dict()
+
+
+def di_server_destroy(srv: Server):
+    srv.close()
 
 
 def di_last_error() -> str:

@@ -1,433 +1,16 @@
-// Batched D-iteration: k independent right-hand sides on one graph, T at a time.
-//
-// The fluid of a tile of T columns is node-major, F[i*T + c] (FP32), so one pass over the
-// out-links of a visited node serves all T fluids: the push loads each link index once and adds
-// four columns per vector atomic (red.global.add.v4.f32). H[i*T + c] is FP64. Every column keeps
-// its own DI-SOP rule (Section 2.3): column c of node i is diffused when
-// |F_ic| > (r_c / L) * out_i with r_c = ||F_c||_1 at the sweep start, and a node is pushed when
-// any of its columns was diffused (columns that were not send 0, and skip their atomics). A
-// column retires when r_c <= tol_c; the tile's WHILE loop ends when every column has retired.
-// With FP32 fluid, retirement is followed by the exact FP64 residual of every column
-// (F*_c = B_c + P.H_c - H_c); a column whose exact residual is above its tolerance re-enters
-// the loop from F*_c.
+// Batched D-iteration: k independent right-hand sides on one graph, solved T at a time in the
+// tiles of di_tile.cuh. With FP32 fluid, retirement is followed by the exact FP64 residual of
+// every column; a column whose exact residual is above its tolerance re-enters the sweep loop
+// from F*_c, aiming at half its tolerance.
 //
 // The tile width T is a template parameter (4, 8, 16, 32). The autotuner times a short probe of
 // each width on the graph itself and keeps the fastest (cached per graph).
 #include <cmath>
 #include <cstring>
 
-#include "di_batch.cuh"
+#include "di_tile.cuh"
 
 namespace di {
-
-constexpr int kMaxT = 32;
-
-struct BatchCtl {
-    double d;
-    double L;
-    double tol[kMaxT];
-    double r[kMaxT];
-    double e[kMaxT];
-    int32_t active[kMaxT];
-    int32_t retire_sweep[kMaxT];
-    unsigned long long pushed;       // sum of out_i over node visits (a node counted once per sweep)
-    unsigned long long visited;      // node visits
-    unsigned long long col_visits;   // (node, column) diffusions
-    unsigned long long front_total;
-    int32_t ncols;
-    int32_t schedule;
-    int32_t max_sweeps;
-    int32_t sweeps;
-    int32_t done;
-    int32_t status;                  // 0 ok, 1 bad right-hand side, 2 seed out of range
-    int32_t force_cyc;
-    int32_t last_selected;
-    int32_t front_count;
-    int32_t batch_next;
-    int32_t body_runs;
-    uint32_t ticket;
-};
-
-// ------------------------------------------------------------------------------------------
-// kernels
-// ------------------------------------------------------------------------------------------
-
-// Bn[i*T + c] = B[(c0 + c) * n + i] for c < ncols (0 for padding columns)
-template <int T>
-__global__ void kb_load_B(const double *B, int32_t n, int c0, int ncols, double *Bn) {
-    const int64_t total = (int64_t)n * T;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / T;
-        const int c = (int)(idx % T);
-        Bn[idx] = c < ncols ? B[(int64_t)(c0 + c) * n + i] : 0.0;
-    }
-}
-
-// Bn[s*T + c] += (1 - d) / |S_c| for every seed s of column c (seeds of columns c0 .. c0+ncols)
-template <int T>
-__global__ void kb_seed_B(const int64_t *off, const int32_t *seeds, int32_t n, int c0, int ncols, double d, double *Bn,
-                          BatchCtl *ctl) {
-    const int64_t e0 = off[c0], e1 = off[c0 + ncols];
-    for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1; e += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = ncols - 1;          // column whose range holds e
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (off[c0 + mid] <= e) lo = mid; else hi = mid - 1;
-        }
-        const int32_t s = seeds[e];
-        if (s < 0 || s >= n) {
-            ctl->status = 2;
-            continue;
-        }
-        const double cnt = (double)(off[c0 + lo + 1] - off[c0 + lo]);
-        atomicAdd(&Bn[(int64_t)s * T + lo], (1.0 - d) / cnt);
-    }
-}
-
-template <int T>
-__global__ void kb_init(const double *Bn, int32_t n, float *F, double *H, BatchCtl *ctl) {
-    bool bad = false;
-    const int64_t total = (int64_t)n * T;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const double b = Bn[idx];
-        if (!(b >= 0.0) || isinf(b)) bad = true;
-        F[idx] = (float)b;
-        H[idx] = 0.0;
-    }
-    if (bad) ctl->status = 1;
-}
-
-// Per-column sums of |v| over a node-major [n][T] array into `out[c]` (FP64, fixed order);
-// the finishing block then runs `tail(total)` on thread 0 after writing the sums.
-template <int T, class V, class Tail>
-__device__ __forceinline__ void column_l1(const V *v, int32_t n, double *partials, BatchCtl *ctl, double *out,
-                                          Tail &&tail) {
-    __shared__ double ssum[8][T];
-    __shared__ bool is_last;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double s = 0.0;
-    const int64_t total = (int64_t)n * T;
-    // blockDim (256) and the grid stride are multiples of T, so a thread always sees column tid % T
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + tid; idx < total; idx += (int64_t)gridDim.x * blockDim.x)
-        s += fabs((double)v[idx]);
-#pragma unroll
-    for (int o = 16; o >= T; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-    if (lane < T) ssum[warp][lane] = s;
-    __syncthreads();
-    if (tid < T) {
-        double b = 0.0;
-        for (int w = 0; w < 8; w++) b += ssum[w][tid];
-        partials[(int64_t)blockIdx.x * T + tid] = b;
-        __threadfence();
-    }
-    __syncthreads();
-    if (tid == 0) is_last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    if (tid < T) {
-        double tot = 0.0;
-        for (int b = 0; b < (int)gridDim.x; b++) tot += __ldcg(&partials[(int64_t)b * T + tid]);
-        out[tid] = tot;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        ctl->ticket = 0;
-        tail();
-    }
-}
-
-// Column retirement and the stop test (thread 0 of the finishing block).
-__device__ __forceinline__ void batch_stop_test(BatchCtl *ctl, cudaGraphConditionalHandle h, int set_cond) {
-    bool any = false;
-    double rsum = 0.0;
-    for (int c = 0; c < ctl->ncols; c++) {
-        if (ctl->active[c] && !(ctl->r[c] > ctl->tol[c])) {
-            ctl->active[c] = 0;
-            ctl->retire_sweep[c] = ctl->sweeps;
-        }
-        any = any || ctl->active[c];
-        rsum += ctl->r[c];
-    }
-    const int sel = ctl->last_selected;
-    ctl->force_cyc = (sel == 0 && rsum > 0.0) ? 1 : 0;
-    ctl->last_selected = 0;
-    ctl->front_total += (unsigned long long)ctl->front_count;
-    ctl->front_count = 0;
-    ctl->batch_next = 0;
-    if (set_cond) ctl->body_runs++;
-    const bool cont = ctl->status == 0 && any && ctl->sweeps < ctl->max_sweeps;
-    ctl->done = cont ? 0 : 1;
-    if (set_cond) cudaGraphSetConditional(h, cont ? 1u : 0u);
-}
-
-template <int T>
-__global__ void __launch_bounds__(256) kb_reduce(const float *F, int32_t n, double *partials, BatchCtl *ctl,
-                                                 cudaGraphConditionalHandle h, int set_cond) {
-    column_l1<T>(F, n, partials, ctl, ctl->r, [&] { batch_stop_test(ctl, h, set_cond); });
-}
-
-// A block handles 256 consecutive nodes per iteration in T sub-steps of 256/T nodes (T lanes per
-// node, one lane per column); the pushed nodes of the 256 are compacted with one atomic, so the
-// frontier is id-sorted within each 256-node chunk.
-template <int T>
-__global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int32_t *out_info, int32_t n,
-                                                 BatchCtl *ctl, int32_t *front_id, float *front_s) {
-    constexpr int kNodesPerStep = 256 / T;
-    __shared__ double s_thr[T];
-    __shared__ int s_act[T];
-    __shared__ double s_e[8][T];
-    __shared__ unsigned long long s_cnt[3][8];
-    __shared__ int wcount[T][8];
-    __shared__ int chunk_base;
-    if (ctl->done) return;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool cyc = ctl->schedule == DI_CYC || ctl->force_cyc;
-    const double d = ctl->d;
-    if (tid < T) {
-        s_thr[tid] = ctl->L > 0.0 ? ctl->r[tid] / ctl->L : 0.0;
-        s_act[tid] = tid < ctl->ncols ? ctl->active[tid] : 0;
-    }
-    __syncthreads();
-    const int c = tid % T;
-    const int gbase = lane & ~(T - 1);                         // first lane of this node's group
-    const unsigned gmask = (T == 32) ? kFull : (((1u << T) - 1u) << gbase);
-    const unsigned below = gbase ? ((1u << gbase) - 1u) : 0u;  // lanes before this group
-    const bool leader = lane == gbase;
-    const double thr = s_thr[c];
-    const bool act = s_act[c] != 0;
-    double e_loc = 0.0;
-    unsigned long long pushed = 0, visited = 0, colv = 0;
-    for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += (int64_t)gridDim.x * 256) {
-        float shares[T];
-        unsigned lbs[T];
-#pragma unroll
-        for (int j = 0; j < T; j++) {
-            const int64_t i = base + j * kNodesPerStep + tid / T;
-            bool sel = false, pushable = false;
-            int32_t o = 0;
-            float share = 0.f;
-            if (i < n) {
-                const int64_t idx = i * T + c;
-                const float f = F[idx];
-                const int32_t info = out_info[i];
-                o = info & 0x7fffffff;
-                const bool lp = info < 0;
-                sel = act && (cyc ? (f != 0.f) : (fabs((double)f) > thr * (double)o));
-                if (sel) {
-                    F[idx] = 0.f;
-                    const double t = lp ? (double)f * (double)o / ((double)o - d) : (double)f;
-                    H[idx] += t;
-                    colv++;
-                    if (o == 0) e_loc += t;
-                    else {
-                        share = (float)(t * d / (double)o);
-                        pushable = (o - (lp ? 1 : 0)) > 0;
-                    }
-                }
-            }
-            const unsigned bsel = __ballot_sync(kFull, sel) & gmask;
-            const unsigned bpush = __ballot_sync(kFull, pushable) & gmask;
-            if (leader && bsel) {
-                visited++;
-                pushed += (unsigned long long)o;
-            }
-            lbs[j] = __ballot_sync(kFull, leader && bpush != 0);
-            shares[j] = share;
-            if (lane == 0) wcount[j][warp] = __popc(lbs[j]);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int run = 0;
-            for (int j = 0; j < T; j++)
-                for (int w = 0; w < 8; w++) {
-                    const int v = wcount[j][w];
-                    wcount[j][w] = run;
-                    run += v;
-                }
-            chunk_base = run ? atomicAdd(&ctl->front_count, run) : 0;
-        }
-        __syncthreads();
-        const int cb = chunk_base;
-#pragma unroll
-        for (int j = 0; j < T; j++) {
-            if (lbs[j] & (1u << gbase)) {
-                const int pos = cb + wcount[j][warp] + __popc(lbs[j] & below);
-                front_s[(int64_t)pos * T + c] = shares[j];
-                if (leader) front_id[pos] = (int32_t)(base + j * kNodesPerStep + tid / T);
-            }
-        }
-        __syncthreads();
-    }
-    // per-column dangling mass
-#pragma unroll
-    for (int o2 = 16; o2 >= T; o2 >>= 1) e_loc += __shfl_xor_sync(kFull, e_loc, o2);
-    if (lane < T) s_e[warp][lane] = e_loc;
-    pushed = warp_sum(pushed);
-    visited = warp_sum(visited);
-    colv = warp_sum(colv);
-    if (lane == 0) { s_cnt[0][warp] = pushed; s_cnt[1][warp] = visited; s_cnt[2][warp] = colv; }
-    __syncthreads();
-    if (tid < T) {
-        double sum = 0.0;
-        for (int w = 0; w < 8; w++) sum += s_e[w][tid];
-        if (sum != 0.0) atomicAdd(&ctl->e[tid], sum);
-    }
-    if (tid == 0) {
-        unsigned long long a = 0, b = 0, cc = 0;
-        for (int w = 0; w < 8; w++) { a += s_cnt[0][w]; b += s_cnt[1][w]; cc += s_cnt[2][w]; }
-        if (a) atomicAdd(&ctl->pushed, a);
-        if (b) {
-            atomicAdd(&ctl->visited, b);
-            atomicAdd(&ctl->last_selected, (int)b);
-        }
-        if (cc) atomicAdd(&ctl->col_visits, cc);
-        if (blockIdx.x == 0) atomicAdd(&ctl->sweeps, 1);
-    }
-}
-
-template <int T>
-__global__ void kb_fill(double *Bn, int64_t count, double v) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-        Bn[i] = v;
-}
-
-__device__ __forceinline__ void red_add_v4(float *p, float4 v) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-                 : "memory");
-}
-
-// One frontier node at a time per warp: T/4 lanes cover the T columns of one link, so a warp
-// walks 128/T links per step, each link index loaded once for its T fluids.
-template <int T>
-__global__ void __launch_bounds__(256) kb_push(const int32_t *__restrict__ front_id, const float *__restrict__ front_s,
-                                               const int64_t *__restrict__ rp_out, const int32_t *__restrict__ col_out,
-                                               float *F, BatchCtl *ctl) {
-    if (ctl->done) return;
-    constexpr int LPE = T / 4;          // lanes per link
-    constexpr int EPI = 32 / LPE;       // links per warp step
-    const int lane = (int)lane_id();
-    const int q = lane % LPE, es = lane / LPE;
-    const int count = ctl->front_count;
-    constexpr int kGrab = 32;
-    for (;;) {
-        int c0 = 0;
-        if (lane == 0) c0 = atomicAdd(&ctl->batch_next, kGrab);
-        c0 = __shfl_sync(kFull, c0, 0);
-        if (c0 >= count) break;
-        const int cend = min(c0 + kGrab, count);
-        for (int p = c0; p < cend; p++) {
-            const int32_t u = front_id[p];
-            const int64_t beg = rp_out[u];
-            const int deg = (int)(rp_out[u + 1] - beg);
-            const float4 s = reinterpret_cast<const float4 *>(front_s + (int64_t)p * T)[q];
-            const bool any = (s.x != 0.f) || (s.y != 0.f) || (s.z != 0.f) || (s.w != 0.f);
-            if (!any) continue;
-            for (int e = es; e < deg; e += EPI) {
-                const int32_t j = col_out[beg + e];
-                if (j != u) red_add_v4(F + (int64_t)j * T + 4 * q, s);
-            }
-        }
-    }
-}
-
-// Exact residual of the history, per column: F*_ic = B_ic + sum_{j in in(i)} d H_jc / out_j - H_ic.
-// (32/T) link slots x T columns per warp; rows with more than kPullHeavy links take their
-// chunk partial sums from kb_resid_heavy.
-template <int T>
-__global__ void kb_resid_heavy(const int64_t *rp_in, const int32_t *col_in, const int32_t *heavy_rows,
-                               const int32_t *chunk_off, const int32_t *chunk_row, int32_t n_chunks,
-                               const int32_t *out_info, const double *H, double d, double *partial) {
-    constexpr int SL = 32 / T;
-    const int lane = (int)lane_id(), c = lane % T, slot = lane / T;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < n_chunks; ch += nwarps) {
-        const int32_t h = chunk_row[ch];
-        const int32_t row = heavy_rows[h];
-        const int64_t b = rp_in[row] + (int64_t)(ch - chunk_off[h]) * kPullChunk;
-        const int64_t e = min(b + (int64_t)kPullChunk, rp_in[row + 1]);
-        double acc = 0.0;
-        for (int64_t k = b + slot; k < e; k += SL) {
-            const int32_t j = col_in[k];
-            acc += d * H[(int64_t)j * T + c] / (double)(out_info[j] & 0x7fffffff);
-        }
-#pragma unroll
-        for (int o = 16; o >= T; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        if (lane < T) partial[ch * T + c] = acc;
-    }
-}
-
-template <int T>
-__global__ void __launch_bounds__(256) kb_resid(const int64_t *rp_in, const int32_t *col_in, const int32_t *out_info,
-                                                const int32_t *heavy_rows, const int32_t *heavy_chunk_off,
-                                                const double *heavy_partial, int32_t n_heavy, const double *Bn,
-                                                const double *H, double d, int32_t n, float *F, double *out_l1,
-                                                double *partials, BatchCtl *ctl) {
-    constexpr int SL = 32 / T;
-    __shared__ double ssum[8][T];
-    __shared__ bool is_last;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int c = lane % T, slot = lane / T;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double colsum = 0.0;
-    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5; i < n; i += nwarps) {
-        const int64_t b = rp_in[i], e = rp_in[i + 1];
-        double acc = 0.0;
-        if (e - b > kPullHeavy) {
-            if (slot == 0) {
-                int lo = 0, hi = n_heavy - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (heavy_rows[mid] < i) lo = mid + 1; else hi = mid;
-                }
-                for (int ch = heavy_chunk_off[lo]; ch < heavy_chunk_off[lo + 1]; ch++) acc += heavy_partial[(int64_t)ch * T + c];
-            }
-        } else {
-            for (int64_t k = b + slot; k < e; k += SL) {
-                const int32_t j = col_in[k];
-                acc += d * H[(int64_t)j * T + c] / (double)(out_info[j] & 0x7fffffff);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o >= T; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        if (lane < T) {
-            const int64_t idx = i * T + c;
-            const double fs = Bn[idx] + acc - H[idx];
-            F[idx] = (float)fs;
-            colsum += fabs(fs);
-        }
-    }
-    if (lane < T) ssum[warp][lane] = colsum;
-    __syncthreads();
-    if (tid < T) {
-        double s = 0.0;
-        for (int w = 0; w < 8; w++) s += ssum[w][tid];
-        partials[(int64_t)blockIdx.x * T + tid] = s;
-        __threadfence();
-    }
-    __syncthreads();
-    if (tid == 0) is_last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    if (tid < T) {
-        double tot = 0.0;
-        for (int bb = 0; bb < (int)gridDim.x; bb++) tot += __ldcg(&partials[(int64_t)bb * T + tid]);
-        out_l1[tid] = tot;
-    }
-    __syncthreads();
-    if (tid == 0) ctl->ticket = 0;
-}
-
-// X[(c0 + c) * n + i] = H[i*T + c] for c < ncols   (column-major output block)
-template <int T>
-__global__ void kb_extract(const double *H, int32_t n, int ncols, double *X) {
-    const int64_t total = (int64_t)n * ncols;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = idx / n, i = idx % n;
-        X[idx] = H[i * T + c];
-    }
-}
 
 // ------------------------------------------------------------------------------------------
 // host side
@@ -440,111 +23,6 @@ BatchWorkspace::~BatchWorkspace() {
 }
 
 void destroy_batch_workspace(BatchWorkspace *w) { delete w; }
-
-static int tile_index(int T) { return T == 4 ? 0 : T == 8 ? 1 : T == 16 ? 2 : 3; }
-
-static void ensure_batch(di_graph *g, int T) {
-    if (!g->bws) g->bws = new BatchWorkspace();
-    BatchWorkspace &w = *g->bws;
-    const size_t n = (size_t)g->n;
-    if (w.T_alloc < T) {
-        for (auto &e : w.exec)
-            if (e) cudaGraphExecDestroy(e);
-        for (auto &e : w.exec) e = nullptr;
-        w.F.ensure(sizeof(float) * n * T);
-        w.H.ensure(sizeof(double) * n * T);
-        w.Bn.ensure(sizeof(double) * n * T);
-        w.front_id.ensure(sizeof(int32_t) * n);
-        w.front_s.ensure(sizeof(float) * n * T);
-        w.heavy_partial.ensure(sizeof(double) * (size_t)(g->n_heavy_in_chunks + 1) * T);
-        w.T_alloc = T;
-    }
-    w.partials.ensure(sizeof(double) * kReduceBlocks * kMaxT);
-    w.ctl.ensure(sizeof(BatchCtl));
-    w.stage.ensure(sizeof(double) * n * T);
-    if (!w.capture_stream) DI_CHECK_CUDA(cudaStreamCreateWithFlags(&w.capture_stream, cudaStreamNonBlocking));
-    if (!w.ctl_host) DI_CHECK_CUDA(cudaMallocHost(&w.ctl_host, sizeof(BatchCtl)));
-}
-
-struct BLaunch {
-    int ew, sel, push, red, pull;
-};
-
-template <int T>
-static BLaunch blaunch(const di_graph *g) {
-    BLaunch l;
-    const int sms = g->dev.sms;
-    const int64_t n = g->n;
-    auto cap = [&](int64_t want, int64_t lim) { return (int)(want < 1 ? 1 : (want < lim ? want : lim)); };
-    l.ew = cap((n * T + 255) / 256, (int64_t)sms * 8);
-    l.sel = cap((n * T + 255) / 256, (int64_t)sms * 8);
-    int occ = 0;
-    DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_push<T>, 256, 0));
-    l.push = sms * (occ > 0 ? occ : 1);
-    l.red = cap((n * T + 255) / 256, (int64_t)(sms * 4 < kReduceBlocks ? sms * 4 : kReduceBlocks));
-    l.pull = cap((n + 7) / 8, (int64_t)(sms * 8 < kReduceBlocks ? sms * 8 : kReduceBlocks));
-    return l;
-}
-
-template <int T>
-static void batch_body(di_graph *g, const BLaunch &l, cudaStream_t s, cudaGraphConditionalHandle h, int set_cond) {
-    BatchWorkspace &w = *g->bws;
-    BatchCtl *ctl = w.ctl.as<BatchCtl>();
-    kb_select<T><<<l.sel, 256, 0, s>>>(w.F.as<float>(), w.H.as<double>(), g->out_info.as<int32_t>(), g->n, ctl,
-                                       w.front_id.as<int32_t>(), w.front_s.as<float>());
-    kb_push<T><<<l.push, 256, 0, s>>>(w.front_id.as<int32_t>(), w.front_s.as<float>(), g->rp_out.as<int64_t>(),
-                                      g->col_out.as<int32_t>(), w.F.as<float>(), ctl);
-    kb_reduce<T><<<l.red, 256, 0, s>>>(w.F.as<float>(), g->n, w.partials.as<double>(), ctl, h, set_cond);
-}
-
-template <int T>
-static cudaGraphExec_t batch_graph(di_graph *g, const BLaunch &l) {
-    BatchWorkspace &w = *g->bws;
-    cudaGraphExec_t &ex = w.exec[tile_index(T)];
-    if (ex) return ex;
-    cudaGraph_t graph;
-    DI_CHECK_CUDA(cudaGraphCreate(&graph, 0));
-    cudaGraphConditionalHandle h;
-    DI_CHECK_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    DI_CHECK_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
-    DI_CHECK_CUDA(cudaStreamBeginCaptureToGraph(w.capture_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                                cudaStreamCaptureModeThreadLocal));
-    batch_body<T>(g, l, w.capture_stream, h, 1);
-    cudaGraph_t captured;
-    DI_CHECK_CUDA(cudaStreamEndCapture(w.capture_stream, &captured));
-    DI_CHECK_CUDA(cudaGraphInstantiate(&ex, graph, 0));
-    DI_CHECK_CUDA(cudaGraphDestroy(graph));
-    return ex;
-}
-
-template <int T>
-static void batch_resid(di_graph *g, const BLaunch &l, double d, cudaStream_t s) {
-    BatchWorkspace &w = *g->bws;
-    BatchCtl *ctl = w.ctl.as<BatchCtl>();
-    if (g->n_heavy_in_chunks > 0) {
-        int blocks = (g->n_heavy_in_chunks + 7) / 8;
-        if (blocks > g->dev.sms * 8) blocks = g->dev.sms * 8;
-        kb_resid_heavy<T><<<blocks, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(),
-                                                 g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(),
-                                                 g->heavy_in_chunk_row.as<int32_t>(), g->n_heavy_in_chunks,
-                                                 g->out_info.as<int32_t>(), w.H.as<double>(), d,
-                                                 w.heavy_partial.as<double>());
-    }
-    kb_resid<T><<<l.pull, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), g->out_info.as<int32_t>(),
-                                       g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(),
-                                       w.heavy_partial.as<double>(), g->n_heavy_in, w.Bn.as<double>(),
-                                       w.H.as<double>(), d, g->n, w.F.as<float>(), ctl->r, w.partials.as<double>(), ctl);
-}
-
-static void read_bctl(BatchWorkspace &w, cudaStream_t s) {
-    DI_CHECK_CUDA(cudaMemcpyAsync(w.ctl_host, w.ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
-    DI_CHECK_CUDA(cudaStreamSynchronize(s));
-}
 
 // Solves one tile of up to T columns [c0, c0 + ncols): right-hand sides already in w.Bn.
 // Accumulates the report into `acc`; writes per-column residuals into res_host[c0 + c].
@@ -570,7 +48,7 @@ static void solve_tile(di_graph *g, int c0, int ncols, double d, const double *t
     DI_CHECK_CUDA(cudaMemcpyAsync(ctl, &hc, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
     kb_init<T><<<l.ew, 256, 0, s>>>(w.Bn.as<double>(), g->n, w.F.as<float>(), w.H.as<double>(), ctl);
     int64_t launches = 1;
-    cudaGraphExec_t ex = batch_graph<T>(g, l);
+    cudaGraphExec_t ex = batch_graph<T>(g, w, l);
     int rounds = 0;
     for (;;) {
         kb_reduce<T><<<l.red, 256, 0, s>>>(w.F.as<float>(), g->n, w.partials.as<double>(), ctl,
@@ -582,7 +60,7 @@ static void solve_tile(di_graph *g, int c0, int ncols, double d, const double *t
             read_bctl(w, s);
             break;
         }
-        batch_resid<T>(g, l, d, s);
+        batch_resid<T>(g, w, l, d, s);
         launches += g->n_heavy_in_chunks > 0 ? 2 : 1;
         read_bctl(w, s);
         rounds++;
@@ -652,7 +130,8 @@ static double probe(di_graph *g, double d, cudaStream_t s) {
 
 static int autotune(di_graph *g, double d, cudaStream_t s) {
     if (g->bws && g->bws->tuned_T) return g->bws->tuned_T;
-    ensure_batch(g, 32);
+    if (!g->bws) g->bws = new BatchWorkspace();
+    ensure_batch(g, *g->bws, 32);
     double best = -1.0;
     int bestT = 8;
     const int cands[4] = {4, 8, 16, 32};
@@ -672,7 +151,8 @@ template <int T>
 static void batch_all(di_graph *g, int k, const double *B, bool B_dev, const int64_t *off_dev, const int32_t *seeds_dev,
                       double d, const double *tol_host, int schedule, int max_sweeps, bool refine, double *X_out,
                       bool X_dev, double *res_host, di_solve_info *acc, cudaStream_t s) {
-    ensure_batch(g, T);
+    if (!g->bws) g->bws = new BatchWorkspace();
+    ensure_batch(g, *g->bws, T);
     BatchWorkspace &w = *g->bws;
     const BLaunch l = blaunch<T>(g);
     BatchCtl *ctl = w.ctl.as<BatchCtl>();

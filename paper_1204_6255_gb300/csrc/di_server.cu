@@ -1,0 +1,416 @@
+// Serving personalised-PageRank requests over resident graphs with continuous batching.
+//
+// Every graph has a worker thread with its own CUDA stream and one tile of T request slots
+// (di_tile.cuh: node-major FP32 fluid, FP64 history, per-column DI-SOP selection and
+// retirement). The worker repeats one step:
+//   1. admit queued requests into free slots (reset the slot's columns, scatter the seeds'
+//      mass (1 - d) / |S| into B and F);
+//   2. run at most `sweeps_per_step` sweeps of the tile from one CUDA-graph launch (the WHILE
+//      loop also ends as soon as every occupied slot has retired);
+//   3. retire: a slot whose ||F_c||_1 fell to its tolerance is finished; for tolerances below
+//      1e-6 the exact FP64 residual of the tile (B + P.H - H) is recomputed first and a slot
+//      whose exact residual is still above its tolerance keeps sweeping from it;
+//   4. copy each finished column's history to the request and free its slot.
+// Requests that arrive while others are on the GPU are admitted at the next step as slots
+// free up, so requests of different arrival times share sweeps, and the workers of different
+// graphs run concurrently on the device. Each column is an independent problem; batch-mates
+// only change which nodes a sweep visits, not the fixed point.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <thread>
+#include <unordered_map>
+
+#include "di_tile.cuh"
+
+namespace di {
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+template <int T>
+__global__ void ks_cols_reset(float *F, double *H, double *Bn, int32_t n, uint32_t mask) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int c = 0; c < T; c++) {
+            if (!(mask >> c & 1u)) continue;
+            F[i * T + c] = 0.f;
+            H[i * T + c] = 0.0;
+            Bn[i * T + c] = 0.0;
+        }
+    }
+}
+
+template <int T>
+__global__ void ks_seed_col(const int32_t *seeds, int cnt, int c, double share, float *F, double *Bn) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+        const int64_t s = seeds[e];
+        atomicAdd(&Bn[s * T + c], share);
+        atomicAdd(&F[s * T + c], (float)share);
+    }
+}
+
+template <int T>
+__global__ void ks_col_extract(const double *H, int32_t n, int c, double *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = H[i * T + c];
+}
+
+struct Request {
+    int64_t id = 0;
+    int graph = 0;
+    std::vector<int32_t> seeds;
+    double tol = 0.0;
+    double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+    int slot = -1;
+    int admit_sweep = 0;
+    std::vector<double> X;
+    di_status status = DI_OK;
+    int sweeps = 0;
+    double residual = 0.0;
+    bool done = false;
+};
+
+}  // namespace
+
+struct Worker;
+
+}  // namespace di
+
+struct di_server {
+    double d = 0.85;
+    int sweeps_per_step = 4;
+    int max_request_sweeps = 100000;
+    std::vector<std::unique_ptr<di::Worker>> workers;
+    std::mutex mu;                       // requests map, completion signalling
+    std::condition_variable done_cv;
+    std::unordered_map<int64_t, std::shared_ptr<di::Request>> requests;
+    int64_t next_id = 1;
+    std::atomic<bool> stop{false};
+    ~di_server();
+};
+
+namespace di {
+
+struct Worker {
+    di_server *srv = nullptr;
+    di_graph *g = nullptr;
+    int index = 0;
+    int T = 32;
+    BatchWorkspace w;
+    cudaStream_t s = nullptr;
+    DevBuf seeds_dev, col_out;
+    double *pinned = nullptr;            // one column of X on its way to the host
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::vector<std::shared_ptr<Request>> slot;
+    std::thread th;
+    std::atomic<bool> failed{false};
+
+    ~Worker() {
+        if (pinned) cudaFreeHost(pinned);
+        if (s) cudaStreamDestroy(s);
+    }
+
+    template <int TT>
+    void step_loop();
+    void run();
+};
+
+template <int TT>
+void Worker::step_loop() {
+    const int32_t n = g->n;
+    const BLaunch l = blaunch<TT>(g);
+    BatchCtl *ctl = w.ctl.as<BatchCtl>();
+    BatchCtl &hc = *(BatchCtl *)w.ctl_host;
+    memset(&hc, 0, sizeof(BatchCtl));
+    hc.d = srv->d;
+    hc.L = (double)g->L;
+    hc.ncols = TT;
+    hc.schedule = DI_SOP;
+    hc.last_selected = -1;
+    for (int c = 0; c < TT; c++) hc.retire_sweep[c] = -1;
+    DI_CHECK_CUDA(cudaMemsetAsync(w.F.p, 0, sizeof(float) * (size_t)n * TT, s));
+    DI_CHECK_CUDA(cudaMemsetAsync(w.H.p, 0, sizeof(double) * (size_t)n * TT, s));
+    DI_CHECK_CUDA(cudaMemsetAsync(w.Bn.p, 0, sizeof(double) * (size_t)n * TT, s));
+    cudaGraphExec_t ex = batch_graph<TT>(g, w, l);
+    slot.assign(TT, nullptr);
+    while (!srv->stop.load()) {
+        // 1. admission
+        std::vector<std::shared_ptr<Request>> admitted;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            bool any_busy = false;
+            for (auto &r : slot) any_busy = any_busy || (r != nullptr);
+            if (!any_busy && queue.empty()) {
+                cv.wait_for(lk, std::chrono::milliseconds(20));
+                continue;
+            }
+            for (int c = 0; c < TT && !queue.empty(); c++) {
+                if (slot[c]) continue;
+                auto r = queue.front();
+                queue.pop_front();
+                r->slot = c;
+                r->t_admit = now_ms();
+                slot[c] = r;
+                admitted.push_back(r);
+            }
+        }
+        if (!admitted.empty()) {
+            uint32_t mask = 0;
+            for (auto &r : admitted) mask |= 1u << r->slot;
+            ks_cols_reset<TT><<<l.ew, 256, 0, s>>>(w.F.as<float>(), w.H.as<double>(), w.Bn.as<double>(), n, mask);
+            for (auto &r : admitted) {
+                const int cnt = (int)r->seeds.size();
+                seeds_dev.ensure(sizeof(int32_t) * (size_t)cnt);
+                DI_CHECK_CUDA(cudaMemcpyAsync(seeds_dev.p, r->seeds.data(), sizeof(int32_t) * (size_t)cnt,
+                                              cudaMemcpyHostToDevice, s));
+                ks_seed_col<TT><<<(cnt + 255) / 256, 256, 0, s>>>(seeds_dev.as<int32_t>(), cnt, r->slot,
+                                                                   (1.0 - srv->d) / cnt, w.F.as<float>(),
+                                                                   w.Bn.as<double>());
+                // the seed upload is synchronous with respect to the host buffer only after this
+                DI_CHECK_CUDA(cudaStreamSynchronize(s));
+                const int c = r->slot;
+                hc.active[c] = 1;
+                hc.tol[c] = r->tol;
+                hc.r[c] = 0.0;
+                hc.e[c] = 0.0;
+                hc.retire_sweep[c] = -1;
+                r->admit_sweep = hc.sweeps;
+            }
+            DI_CHECK_CUDA(cudaGetLastError());
+        }
+        // 2. a bounded number of sweeps
+        hc.max_sweeps = hc.sweeps + srv->sweeps_per_step;
+        hc.done = 0;
+        hc.ticket = 0;
+        DI_CHECK_CUDA(cudaMemcpyAsync(ctl, &hc, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
+        kb_reduce<TT><<<l.red, 256, 0, s>>>(w.F.as<float>(), n, w.partials.as<double>(), ctl,
+                                            cudaGraphConditionalHandle(0), 0);
+        DI_CHECK_CUDA(cudaGraphLaunch(ex, s));
+        DI_CHECK_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+        DI_CHECK_CUDA(cudaStreamSynchronize(s));
+        // 3. retirement
+        std::vector<int> retired;
+        bool need_exact = false;
+        for (int c = 0; c < TT; c++) {
+            if (!slot[c]) continue;
+            const bool capped = hc.sweeps - slot[c]->admit_sweep >= srv->max_request_sweeps;
+            if (!hc.active[c] || capped) {
+                retired.push_back(c);
+                need_exact = need_exact || slot[c]->tol < 1e-6;
+            }
+        }
+        if (retired.empty()) continue;
+        if (need_exact) {
+            batch_resid<TT>(g, w, l, srv->d, s);
+            DI_CHECK_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+            DI_CHECK_CUDA(cudaStreamSynchronize(s));
+        }
+        for (int c : retired) {
+            auto r = slot[c];
+            const bool capped = hc.sweeps - r->admit_sweep >= srv->max_request_sweeps;
+            if (hc.r[c] > r->tol && !capped) {
+                hc.active[c] = 1;            // keeps sweeping from the exact residual
+                hc.tol[c] = 0.5 * r->tol;
+                continue;
+            }
+            // 4. the column's history goes to the request
+            ks_col_extract<TT><<<l.ew, 256, 0, s>>>(w.H.as<double>(), n, c, col_out.as<double>());
+            DI_CHECK_CUDA(cudaMemcpyAsync(pinned, col_out.p, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
+            DI_CHECK_CUDA(cudaStreamSynchronize(s));
+            r->X.assign(pinned, pinned + n);
+            r->sweeps = hc.sweeps - r->admit_sweep;
+            r->residual = hc.r[c];
+            r->status = hc.r[c] <= r->tol ? DI_OK : DI_ERR_NOT_CONVERGED;
+            hc.active[c] = 0;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                slot[c] = nullptr;
+            }
+            {
+                std::lock_guard<std::mutex> lk(srv->mu);
+                r->t_done = now_ms();
+                r->done = true;
+            }
+            srv->done_cv.notify_all();
+        }
+    }
+}
+
+void Worker::run() {
+    try {
+        DI_CHECK_CUDA(cudaSetDevice(g->dev.device));
+        switch (T) {
+            case 4: step_loop<4>(); break;
+            case 8: step_loop<8>(); break;
+            case 16: step_loop<16>(); break;
+            default: step_loop<32>(); break;
+        }
+    } catch (const Fail &) {
+        failed.store(true);
+    }
+    // fail whatever is left
+    std::vector<std::shared_ptr<Request>> left;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto &r : slot)
+            if (r) left.push_back(r);
+        for (auto &r : queue) left.push_back(r);
+        queue.clear();
+    }
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        for (auto &r : left)
+            if (!r->done) {
+                r->status = srv->stop.load() ? DI_ERR_BUSY : DI_ERR_CUDA;
+                r->done = true;
+                r->t_done = now_ms();
+            }
+    }
+    srv->done_cv.notify_all();
+}
+
+}  // namespace di
+
+di_server::~di_server() {
+    stop.store(true);
+    for (auto &w : workers) {
+        w->cv.notify_all();
+        if (w->th.joinable()) w->th.join();
+    }
+}
+
+using namespace di;
+
+extern "C" {
+
+di_status di_server_create(di_graph *const *graphs, int32_t n_graphs, const di_server_opts *opts, di_server **out) {
+    return guarded([&] {
+        DI_REQUIRE(out != nullptr, DI_ERR_INVALID_ARG, "out is NULL");
+        *out = nullptr;
+        DI_REQUIRE(graphs != nullptr && n_graphs >= 1, DI_ERR_INVALID_ARG, "need at least one graph");
+        di_server_opts o;
+        memset(&o, 0, sizeof(o));
+        if (opts) o = *opts;
+        const double d = o.d == 0.0 ? 0.85 : o.d;
+        DI_REQUIRE(d > 0.0 && d < 1.0, DI_ERR_INVALID_ARG, "d must be in (0, 1) (got %g)", d);
+        int T = o.slots == 0 ? 32 : o.slots;
+        DI_REQUIRE(T == 4 || T == 8 || T == 16 || T == 32, DI_ERR_INVALID_ARG, "slots must be 4, 8, 16 or 32");
+        // request state per slot and node: F (4) + H (8) + B (8) + frontier share (4) bytes
+        auto state_bytes = [&](int t) {
+            int64_t b = 0;
+            for (int i = 0; i < n_graphs; i++) b += (int64_t)graphs[i]->n * t * 24;
+            return b;
+        };
+        if (o.mem_budget > 0) {
+            while (T > 4 && state_bytes(T) > o.mem_budget) T /= 2;
+            DI_REQUIRE(state_bytes(T) <= o.mem_budget, DI_ERR_OOM,
+                       "request state needs %lld bytes for 4 slots per graph; budget is %lld",
+                       (long long)state_bytes(T), (long long)o.mem_budget);
+        }
+        std::unique_ptr<di_server> srv(new di_server());
+        srv->d = d;
+        srv->sweeps_per_step = o.sweeps_per_step > 0 ? o.sweeps_per_step : 4;
+        srv->max_request_sweeps = o.max_request_sweeps > 0 ? o.max_request_sweeps : 100000;
+        for (int i = 0; i < n_graphs; i++) {
+            DI_REQUIRE(graphs[i] != nullptr, DI_ERR_INVALID_ARG, "graph %d is NULL", i);
+            std::unique_ptr<Worker> w(new Worker());
+            w->srv = srv.get();
+            w->g = graphs[i];
+            w->index = i;
+            w->T = T;
+            DeviceGuard dg(graphs[i]->dev.device);
+            ensure_batch(graphs[i], w->w, T);
+            w->col_out.ensure(sizeof(double) * (size_t)graphs[i]->n);
+            DI_CHECK_CUDA(cudaStreamCreateWithFlags(&w->s, cudaStreamNonBlocking));
+            DI_CHECK_CUDA(cudaMallocHost(&w->pinned, sizeof(double) * (size_t)graphs[i]->n));
+            srv->workers.push_back(std::move(w));
+        }
+        for (auto &w : srv->workers) {
+            Worker *wp = w.get();
+            w->th = std::thread([wp] { wp->run(); });
+        }
+        *out = srv.release();
+    });
+}
+
+di_status di_server_submit(di_server *srv, int32_t graph, const int32_t *seeds, int32_t n_seeds, double tol,
+                           int64_t *request_id) {
+    return guarded([&] {
+        DI_REQUIRE(srv && request_id, DI_ERR_INVALID_ARG, "server or request_id is NULL");
+        DI_REQUIRE(graph >= 0 && graph < (int32_t)srv->workers.size(), DI_ERR_INVALID_ARG, "graph %d out of range",
+                   graph);
+        DI_REQUIRE(seeds && n_seeds >= 1, DI_ERR_INVALID_ARG, "a request needs at least one seed");
+        DI_REQUIRE(tol > 0.0 && std::isfinite(tol), DI_ERR_INVALID_ARG, "tol must be positive (got %g)", tol);
+        Worker &w = *srv->workers[graph];
+        DI_REQUIRE(!w.failed.load(), DI_ERR_CUDA, "the worker of graph %d stopped on a CUDA error", graph);
+        auto r = std::make_shared<Request>();
+        r->graph = graph;
+        r->seeds.assign(seeds, seeds + n_seeds);
+        for (int32_t v : r->seeds)
+            DI_REQUIRE(v >= 0 && v < w.g->n, DI_ERR_OUT_OF_RANGE_ID, "seed %d outside [0, %d)", v, w.g->n);
+        r->tol = tol;
+        r->t_submit = now_ms();
+        {
+            std::lock_guard<std::mutex> lk(srv->mu);
+            r->id = srv->next_id++;
+            srv->requests[r->id] = r;
+        }
+        {
+            std::lock_guard<std::mutex> lk(w.mu);
+            w.queue.push_back(r);
+        }
+        w.cv.notify_one();
+        *request_id = r->id;
+    });
+}
+
+di_status di_server_wait(di_server *srv, int64_t request_id, double *X_out, di_request_info *info,
+                         int32_t timeout_ms) {
+    return guarded([&] {
+        DI_REQUIRE(srv != nullptr, DI_ERR_INVALID_ARG, "server is NULL");
+        std::shared_ptr<Request> r;
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            auto it = srv->requests.find(request_id);
+            DI_REQUIRE(it != srv->requests.end(), DI_ERR_INVALID_ARG, "unknown request %lld", (long long)request_id);
+            r = it->second;
+            const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+            while (!r->done) {
+                if (srv->done_cv.wait_until(lk, deadline) == std::cv_status::timeout && !r->done) {
+                    set_error("request %lld not finished after %d ms", (long long)request_id, timeout_ms);
+                    throw Fail{DI_ERR_TIMEOUT};
+                }
+            }
+            srv->requests.erase(it);
+        }
+        if (info) {
+            memset(info, 0, sizeof(*info));
+            info->status = r->status;
+            info->sweeps = r->sweeps;
+            info->graph = r->graph;
+            info->slot = r->slot;
+            info->residual_l1 = r->residual;
+            info->queue_ms = r->t_admit > 0 ? r->t_admit - r->t_submit : 0.0;
+            info->service_ms = r->t_admit > 0 ? r->t_done - r->t_admit : 0.0;
+            info->total_ms = r->t_done - r->t_submit;
+        }
+        if (X_out && !r->X.empty()) {
+            cudaStream_t s = nullptr;
+            from_device(X_out, r->X.data(), sizeof(double) * r->X.size(), s);
+            DI_CHECK_CUDA(cudaStreamSynchronize(s));
+        }
+        DI_REQUIRE(r->status == DI_OK, r->status, "request %lld ended with status %d", (long long)request_id,
+                   (int)r->status);
+    });
+}
+
+void di_server_destroy(di_server *srv) { delete srv; }
+
+}  // extern "C"
