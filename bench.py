@@ -189,6 +189,128 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------------------
+# PPR legs: batched solves and served requests, each against per-request plain solves
+# ------------------------------------------------------------------------------------------
+def pct(values, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(values, dtype=float), q)) if values else None
+
+
+def ppr_batch_leg(di, workloads, torch):
+    """256 personalised PageRank requests on the 2M-node graph (seed sets of 1..1000 nodes,
+    tol 1e-6): one batched call against the same requests solved one by one (a sample)."""
+    import numpy as np
+    cfg = workloads.WORKLOADS["ppr_n2m_k256"]
+    n, src, dst = workloads.generate(cfg["spec"])
+    g = di.di_graph_create(n, src, dst)
+    k, d, tol = cfg["k"], cfg["d"], cfg["tol"]
+    off, seeds = workloads.seed_sets(n, k, cfg["max_seeds"], seed=cfg["spec"].seed)
+    off_d, seeds_d = torch.from_numpy(off).cuda(), torch.from_numpy(seeds).cuda()
+    X = torch.empty((k, n), dtype=torch.float64, device="cuda")
+    di.di_ppr_batch(g, off_d[:9], seeds_d, d, tol, X_out=X[:8])        # autotune + warm-up
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    _, res, info = di.di_ppr_batch(g, off_d, seeds_d, d, tol, X_out=X)
+    torch.cuda.synchronize()
+    batch_s = time.perf_counter() - t
+    # per-request plain solves (single right-hand side, FP32 fluid + refinement), a sample
+    sample = 48
+    B = torch.zeros(n, dtype=torch.float64, device="cuda")
+    Xs = torch.empty(n, dtype=torch.float64, device="cuda")
+    for r in range(2):                                   # warm-up of the same path
+        B.zero_()
+        sr = seeds_d[off[r]:off[r + 1]].long()
+        B.index_add_(0, sr, torch.full((sr.numel(),), (1 - d) / sr.numel(), dtype=torch.float64, device="cuda"))
+        di.di_solve(g, B, d, tol, di.DI_SOP, MAX_SWEEPS, X_out=Xs)
+    torch.cuda.synchronize()
+    lat = []
+    t0 = time.perf_counter()
+    for r in range(sample):
+        B.zero_()
+        sr = seeds_d[off[r]:off[r + 1]].long()
+        B.index_add_(0, sr, torch.full((sr.numel(),), (1 - d) / sr.numel(), dtype=torch.float64, device="cuda"))
+        t = time.perf_counter()
+        di.di_solve(g, B, d, tol, di.DI_SOP, MAX_SWEEPS, X_out=Xs)
+        lat.append(1e3 * (time.perf_counter() - t))
+    solo_s = time.perf_counter() - t0
+    return {"requests": k, "graph": f"N={n}, L={g.stats['L']}", "tol": tol, "rhs_tile": info["rhs_tile"],
+            "batched_qps": k / batch_s, "batched_ms": 1e3 * batch_s,
+            "per_request_qps": sample / solo_s, "per_request_p50_ms": pct(lat, 50), "per_request_p99_ms": pct(lat, 99),
+            "speedup": (k / batch_s) / (sample / solo_s), "max_residual": float(np.max(res))}
+
+
+def serving_leg(di, workloads, torch, rate_qps=600.0, n_req=300, slots=16):
+    """Poisson stream of personalised PageRank requests over four resident graphs (N = 100k,
+    500k, 2M, 5M), tolerances 1e-4/1e-6/1e-8, seed sets of 1..1000 nodes: the continuously
+    batched server against the same stream served by plain single-RHS solves in arrival order."""
+    import threading
+    import numpy as np
+    cfg = workloads.WORKLOADS["serve_4g"]
+    d = cfg["d"]
+    graphs = []
+    for spec in cfg["specs"]:
+        n, src, dst = workloads.generate(spec)
+        graphs.append(di.di_graph_create(n, src, dst))
+    u = workloads.uniform(4242, 1, 3 * n_req)
+    gaps = -np.log(1.0 - u[:n_req]) / rate_qps                  # Poisson arrivals
+    arrive = np.cumsum(gaps)
+    gsel = (u[n_req:2 * n_req] * len(graphs)).astype(int)
+    tsel = (u[2 * n_req:] * 3).astype(int)
+    reqs = []
+    for i in range(n_req):
+        g = graphs[gsel[i]]
+        off, seeds = workloads.seed_sets(g.n, 1, cfg["max_seeds"], seed=7000 + i)
+        reqs.append((gsel[i], seeds, cfg["tols"][tsel[i]]))
+
+    # served
+    srv = di.di_server_create(graphs, d=d, slots=slots, sweeps_per_step=4)
+    for gi in range(len(graphs)):                                   # warm every worker
+        di.di_server_wait(srv, di.di_server_submit(srv, gi, np.array([0], np.int32), 1e-4), timeout_ms=60000)
+    ids = [None] * n_req
+    t0 = time.perf_counter()
+    for i, (gi, seeds, tol) in enumerate(reqs):
+        delay = arrive[i] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids[i] = di.di_server_submit(srv, int(gi), seeds, tol)
+    lat, worst = [], 0.0
+    for i in range(n_req):
+        _, info = di.di_server_wait(srv, ids[i], timeout_ms=600000)
+        lat.append(info["total_ms"])
+        worst = max(worst, info["residual_l1"] / reqs[i][2])
+    served_s = time.perf_counter() - t0
+    srv.close()
+
+    # per-request plain solves in arrival order (one request at a time on the same GPU)
+    Bs = [torch.zeros(g.n, dtype=torch.float64, device="cuda") for g in graphs]
+    Xs = [torch.empty(g.n, dtype=torch.float64, device="cuda") for g in graphs]
+    for gi, g in enumerate(graphs):                                 # warm-up of the same path
+        B = Bs[gi]
+        B.zero_()
+        sd = torch.arange(0, 8, dtype=torch.int64, device="cuda")
+        B.index_add_(0, sd, torch.full((8,), (1 - d) / 8, dtype=torch.float64, device="cuda"))
+        di.di_solve(g, B, d, 1e-4, di.DI_SOP, MAX_SWEEPS, X_out=Xs[gi])
+    torch.cuda.synchronize()
+    lat_p = []
+    t0 = time.perf_counter()
+    for i, (gi, seeds, tol) in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if now < arrive[i]:
+            time.sleep(arrive[i] - now)
+        B = Bs[gi]
+        B.zero_()
+        sd = torch.from_numpy(seeds.astype(np.int64)).cuda()
+        B.index_add_(0, sd, torch.full((sd.numel(),), (1 - d) / sd.numel(), dtype=torch.float64, device="cuda"))
+        di.di_solve(graphs[gi], B, d, tol, di.DI_SOP, MAX_SWEEPS, X_out=Xs[gi])
+        lat_p.append(1e3 * ((time.perf_counter() - t0) - arrive[i]))
+    plain_s = time.perf_counter() - t0
+    return {"requests": n_req, "arrival_qps": rate_qps, "graphs": [g.n for g in graphs], "slots": slots,
+            "served_qps": n_req / served_s, "served_p50_ms": pct(lat, 50), "served_p99_ms": pct(lat, 99),
+            "plain_qps": n_req / plain_s, "plain_p50_ms": pct(lat_p, 50), "plain_p99_ms": pct(lat_p, 99),
+            "worst_residual_over_tol": worst}
+
+
+# ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
 def run_gpu(args):
@@ -324,6 +446,9 @@ def run_gpu(args):
         ms = a.elapsed_time(b)
         legs["pi"] = {"ms_to_residual": ms, "GTEPS": pinf["pushed_edges"] / (ms * 1e-3) / 1e9,
                       "iterations": pinf["sweeps"], "residual_l1": pinf["residual_l1"]}
+    if not args.no_legs:
+        legs["ppr_batch"] = ppr_batch_leg(di, workloads, torch)
+        legs["serving"] = serving_leg(di, workloads, torch)
     legs["di_sop"] = {"ms_to_residual": statistics.median(step_ms), "sweeps": infos[-1]["sweeps"],
                       "pushed_per_L": infos[-1]["pushed_edges"] / st["L"], "refine_rounds": infos[-1]["refine_rounds"],
                       "residual_l1": infos[-1]["residual_l1"]}

@@ -302,14 +302,14 @@ def di_solve_batch(g: Graph, B, d: float, tol, schedule: int = DI_SOP, max_sweep
 
 
 def di_ppr_batch(g: Graph, seed_offsets, seeds, d: float, tol, schedule: int = DI_SOP, max_sweeps: int = 0,
-                 rhs_tile: int = 0, refine: int = 0, X_out=None, res_out=None):
+                 rhs_tile: int = 0, refine: int = 0, host_loop: int = 0, X_out=None, res_out=None):
     """Personalised PageRank for k seed sets (seed_offsets int64[k+1], seeds int32): column r has
     B_r = (1-d)/|S_r| on its seeds. Returns (X (k, n), residuals (k,), info)."""
     k = int(seed_offsets.shape[0]) - 1
     tol = _tol_array(tol, k, seeds)
     X = X_out if X_out is not None else (_like(seeds, k * g.n, np.float64).reshape(k, g.n))
     res = res_out if res_out is not None else np.empty(k, dtype=np.float64)
-    o = SolveOpts(int(schedule), DI_FLUID_F32, int(max_sweeps), int(refine), 0, int(rhs_tile), 0, 0)
+    o = SolveOpts(int(schedule), DI_FLUID_F32, int(max_sweeps), int(refine), int(host_loop), int(rhs_tile), 0, 0)
     info = SolveInfo()
     _check(load().di_ppr_batch(g.handle, k, _ptr(seed_offsets, np.int64), _ptr(seeds, np.int32), float(d),
                                _ptr(tol, np.float64), ctypes.byref(o), _ptr(X, np.float64), _ptr(res, np.float64),

@@ -54,7 +54,17 @@ static void solve_tile(di_graph *g, int c0, int ncols, double d, const double *t
         kb_reduce<T><<<l.red, 256, 0, s>>>(w.F.as<float>(), g->n, w.partials.as<double>(), ctl,
                                            cudaGraphConditionalHandle(0), 0);
         DI_CHECK_CUDA(cudaGetLastError());
-        DI_CHECK_CUDA(cudaGraphLaunch(ex, s));
+        if (w.host_loop) {
+            // host-driven sweeps (one sync per sweep), for profiling the kernels one by one
+            for (;;) {
+                read_bctl(w, s);
+                if (hc.done) break;
+                batch_body<T>(g, w, l, s, cudaGraphConditionalHandle(0), 0);
+                launches += 3;
+            }
+        } else {
+            DI_CHECK_CUDA(cudaGraphLaunch(ex, s));
+        }
         launches += 1;
         if (!refine) {
             read_bctl(w, s);
@@ -233,6 +243,8 @@ static di_status batch_entry(di_graph *g, int32_t k, const double *B, const int6
         const bool B_dev = B && is_device_ptr(B);
         const bool X_dev = is_device_ptr(X_out);
         int T = o.rhs_tile ? o.rhs_tile : autotune(g, d, s);
+        if (!g->bws) g->bws = new BatchWorkspace();
+        g->bws->host_loop = o.host_loop != 0;
         std::vector<double> res((size_t)k, 0.0);
         di_solve_info acc;
         memset(&acc, 0, sizeof(acc));

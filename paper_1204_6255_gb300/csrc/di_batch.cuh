@@ -9,10 +9,11 @@ struct BatchWorkspace {
     int T_alloc = 0;                 // widest tile the buffers hold
     int tuned_T = 0;                 // autotuned tile width (0 = not tuned yet)
     double probe_rate[4] = {0, 0, 0, 0};   // column-link updates per second of each width
-    DevBuf F, H, Bn, front_id, front_s, heavy_partial, partials, ctl, stage;
+    DevBuf F, H, Bn, front_id, front_s, heavy_partial, partials, ctl, stage, y;
     cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};   // per tile width
     cudaStream_t capture_stream = nullptr;
     void *ctl_host = nullptr;
+    bool host_loop = false;          // drive the sweeps from the host instead of the graph
     ~BatchWorkspace();
 };
 

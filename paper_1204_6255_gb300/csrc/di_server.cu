@@ -197,18 +197,19 @@ void Worker::step_loop() {
         DI_CHECK_CUDA(cudaStreamSynchronize(s));
         // 3. retirement
         std::vector<int> retired;
-        bool need_exact = false;
+        uint32_t exact_mask = 0;
         for (int c = 0; c < TT; c++) {
             if (!slot[c]) continue;
             const bool capped = hc.sweeps - slot[c]->admit_sweep >= srv->max_request_sweeps;
             if (!hc.active[c] || capped) {
                 retired.push_back(c);
-                need_exact = need_exact || slot[c]->tol < 1e-6;
+                if (slot[c]->tol < 1e-6) exact_mask |= 1u << c;
             }
         }
         if (retired.empty()) continue;
-        if (need_exact) {
-            batch_resid<TT>(g, w, l, srv->d, s);
+        if (exact_mask) {
+            // exact residual of just the retiring tight-tolerance columns
+            batch_resid<TT>(g, w, l, srv->d, s, exact_mask);
             DI_CHECK_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
             DI_CHECK_CUDA(cudaStreamSynchronize(s));
         }

@@ -103,9 +103,17 @@ __device__ __forceinline__ void column_l1(const V *v, int32_t n, double *partial
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double s = 0.0;
     const int64_t total = (int64_t)n * T;
-    // blockDim (256) and the grid stride are multiples of T, so a thread always sees column tid % T
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + tid; idx < total; idx += (int64_t)gridDim.x * blockDim.x)
-        s += fabs((double)v[idx]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // blockDim (256) and the grid stride are multiples of T, so a thread always sees column
+    // tid % T; four independent loads per step, summed in FP32 and widened to FP64 (this
+    // part's FP64 rate is low)
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + tid;
+    for (; idx + 3 * stride < total; idx += 4 * stride) {
+        const float a = fabsf((float)__ldcg(v + idx)), b = fabsf((float)__ldcg(v + idx + stride));
+        const float c2 = fabsf((float)__ldcg(v + idx + 2 * stride)), e2 = fabsf((float)__ldcg(v + idx + 3 * stride));
+        s += (double)((a + b) + (c2 + e2));
+    }
+    for (; idx < total; idx += stride) s += (double)fabsf((float)__ldcg(v + idx));
 #pragma unroll
     for (int o = 16; o >= T; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
     if (lane < T) ssum[warp][lane] = s;
@@ -176,6 +184,8 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
     __shared__ unsigned long long s_cnt[3][8];
     __shared__ int wcount[T][8];
     __shared__ int chunk_base;
+    __shared__ float s_share[T][256];       // per sub-step share of every lane
+    __shared__ unsigned s_lbs[T][8];        // per sub-step leader ballot of every warp
     if (ctl->done) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool cyc = ctl->schedule == DI_CYC || ctl->force_cyc;
@@ -190,14 +200,13 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
     const unsigned gmask = (T == 32) ? kFull : (((1u << T) - 1u) << gbase);
     const unsigned below = gbase ? ((1u << gbase) - 1u) : 0u;  // lanes before this group
     const bool leader = lane == gbase;
-    const double thr = s_thr[c];
+    const float thr_f = (float)s_thr[c];
+    const float d_f = (float)d;
     const bool act = s_act[c] != 0;
-    double e_loc = 0.0;
+    float e_run = 0.f;
     unsigned long long pushed = 0, visited = 0, colv = 0;
     for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += (int64_t)gridDim.x * 256) {
-        float shares[T];
-        unsigned lbs[T];
-#pragma unroll
+#pragma unroll 4
         for (int j = 0; j < T; j++) {
             const int64_t i = base + j * kNodesPerStep + tid / T;
             bool sel = false, pushable = false;
@@ -209,15 +218,17 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
                 const int32_t info = out_info[i];
                 o = info & 0x7fffffff;
                 const bool lp = info < 0;
-                sel = act && (cyc ? (f != 0.f) : (fabs((double)f) > thr * (double)o));
+                sel = act && (cyc ? (f != 0.f) : (fabsf(f) > thr_f * (float)o));
                 if (sel) {
                     F[idx] = 0.f;
-                    const double t = lp ? (double)f * (double)o / ((double)o - d) : (double)f;
-                    H[idx] += t;
+                    // FP32 transit and share; FP64 only for H += transit
+                    const float of = (float)o;
+                    const float tf = lp ? f * of / (of - d_f) : f;
+                    H[idx] += (double)tf;
                     colv++;
-                    if (o == 0) e_loc += t;
+                    if (o == 0) e_run += tf;
                     else {
-                        share = (float)(t * d / (double)o);
+                        share = tf * d_f / of;
                         pushable = (o - (lp ? 1 : 0)) > 0;
                     }
                 }
@@ -228,9 +239,12 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
                 visited++;
                 pushed += (unsigned long long)o;
             }
-            lbs[j] = __ballot_sync(kFull, leader && bpush != 0);
-            shares[j] = share;
-            if (lane == 0) wcount[j][warp] = __popc(lbs[j]);
+            const unsigned lb = __ballot_sync(kFull, leader && bpush != 0);
+            s_share[j][tid] = share;
+            if (lane == 0) {
+                s_lbs[j][warp] = lb;
+                wcount[j][warp] = __popc(lb);
+            }
         }
         __syncthreads();
         if (tid == 0) {
@@ -245,17 +259,19 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
         }
         __syncthreads();
         const int cb = chunk_base;
-#pragma unroll
+#pragma unroll 4
         for (int j = 0; j < T; j++) {
-            if (lbs[j] & (1u << gbase)) {
-                const int pos = cb + wcount[j][warp] + __popc(lbs[j] & below);
-                front_s[(int64_t)pos * T + c] = shares[j];
+            const unsigned lb = s_lbs[j][warp];
+            if (lb & (1u << gbase)) {
+                const int pos = cb + wcount[j][warp] + __popc(lb & below);
+                front_s[(int64_t)pos * T + c] = s_share[j][tid];
                 if (leader) front_id[pos] = (int32_t)(base + j * kNodesPerStep + tid / T);
             }
         }
         __syncthreads();
     }
     // per-column dangling mass
+    double e_loc = (double)e_run;
 #pragma unroll
     for (int o2 = 16; o2 >= T; o2 >>= 1) e_loc += __shfl_xor_sync(kFull, e_loc, o2);
     if (lane < T) s_e[warp][lane] = e_loc;
@@ -327,13 +343,57 @@ __global__ void __launch_bounds__(256) kb_push(const int32_t *__restrict__ front
     }
 }
 
+// Double-float helpers (an unevaluated sum hi + lo of two FP32 numbers; Knuth two-sum and an
+// FMA-based exact product) so the link sums of the residual need no FP64 arithmetic.
+static __device__ __forceinline__ float2 tdf_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    float e = (a.x - (s - bb)) + (b.x - bb);
+    e += a.y + b.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+static __device__ __forceinline__ float2 tdf_mul(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float hi = p + e;
+    return make_float2(hi, e - (hi - p));
+}
+static __device__ __forceinline__ float2 tdf_from(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+// y[i*T + c] = d * H_ic / out_i as double-float (0 for a dangling node); d / out_i is formed
+// once per node and shared by the T columns.
+template <int T>
+__global__ void kb_resid_y(const double *H, const int32_t *out_info, int32_t n, double d, uint32_t mask, float2 *y) {
+    const int64_t total = (int64_t)n * T;
+    const int lane = threadIdx.x & 31, leader = lane & ~(T - 1);
+    // whole warps iterate together (total is a multiple of T, blocks of 256 threads)
+    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) & ~31ll; base < total;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t idx = base + (threadIdx.x & ~31) + lane;
+        float2 c = make_float2(0.f, 0.f);
+        if (lane == leader && idx < total) {
+            const int32_t o = out_info[idx / T] & 0x7fffffff;
+            if (o) c = tdf_from(d / (double)o);           // one division per node
+        }
+        c.x = __shfl_sync(kFull, c.x, leader);
+        c.y = __shfl_sync(kFull, c.y, leader);
+        if (idx < total && (mask >> (lane & (T - 1)) & 1u)) y[idx] = tdf_mul(tdf_from(H[idx]), c);
+    }
+}
+
 // Exact residual of the history, per column: F*_ic = B_ic + sum_{j in in(i)} d H_jc / out_j - H_ic.
 // (32/T) link slots x T columns per warp; rows with more than kPullHeavy links take their
 // chunk partial sums from kb_resid_heavy.
 template <int T>
 __global__ void kb_resid_heavy(const int64_t *rp_in, const int32_t *col_in, const int32_t *heavy_rows,
                                const int32_t *chunk_off, const int32_t *chunk_row, int32_t n_chunks,
-                               const int32_t *out_info, const double *H, double d, double *partial) {
+                               const float2 *y, uint32_t mask, float2 *partial) {
     constexpr int SL = 32 / T;
     const int lane = (int)lane_id(), c = lane % T, slot = lane / T;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -342,23 +402,26 @@ __global__ void kb_resid_heavy(const int64_t *rp_in, const int32_t *col_in, cons
         const int32_t row = heavy_rows[h];
         const int64_t b = rp_in[row] + (int64_t)(ch - chunk_off[h]) * kPullChunk;
         const int64_t e = min(b + (int64_t)kPullChunk, rp_in[row + 1]);
-        double acc = 0.0;
-        for (int64_t k = b + slot; k < e; k += SL) {
-            const int32_t j = col_in[k];
-            acc += d * H[(int64_t)j * T + c] / (double)(out_info[j] & 0x7fffffff);
-        }
+        float2 acc = make_float2(0.f, 0.f);
+        if (mask >> c & 1u)
+            for (int64_t k = b + slot; k < e; k += SL) acc = tdf_add(acc, y[(int64_t)__ldcs(col_in + k) * T + c]);
 #pragma unroll
-        for (int o = 16; o >= T; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        for (int o = 16; o >= T; o >>= 1) {
+            float2 t;
+            t.x = __shfl_xor_sync(kFull, acc.x, o);
+            t.y = __shfl_xor_sync(kFull, acc.y, o);
+            acc = tdf_add(acc, t);
+        }
         if (lane < T) partial[ch * T + c] = acc;
     }
 }
 
 template <int T>
-__global__ void __launch_bounds__(256) kb_resid(const int64_t *rp_in, const int32_t *col_in, const int32_t *out_info,
+__global__ void __launch_bounds__(256) kb_resid(const int64_t *rp_in, const int32_t *col_in, const float2 *y,
                                                 const int32_t *heavy_rows, const int32_t *heavy_chunk_off,
-                                                const double *heavy_partial, int32_t n_heavy, const double *Bn,
-                                                const double *H, double d, int32_t n, float *F, double *out_l1,
-                                                double *partials, BatchCtl *ctl) {
+                                                const float2 *heavy_partial, int32_t n_heavy, const double *Bn,
+                                                const double *H, int32_t n, uint32_t mask, float *F,
+                                                double *out_l1, double *partials, BatchCtl *ctl) {
     constexpr int SL = 32 / T;
     __shared__ double ssum[8][T];
     __shared__ bool is_last;
@@ -368,27 +431,33 @@ __global__ void __launch_bounds__(256) kb_resid(const int64_t *rp_in, const int3
     double colsum = 0.0;
     for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5; i < n; i += nwarps) {
         const int64_t b = rp_in[i], e = rp_in[i + 1];
-        double acc = 0.0;
-        if (e - b > kPullHeavy) {
+        float2 acc = make_float2(0.f, 0.f);
+        const bool mine = (mask >> c & 1u) != 0;
+        if (!mine) {
+            // this column keeps its fluid
+        } else if (e - b > kPullHeavy) {
             if (slot == 0) {
                 int lo = 0, hi = n_heavy - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
                     if (heavy_rows[mid] < i) lo = mid + 1; else hi = mid;
                 }
-                for (int ch = heavy_chunk_off[lo]; ch < heavy_chunk_off[lo + 1]; ch++) acc += heavy_partial[(int64_t)ch * T + c];
+                for (int ch = heavy_chunk_off[lo]; ch < heavy_chunk_off[lo + 1]; ch++)
+                    acc = tdf_add(acc, heavy_partial[(int64_t)ch * T + c]);
             }
         } else {
-            for (int64_t k = b + slot; k < e; k += SL) {
-                const int32_t j = col_in[k];
-                acc += d * H[(int64_t)j * T + c] / (double)(out_info[j] & 0x7fffffff);
-            }
+            for (int64_t k = b + slot; k < e; k += SL) acc = tdf_add(acc, y[(int64_t)__ldcs(col_in + k) * T + c]);
         }
 #pragma unroll
-        for (int o = 16; o >= T; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        if (lane < T) {
+        for (int o = 16; o >= T; o >>= 1) {
+            float2 t;
+            t.x = __shfl_xor_sync(kFull, acc.x, o);
+            t.y = __shfl_xor_sync(kFull, acc.y, o);
+            acc = tdf_add(acc, t);
+        }
+        if (lane < T && mine) {
             const int64_t idx = i * T + c;
-            const double fs = Bn[idx] + acc - H[idx];
+            const double fs = Bn[idx] + ((double)acc.x + (double)acc.y) - H[idx];
             F[idx] = (float)fs;
             colsum += fabs(fs);
         }
@@ -406,7 +475,7 @@ __global__ void __launch_bounds__(256) kb_resid(const int64_t *rp_in, const int3
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    if (tid < T) {
+    if (tid < T && (mask >> tid & 1u)) {
         double tot = 0.0;
         for (int bb = 0; bb < (int)gridDim.x; bb++) tot += __ldcg(&partials[(int64_t)bb * T + tid]);
         out_l1[tid] = tot;
@@ -438,7 +507,8 @@ static void ensure_batch(di_graph *g, BatchWorkspace &w, int T) {
         w.Bn.ensure(sizeof(double) * n * T);
         w.front_id.ensure(sizeof(int32_t) * n);
         w.front_s.ensure(sizeof(float) * n * T);
-        w.heavy_partial.ensure(sizeof(double) * (size_t)(g->n_heavy_in_chunks + 1) * T);
+        w.heavy_partial.ensure(sizeof(float2) * (size_t)(g->n_heavy_in_chunks + 1) * T);
+        w.y.ensure(sizeof(float2) * n * T);
         w.T_alloc = T;
     }
     w.partials.ensure(sizeof(double) * kReduceBlocks * kMaxT);
@@ -503,22 +573,26 @@ static cudaGraphExec_t batch_graph(di_graph *g, BatchWorkspace &w, const BLaunch
     return ex;
 }
 
+// Exact residual of the columns in `mask`: F_c <- F*_c and ctl->r[c] <- ||F*_c||_1; other
+// columns are untouched, and their lanes issue no loads.
 template <int T>
-static void batch_resid(di_graph *g, BatchWorkspace &w, const BLaunch &l, double d, cudaStream_t s) {
+static void batch_resid(di_graph *g, BatchWorkspace &w, const BLaunch &l, double d, cudaStream_t s,
+                        uint32_t mask = 0xffffffffu) {
     BatchCtl *ctl = w.ctl.as<BatchCtl>();
+    kb_resid_y<T><<<l.ew, 256, 0, s>>>(w.H.as<double>(), g->out_info.as<int32_t>(), g->n, d, mask, w.y.as<float2>());
     if (g->n_heavy_in_chunks > 0) {
         int blocks = (g->n_heavy_in_chunks + 7) / 8;
         if (blocks > g->dev.sms * 8) blocks = g->dev.sms * 8;
         kb_resid_heavy<T><<<blocks, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(),
                                                  g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(),
                                                  g->heavy_in_chunk_row.as<int32_t>(), g->n_heavy_in_chunks,
-                                                 g->out_info.as<int32_t>(), w.H.as<double>(), d,
-                                                 w.heavy_partial.as<double>());
+                                                 w.y.as<float2>(), mask, w.heavy_partial.as<float2>());
     }
-    kb_resid<T><<<l.pull, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), g->out_info.as<int32_t>(),
+    kb_resid<T><<<l.pull, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), w.y.as<float2>(),
                                        g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(),
-                                       w.heavy_partial.as<double>(), g->n_heavy_in, w.Bn.as<double>(),
-                                       w.H.as<double>(), d, g->n, w.F.as<float>(), ctl->r, w.partials.as<double>(), ctl);
+                                       w.heavy_partial.as<float2>(), g->n_heavy_in, w.Bn.as<double>(),
+                                       w.H.as<double>(), g->n, mask, w.F.as<float>(), ctl->r, w.partials.as<double>(),
+                                       ctl);
 }
 
 static void read_bctl(BatchWorkspace &w, cudaStream_t s) {

@@ -128,3 +128,14 @@ def test_ppr_workload_sample():
         assert ok
         # tol 1e-6 on ||F||_1 bounds the error by 1e-6 / (1 - d) in L1
         assert np.abs(H - X[r]).sum() <= cfg["tol"] / (1 - cfg["d"]) + 1e-10
+
+
+def test_first_batch_call_with_explicit_tile_and_host_loop():
+    # a fresh graph whose first batched call names its tile width (no autotuning beforehand)
+    n, g, og = _graph(1500, 6000, seed=101)
+    off, seeds = workloads.seed_sets(n, 5, 40, seed=102)
+    X1, res1, _ = di.di_ppr_batch(g, off, seeds, D, 1e-10, rhs_tile=8, host_loop=1)
+    X2, res2, _ = di.di_ppr_batch(g, off, seeds, D, 1e-10, rhs_tile=8)
+    for r in range(5):
+        ref = _oracle_X(og, oracle.ppr_B(n, seeds[off[r]:off[r + 1]], D))
+        assert rel_l1(X1[r], ref) <= TOL_X and rel_l1(X2[r], ref) <= TOL_X
