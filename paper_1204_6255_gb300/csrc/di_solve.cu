@@ -630,6 +630,13 @@ enum { PULL_PI = 0, PULL_RESID = 1 };
 //               c_i = d / out_i (all double-float); sum delta -> ctl->r, iteration count and the
 //               WHILE condition.
 //   PULL_RESID: F*_i = B_i + acc_i - H_i (FP64) -> F_i (as T); sum |F*| -> ctl->r.
+// Segmented sum over the links of 32 consecutive rows per warp: each lane takes kPullVT
+// contiguous links per round (kPullVT index loads, then kPullVT gathers in flight), forms a
+// segmented prefix over them, and one segmented scan across the 32 lanes joins rows that span
+// lanes; a row's last link writes the row's sum, so no two lanes write the same row. A row
+// that runs past a round carries into the next.
+constexpr int kPullVT = 8;
+
 template <int MODE, class T>
 __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in, const int32_t *__restrict__ col_in,
                                               const float2 *y0, float2 *y1, int32_t n, const int32_t *heavy_rows,
@@ -639,12 +646,15 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
                                               float2 *Xdf, const double *H, T *F, double *partials, SolveCtl *ctl,
                                               cudaGraphConditionalHandle hcond, int set_cond) {
     __shared__ float2 acc_s[8][32];
+    __shared__ int s_off[8][33];
+    __shared__ int64_t s_beg[8][32];
     __shared__ double scratch[32];
     const int lane = (int)lane_id(), warp = threadIdx.x >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const bool odd = (MODE == PULL_PI) && (ctl->sweeps & 1);
     const float2 *y_in = odd ? y1 : y0;
     float2 *y_out = odd ? const_cast<float2 *>(y0) : y1;
+    const uint64_t stream = policy_evict_first();
     double sum = 0.0;
     float run = 0.f;
     int runs = 0;
@@ -664,32 +674,87 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
             heavy = dd > kPullHeavy;
             deg = heavy ? 0 : (int)dd;
         }
+        const int inc = warp_inclusive_scan(deg);
+        const int total = __shfl_sync(kFull, inc, 31);
+        s_off[warp][lane] = inc - deg;
+        if (lane == 31) s_off[warp][32] = total;
+        s_beg[warp][lane] = beg - (inc - deg);      // link e of row k sits at s_beg[k] + e
         acc_s[warp][lane] = make_float2(0.f, 0.f);
         __syncwarp();
-        const int inc = warp_inclusive_scan(deg);
-        const int off = inc - deg;
-        const int total = __shfl_sync(kFull, inc, 31);
-        for (int q0 = 0; q0 < total; q0 += 32) {
-            const int q = q0 + lane;
-            const int ow = warp_owner(off, q);
-            const int64_t ob = __shfl_sync(kFull, beg, ow);
-            const int oo = __shfl_sync(kFull, off, ow);
-            const bool act = q < total;
-            float2 v = act ? y_in[__ldcs(col_in + ob + (q - oo))] : make_float2(0.f, 0.f);
-            const int own = act ? ow : 32;
-            // segmented inclusive scan; owners are non-decreasing across lanes
+        float2 carry = make_float2(0.f, 0.f);
+        int carry_row = -1;
+        for (int e0 = 0; e0 < total; e0 += 32 * kPullVT) {
+            const int first = e0 + lane * kPullVT;
+            int k = 0;   // last row with s_off[k] <= first
 #pragma unroll
-            for (int s = 1; s < 32; s <<= 1) {
-                float2 vv;
-                vv.x = __shfl_up_sync(kFull, v.x, s);
-                vv.y = __shfl_up_sync(kFull, v.y, s);
-                const int o2 = __shfl_up_sync(kFull, own, s);
-                if (lane >= s && o2 == own) v = df_add(v, vv);
+            for (int step = 16; step > 0; step >>= 1)
+                if (s_off[warp][k + step] <= first) k += step;
+            int next = s_off[warp][k + 1];
+            int key[kPullVT];
+            int32_t j[kPullVT];
+#pragma unroll
+            for (int v = 0; v < kPullVT; v++) {
+                const int e = first + v;
+                key[v] = 64 + lane;                 // past the end: a key no row uses
+                if (e < total) {
+                    while (e >= next) next = s_off[warp][++k + 1];
+                    key[v] = k;
+                    j[v] = ld_stream(col_in + s_beg[warp][k] + e, stream);
+                }
             }
-            const int next_own = __shfl_down_sync(kFull, own, 1);
-            if (act && (lane == 31 || next_own != own)) acc_s[warp][own] = df_add(acc_s[warp][own], v);
-            __syncwarp();
+            float2 val[kPullVT];
+#pragma unroll
+            for (int v = 0; v < kPullVT; v++) val[v] = key[v] < 64 ? y_in[j[v]] : make_float2(0.f, 0.f);
+            // the previous round's carry joins the first link of its row
+            if (lane == 0 && key[0] == carry_row) val[0] = df_add(val[0], carry);
+            // segmented prefix within the lane
+#pragma unroll
+            for (int v = 1; v < kPullVT; v++)
+                if (key[v] == key[v - 1]) val[v] = df_add(val[v - 1], val[v]);
+            // segmented scan of the lanes' last segments (keys never decrease across lanes)
+            float2 sv = val[kPullVT - 1];
+            const int sk = key[kPullVT - 1];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                float2 ov;
+                ov.x = __shfl_up_sync(kFull, sv.x, off);
+                ov.y = __shfl_up_sync(kFull, sv.y, off);
+                const int ok = __shfl_up_sync(kFull, sk, off);
+                if (lane >= off && ok == sk) sv = df_add(ov, sv);
+            }
+            float2 cin;
+            cin.x = __shfl_up_sync(kFull, sv.x, 1);
+            cin.y = __shfl_up_sync(kFull, sv.y, 1);
+            const int ck = __shfl_up_sync(kFull, sk, 1);
+            const bool join = lane > 0 && ck == key[0];
+            // finished rows: the row's last link writes its sum
+#pragma unroll
+            for (int v = 0; v < kPullVT; v++) {
+                const int e = first + v;
+                if (key[v] >= 64) continue;
+                float2 fin = (join && key[v] == key[0]) ? df_add(cin, val[v]) : val[v];
+                if (e + 1 == s_off[warp][key[v] + 1]) acc_s[warp][key[v]] = fin;
+                val[v] = fin;
+            }
+            // carry for the next round: the round's last link, when its row goes on
+            const int last_e = min(e0 + 32 * kPullVT, total) - 1;
+            const int owner_lane = (last_e - e0) / kPullVT, owner_v = (last_e - e0) % kPullVT;
+            float2 cv = make_float2(0.f, 0.f);
+            int crow = -1;
+#pragma unroll
+            for (int v = 0; v < kPullVT; v++)
+                if (v == owner_v) {
+                    cv = val[v];
+                    crow = key[v];
+                }
+            cv.x = __shfl_sync(kFull, cv.x, owner_lane);
+            cv.y = __shfl_sync(kFull, cv.y, owner_lane);
+            crow = __shfl_sync(kFull, crow, owner_lane);
+            const bool goes_on = crow < 64 && last_e + 1 < s_off[warp][crow + 1];
+            carry = goes_on ? cv : make_float2(0.f, 0.f);
+            carry_row = goes_on ? crow : -1;
         }
+        __syncwarp();
         float2 a = acc_s[warp][lane];
         __syncwarp();
         if (heavy) {
