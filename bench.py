@@ -356,7 +356,7 @@ def run_gpu(args):
                               X_out=Xx, **kw)[1]
 
     if args.one_solve:
-        info = step()
+        info = step(profile=1)        # kernels launched one by one, so a profiler sees each
         torch.cuda.synchronize()
         print(json.dumps({"one_solve": {k: info[k] for k in ("sweeps", "pushed_edges", "frontier_entries",
                                                              "kernel_launches", "ms")}}))

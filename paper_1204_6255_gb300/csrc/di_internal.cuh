@@ -144,6 +144,7 @@ struct Workspace {
     int fluid = -1;                 // di_fluid the buffers were sized for
     DevBuf F, H, B, front_id, front_s, front_beg, front_deg, heavy_id, heavy_s, partials, ctl, y0, y1, chunks;
     DevBuf Bdf, cdf, Xdf;           // power iteration in double-float: B, d/out, X
+    double cdf_d = -1.0;            // damping factor cdf currently holds (-1: none)
     cudaGraphExec_t sweep_exec = nullptr;   // reduce -> WHILE{select, push, reduce}
     cudaGraphExec_t pi_exec = nullptr;      // pull -> WHILE{pull}
     cudaStream_t capture_stream = nullptr;

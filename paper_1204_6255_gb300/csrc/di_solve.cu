@@ -572,12 +572,18 @@ __device__ __forceinline__ float2 df_from(double v) {
 }
 __device__ __forceinline__ double df_to(float2 a) { return (double)a.x + (double)a.y; }
 
-// y[j] = d * v[j] / out_j (0 for a dangling node), as double-float (refinement: v = H)
-__global__ void k_scale(const double *v, const int32_t *out_info, int32_t n, double d, float2 *y) {
+// c[j] = d / out_j as double-float (0 for a dangling node)
+__global__ void k_link_weight(const int32_t *out_info, int32_t n, double d, float2 *c) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t o = out_info[i] & 0x7fffffff;
-        y[i] = df_from(o ? d * v[i] / (double)o : 0.0);
+        c[i] = df_from(o ? d / (double)o : 0.0);
     }
+}
+
+// y[j] = v[j] * c[j] in double-float (refinement: v = H, c = d / out)
+__global__ void k_scale(const double *v, const float2 *c, int32_t n, float2 *y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = df_mul(df_from(v[i]), c[i]);
 }
 
 // Power-iteration set-up: c[j] = d / out_j (0 if dangling), B and X_0 = 0 as double-float, y_0 = 0.
@@ -905,6 +911,7 @@ static void ensure_workspace(di_graph *g) {
     ws.y1.ensure(sizeof(float2) * n);
     ws.Bdf.ensure(sizeof(float2) * n);
     ws.cdf.ensure(sizeof(float2) * n);
+    ws.cdf_d = -1.0;
     ws.Xdf.ensure(sizeof(float2) * n);
     if (!ws.capture_stream) DI_CHECK_CUDA(cudaStreamCreateWithFlags(&ws.capture_stream, cudaStreamNonBlocking));
     if (!ws.ctl_host) DI_CHECK_CUDA(cudaMallocHost(&ws.ctl_host, sizeof(SolveCtl)));
@@ -1017,7 +1024,11 @@ template <class T>
 static void launch_refine(di_graph *g, const Launch &l, double d, cudaStream_t s) {
     Workspace &ws = g->ws;
     SolveCtl *ctl = ws.ctl.as<SolveCtl>();
-    k_scale<<<l.ew_blocks, 256, 0, s>>>(ws.H.as<double>(), g->out_info.as<int32_t>(), g->n, d, ws.y0.as<float2>());
+    if (ws.cdf_d != d) {   // d / out is formed once per damping factor
+        k_link_weight<<<l.ew_blocks, 256, 0, s>>>(g->out_info.as<int32_t>(), g->n, d, ws.cdf.as<float2>());
+        ws.cdf_d = d;
+    }
+    k_scale<<<l.ew_blocks, 256, 0, s>>>(ws.H.as<double>(), ws.cdf.as<float2>(), g->n, ws.y0.as<float2>());
     if (g->n_heavy_in_chunks > 0) {
         int blocks = (int)((g->n_heavy_in_chunks + 7) / 8);
         if (blocks > g->dev.sms * 8) blocks = g->dev.sms * 8;
@@ -1195,6 +1206,7 @@ di_status power_iter(di_graph *g, const double *B, double d, double tol, int32_t
         k_pi_init<<<l.ew_blocks, 256, 0, s>>>(ws.B.as<double>(), g->out_info.as<int32_t>(), g->n, d,
                                               ws.Bdf.as<float2>(), ws.cdf.as<float2>(), ws.Xdf.as<float2>(),
                                               ws.y0.as<float2>());
+        ws.cdf_d = d;
         if (!ws.pi_exec) build_pi_graph<T>(g, l);
         DI_CHECK_CUDA(cudaGraphLaunch(ws.pi_exec, s));
         k_df_to_double<<<l.ew_blocks, 256, 0, s>>>(ws.Xdf.as<float2>(), g->n, ws.H.as<double>());
