@@ -55,6 +55,20 @@ def world():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def aggregate(dist, total_ms: float, pushed: float, launches: int, device=None):
+    """Whole-job numbers over the ranks of a replica run: the slowest rank's time and the summed
+    pushed links and kernel launches (each rank solves its own replica). Without a process
+    group the rank's own numbers are returned."""
+    if dist is None:
+        return total_ms, pushed, launches
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([float(pushed), float(launches)], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p[0].item()), int(p[1].item())
+
+
 # ------------------------------------------------------------------------------------------
 # clocks during the timed region
 # ------------------------------------------------------------------------------------------
@@ -180,7 +194,9 @@ def run_reference(args):
         "impl": "reference", "metric": "GTEPS (DI-SOP, N=10M, tol 1e-8)", "value": value, "unit": "GTEPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: N={n}, L={og.L}, d={D}", "step": "one oracle DI-SOP cycle from F=B"},
+        "config": {"workload": f"{WORKLOAD}: N={n}, L={og.L}, d={D}, tol={TOL}, B=(1-d)/N",
+                   "step": "one oracle DI-SOP cycle from F=B (bounded sample of the solve)", "fluid": "f64",
+                   "history": "f64"},
         "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                          "sample": "one sequential DI-SOP cycle per step on the full 10M-node graph"},
         "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -390,12 +406,7 @@ def run_gpu(args):
     total_ms = sum(step_ms)
     pushed = sum(i["pushed_edges"] for i in infos)
     launches = sum(i["kernel_launches"] for i in infos)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        p = torch.tensor([float(pushed), float(launches)], dtype=torch.float64, device=dev)
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-        total_ms, pushed, launches = float(t.item()), float(p[0].item()), int(p[1].item())
+    total_ms, pushed, launches = aggregate(dist, total_ms, pushed, launches, device=dev)
     value = pushed / (total_ms * 1e-3) / 1e9
 
     # end to end through the public API with host buffers: B from pinned host memory, X back

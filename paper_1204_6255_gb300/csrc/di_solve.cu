@@ -198,7 +198,7 @@ constexpr int kSelItems = 8;
 constexpr int kSelChunk = 256 * kSelItems;
 
 template <class T>
-__global__ void __launch_bounds__(256) k_select(T *F, double *H, const int32_t *out_info, const int64_t *rp_out,
+__global__ void __launch_bounds__(256, 5) k_select(T *F, double *H, const int32_t *out_info, const int64_t *rp_out,
                                                 int32_t n, SolveCtl *ctl, int32_t *front_id, T *front_s,
                                                 int64_t *front_beg, int32_t *front_deg, int32_t *heavy_id,
                                                 T *heavy_s, int4 *chunks) {
