@@ -466,6 +466,14 @@ __global__ void k_hub_finalize(const unsigned long long *slots, int32_t *ids) {
     if (i < kHubSlots) ids[i] = slots[i] ? (int32_t)(uint32_t)(slots[i] & 0xffffffffu) : -1;
 }
 
+// the push kernels' copy of the link targets: bit 31 marks a target that owns its hub slot
+__global__ void k_mark_hub_links(const int32_t *col_out, int64_t L, const int32_t *hub_ids, int32_t *col_push) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j = col_out[k];
+        col_push[k] = __ldg(hub_ids + hub_slot(j)) == j ? (int32_t)((uint32_t)j | 0x80000000u) : j;
+    }
+}
+
 static int ceil_log2(int64_t x) {
     int b = 0;
     while ((int64_t(1) << b) < x) b++;
@@ -607,6 +615,10 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
                                                          slots.as<unsigned long long>());
         g->hub_ids.ensure(sizeof(int32_t) * kHubSlots);
         k_hub_finalize<<<(kHubSlots + 255) / 256, 256, 0, s>>>(slots.as<unsigned long long>(), g->hub_ids.as<int32_t>());
+        g->col_push.ensure(sizeof(int32_t) * (size_t)(L > 0 ? L : 1));
+        if (L > 0)
+            k_mark_hub_links<<<grid_for(L, 256, dev), 256, 0, s>>>(g->col_out.as<int32_t>(), L, g->hub_ids.as<int32_t>(),
+                                                                 g->col_push.as<int32_t>());
         DI_CHECK_CUDA(cudaGetLastError());
         DI_CHECK_CUDA(cudaStreamSynchronize(s));
     }

@@ -120,19 +120,26 @@ struct SolveCtl {
     int32_t sweeps;
     int32_t force_cyc;        // next selection ignores the DI-SOP threshold
     int32_t last_selected;    // nodes selected by the latest sweep, -1 before the first
-    int32_t front_count;      // light frontier entries written by the latest selection
+    // light frontier entries (low 40 bits) and frontier segments (high 24 bits) written by the
+    // latest selection: one atomic reserves both for a select chunk
+    unsigned long long front_chunks;
     int32_t heavy_count;      // heavy frontier entries written by the latest selection
     int32_t batch_next;       // dynamic work counter of the push kernel
     int32_t done;             // 1 when the stop test has fired
     int32_t status;           // 0 ok; 1 bad right-hand side
     uint32_t ticket;          // last-block-done counter of the reductions
     int32_t body_runs;        // executions of the WHILE body (kernel-launch accounting)
-    int32_t chunk_count;      // frontier segments (one per select chunk with entries)
     int32_t chunk_next;       // dynamic work counter over the segments
     unsigned long long front_total;  // frontier entries over all sweeps
 };
 
 // Fixed tuning of the single-RHS kernels.
+constexpr int kFrontBits = 40;
+__host__ __device__ inline int32_t front_entries(unsigned long long fc) {
+    return (int32_t)(fc & ((1ull << kFrontBits) - 1));
+}
+__host__ __device__ inline int32_t front_segments(unsigned long long fc) { return (int32_t)(fc >> kFrontBits); }
+
 constexpr int kPushHeavy = 4096;    // out-degree above which a node's edges are split over warps
 constexpr int kPullHeavy = 8192;    // in-degree above which a row's edges are split over warps
 constexpr int kPullChunk = 4096;    // edges per heavy-row chunk of the pull
@@ -194,6 +201,7 @@ struct di_graph {
     di::DevBuf heavy_in_partial;   // float2[n_heavy_in_chunks] (double-float partial sums)
     int64_t n_heavy_out = 0;       // nodes with out-degree > kPushHeavy
     di::DevBuf hub_ids;            // int32[kHubSlots]: hub node per hash slot, -1 when empty
+    di::DevBuf col_push;           // int32[L]: col_out with bit 31 set on links into a hub
     std::mutex mu;                 // serialises use of the workspaces
     di::Workspace ws;
     di::BatchWorkspace *bws = nullptr;   // batched solves (created on first use)

@@ -111,11 +111,10 @@ __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl,
         int sel = ctl->last_selected;
         ctl->force_cyc = (sel == 0 && tot > 0.0) ? 1 : 0;   // a DI-SOP sweep found no node
         ctl->last_selected = 0;
-        ctl->front_total += (unsigned long long)(ctl->front_count + ctl->heavy_count);
-        ctl->front_count = 0;
+        ctl->front_total += (unsigned long long)(front_entries(ctl->front_chunks) + ctl->heavy_count);
+        ctl->front_chunks = 0;
         ctl->heavy_count = 0;
         ctl->batch_next = 0;
-        ctl->chunk_count = 0;
         ctl->chunk_next = 0;
         if (set_cond) ctl->body_runs++;
         bool cont = ctl->status == 0 && tot > ctl->tol && ctl->sweeps < ctl->max_sweeps;
@@ -137,9 +136,11 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
     asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
+// link indices: each lane reads a run of consecutive links, so the line is kept in L1 for the
+// lane's next reads, and marked for early eviction in L2
 __device__ __forceinline__ int32_t ld_stream(const int32_t *p, uint64_t pol) {
     int32_t v;
-    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    asm volatile("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
     return v;
 }
 __device__ __forceinline__ void red_keep_v4(float *p, float4 v, uint64_t pol) {
@@ -196,12 +197,14 @@ __device__ __forceinline__ bool selects(double f, int32_t o, bool cyc, double th
 // row start and degree, so the push needs no dependent row-pointer gather.
 constexpr int kSelItems = 8;
 constexpr int kSelChunk = 256 * kSelItems;
+constexpr int kSelMinBlocks = 3;
 
 template <class T>
-__global__ void __launch_bounds__(256, 5) k_select(T *F, double *H, const int32_t *out_info, const int64_t *rp_out,
-                                                int32_t n, SolveCtl *ctl, int32_t *front_id, T *front_s,
-                                                int64_t *front_beg, int32_t *front_deg, int32_t *heavy_id,
-                                                T *heavy_s, int4 *chunks) {
+__global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, const int32_t *out_info,
+                                                            const int64_t *rp_out, int32_t n, SolveCtl *ctl,
+                                                            int32_t *front_id, T *front_s, int64_t *front_beg,
+                                                            int32_t *front_deg, int32_t *heavy_id, T *heavy_s,
+                                                            int4 *chunks) {
     __shared__ double scratch[32];
     __shared__ unsigned long long scratch_u[32];
     __shared__ int wcount[kSelItems][8];
@@ -218,38 +221,62 @@ __global__ void __launch_bounds__(256, 5) k_select(T *F, double *H, const int32_
     double e_loc = 0.0;
     unsigned long long pushed = 0, visited = 0;
     for (int64_t base = (int64_t)blockIdx.x * kSelChunk; base < n; base += (int64_t)gridDim.x * kSelChunk) {
+        // The loads of a chunk are issued in two waves before any store, so each thread keeps
+        // every item's loads in flight at once: first F and the degree of all items, then H and
+        // the row start of the selected ones.
+        T f[kSelItems];
+        int32_t info[kSelItems];
+#pragma unroll
+        for (int j = 0; j < kSelItems; j++) {
+            const int64_t i = base + j * 256 + threadIdx.x;
+            f[j] = (T)0;
+            info[j] = 0;
+            if (i < n) {
+                f[j] = ld_keep(F + i, keep);
+                info[j] = __ldcs(out_info + i);
+            }
+        }
+        unsigned sel = 0;
+#pragma unroll
+        for (int j = 0; j < kSelItems; j++)
+            if (base + j * 256 + threadIdx.x < n && selects(f[j], info[j] & 0x7fffffff, cyc, thr, thr_f)) sel |= 1u << j;
+        double h[kSelItems];
+        int64_t rb[kSelItems];
+#pragma unroll
+        for (int j = 0; j < kSelItems; j++) {
+            const int64_t i = base + j * 256 + threadIdx.x;
+            h[j] = 0.0;
+            rb[j] = 0;
+            if (sel >> j & 1u) {
+                h[j] = __ldcs(H + i);
+                rb[j] = __ldcs(rp_out + i);
+            }
+        }
         unsigned ballots[kSelItems];
         T shares[kSelItems];
-        int32_t degs[kSelItems];
 #pragma unroll
         for (int j = 0; j < kSelItems; j++) {
             const int64_t i = base + j * 256 + threadIdx.x;
             bool light = false, heavy = false;
             T share = (T)0;
-            int32_t o = 0;
-            if (i < n) {
-                const T f = ld_keep(F + i, keep);
-                const int32_t info = __ldcs(out_info + i);
-                o = info & 0x7fffffff;
-                const bool lp = info < 0;
-                if (selects(f, o, cyc, thr, thr_f)) {
-                    st_keep(F + i, (T)0, keep);
-                    double t;
-                    visit_math(f, o, lp, d, d_f, t, share);
-                    __stcs(H + i, __ldcs(H + i) + t);
-                    visited++;
-                    pushed += (unsigned long long)o;
-                    if (o == 0) {
-                        if (sizeof(T) == 4) e_run += (float)t; else e_loc += t;
-                    } else if (o > kPushHeavy) {
-                        heavy = true;
-                    } else if (o - (lp ? 1 : 0) > 0) {
-                        light = true;
-                    }
+            const int32_t o = info[j] & 0x7fffffff;
+            if (sel >> j & 1u) {
+                const bool lp = info[j] < 0;
+                st_keep(F + i, (T)0, keep);
+                double t;
+                visit_math(f[j], o, lp, d, d_f, t, share);
+                __stcs(H + i, h[j] + t);
+                visited++;
+                pushed += (unsigned long long)o;
+                if (o == 0) {
+                    if (sizeof(T) == 4) e_run += (float)t; else e_loc += t;
+                } else if (o > kPushHeavy) {
+                    heavy = true;
+                } else if (o - (lp ? 1 : 0) > 0) {
+                    light = true;
                 }
             }
             shares[j] = share;
-            degs[j] = o;
             ballots[j] = __ballot_sync(kFull, light);
             if (lane == 0) wcount[j][warp] = __popc(ballots[j]);
             // heavy nodes are rare: one atomic per warp that has any
@@ -275,8 +302,12 @@ __global__ void __launch_bounds__(256, 5) k_select(T *F, double *H, const int32_
                     wcount[j][w] = run;
                     run += c;
                 }
-            chunk_base = run ? atomicAdd(&ctl->front_count, run) : 0;
-            if (run) chunks[atomicAdd(&ctl->chunk_count, 1)] = make_int4((int)base, chunk_base, run, 0);
+            chunk_base = 0;
+            if (run) {
+                const unsigned long long fc = atomicAdd(&ctl->front_chunks, (1ull << kFrontBits) | (unsigned)run);
+                chunk_base = front_entries(fc);
+                chunks[front_segments(fc)] = make_int4((int)base, chunk_base, run, 0);
+            }
         }
         __syncthreads();
         const int cb = chunk_base;
@@ -287,8 +318,8 @@ __global__ void __launch_bounds__(256, 5) k_select(T *F, double *H, const int32_
                 const int64_t i = base + j * 256 + threadIdx.x;
                 __stcs(front_id + p, (int32_t)i);
                 __stcs(front_s + p, shares[j]);
-                __stcs(front_beg + p, (long long)__ldcs(rp_out + i));
-                __stcs(front_deg + p, degs[j]);
+                __stcs(front_beg + p, (long long)rb[j]);
+                __stcs(front_deg + p, info[j] & 0x7fffffff);
             }
         }
         __syncthreads();
@@ -348,7 +379,7 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
         }
     }
 
-    const int count = ctl->front_count;
+    const int count = front_entries(ctl->front_chunks);
     for (int64_t b0 = gwarp * 32; b0 < count; b0 += nwarps * 32) {
         const int64_t idx = b0 + lane;
         int deg = 0;
@@ -401,37 +432,31 @@ constexpr int kHalo = 1024;
 constexpr int kWin = kSelChunk + 2 * kHalo;     // 4096 floats, 16 KB
 constexpr int kWinMinEntries = 24;              // sparser segments push link by link
 
-__global__ void __launch_bounds__(256, 4) k_push_win(const int32_t *__restrict__ front_id, const float *__restrict__ front_s,
+__global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__ front_id, const float *__restrict__ front_s,
                                                   const int64_t *__restrict__ front_beg,
                                                   const int32_t *__restrict__ front_deg,
                                                   const int32_t *__restrict__ heavy_id, const float *__restrict__ heavy_s,
                                                   const int64_t *__restrict__ rp_out,
-                                                  const int32_t *__restrict__ col_out, const int4 *__restrict__ chunks,
+                                                  const int32_t *__restrict__ col_push, const int4 *__restrict__ chunks,
                                                   const int32_t *__restrict__ hub_ids, float *F, SolveCtl *ctl) {
     __shared__ __align__(16) float s_win[kWin];
-    __shared__ int32_t s_hub[kHubSlots];     // hub node of each slot (-1: none)
     __shared__ float s_hacc[kHubSlots];      // this block's pending additions to the hubs
     __shared__ int s_off[8][33];
-    __shared__ int64_t s_beg[8][32];
-    __shared__ int32_t s_u[8][32];
-    __shared__ float s_s[8][32];
+    // per entry of a warp's batch: {row start - link offset (int64), source id, share}
+    __shared__ int4 s_rec[8][32];
     __shared__ int s_chunk, s_batch;
     if (ctl->done) return;
     const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int q = tid; q < kHubSlots; q += 256) {
-        s_hub[q] = hub_ids[q];
-        s_hacc[q] = 0.f;
-    }
+    for (int q = tid; q < kHubSlots; q += 256) s_hacc[q] = 0.f;
     __syncthreads();
-    // a link to a far target: hubs (high in-degree nodes) collect in shared memory, the rest
-    // goes to F directly
-    auto far_add = [&](int32_t j, float v) {
-        const int slot = hub_slot(j);
-        if (s_hub[slot] == j) atomicAdd(&s_hacc[slot], v);
-        else red_keep(&F[j], v, keep);
+    // a link to a far target (jr: target id with bit 31 set when the target is a hub): hubs
+    // (high in-degree nodes) collect in shared memory, the rest goes to F directly
+    auto far_add = [&](int32_t jr, float v) {
+        if (jr < 0) atomicAdd(&s_hacc[hub_slot(jr & 0x7fffffff)], v);
+        else red_keep(&F[jr], v, keep);
     };
 
     // nodes with more than kPushHeavy links: their links in chunks over all warps
@@ -445,13 +470,13 @@ __global__ void __launch_bounds__(256, 4) k_push_win(const int32_t *__restrict__
         for (int64_t c = gwarp; c < nch; c += nwarps) {
             const int64_t cb = b + c * kChunk, ce = min(cb + kChunk, e);
             for (int64_t k = cb + lane; k < ce; k += 32) {
-                const int32_t j = ld_stream(col_out + k, stream);
-                if (j != u) far_add(j, sh);
+                const int32_t jr = ld_stream(col_push + k, stream);
+                if ((jr & 0x7fffffff) != u) far_add(jr, sh);
             }
         }
     }
 
-    const int nchunks = ctl->chunk_count;
+    const int nchunks = front_segments(ctl->front_chunks);
     for (;;) {
         if (tid == 0) {
             s_chunk = atomicAdd(&ctl->chunk_next, 1);
@@ -476,54 +501,58 @@ __global__ void __launch_bounds__(256, 4) k_push_win(const int32_t *__restrict__
             if (b0 >= clen) break;
             const int idx = cstart + b0 + lane;
             int deg = 0;
+            int32_t eu = 0;
+            float es = 0.f;
+            int64_t ebeg = 0;
             if (b0 + lane < clen) {
                 deg = __ldcs(front_deg + idx);
-                s_u[w][lane] = __ldcs(front_id + idx);
-                s_s[w][lane] = __ldcs(front_s + idx);
-                s_beg[w][lane] = (int64_t)__ldcs(front_beg + idx);
+                eu = __ldcs(front_id + idx);
+                es = __ldcs(front_s + idx);
+                ebeg = (int64_t)__ldcs(front_beg + idx);
             }
             const int inc = warp_inclusive_scan(deg);
             const int total = __shfl_sync(kFull, inc, 31);
+            const int64_t rbase = ebeg - (inc - deg);   // link e of the batch sits at col_push[rbase + e]
             s_off[w][lane] = inc - deg;
             if (lane == 31) s_off[w][32] = total;
+            s_rec[w][lane] = make_int4((int)(uint32_t)(uint64_t)rbase, (int)((uint64_t)rbase >> 32), eu, __float_as_int(es));
             __syncwarp();
             for (int e0 = lane * kPushVT; e0 < total; e0 += 32 * kPushVT) {
                 int k = 0;   // last entry with s_off[k] <= e0
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1)
                     if (s_off[w][k + step] <= e0) k += step;
-                // the owner's row in registers; every entry has at least one link, so moving
+                // the owner's record in registers; every entry has at least one link, so moving
                 // to the next link crosses at most one entry boundary
-                int off_k = s_off[w][k], next = s_off[w][k + 1];
-                int64_t row = s_beg[w][k] - off_k;
-                int32_t u = s_u[w][k];
-                float sv = s_s[w][k];
-                int32_t j[kPushVT], uu[kPushVT];
+                int next = s_off[w][k + 1];
+                int4 rec = s_rec[w][k];
+                int32_t jr[kPushVT], uu[kPushVT];
                 float ss[kPushVT];
 #pragma unroll
                 for (int v = 0; v < kPushVT; v++) {
                     const int e = e0 + v;
-                    j[v] = -1;
+                    jr[v] = 0;
+                    uu[v] = 0;   // target 0 and source 0 reads as a loop link: skipped
+                    ss[v] = 0.f;
                     if (e < total) {
                         if (e >= next) {
                             ++k;
-                            off_k = next;
                             next = s_off[w][k + 1];
-                            row = s_beg[w][k] - off_k;
-                            u = s_u[w][k];
-                            sv = s_s[w][k];
+                            rec = s_rec[w][k];
                         }
-                        j[v] = ld_stream(col_out + row + e, stream);
-                        uu[v] = u;
-                        ss[v] = sv;
+                        const int64_t row = (int64_t)(((uint64_t)(uint32_t)rec.y << 32) | (uint32_t)rec.x);
+                        jr[v] = ld_stream(col_push + row + e, stream);
+                        uu[v] = rec.z;
+                        ss[v] = __int_as_float(rec.w);
                     }
                 }
 #pragma unroll
                 for (int v = 0; v < kPushVT; v++) {
-                    if (j[v] < 0 || j[v] == uu[v]) continue;
-                    const unsigned off = (unsigned)(j[v] - lo);
+                    const int32_t j = jr[v] & 0x7fffffff;
+                    if (j == uu[v]) continue;
+                    const unsigned off = (unsigned)(j - lo);
                     if (use_win && off < (unsigned)kWin) atomicAdd(&s_win[off], ss[v]);
-                    else far_add(j[v], ss[v]);
+                    else far_add(jr[v], ss[v]);
                 }
             }
             __syncwarp();
@@ -539,7 +568,7 @@ __global__ void __launch_bounds__(256, 4) k_push_win(const int32_t *__restrict__
     }
     // one atomic per hub that received something from this block
     for (int q = tid; q < kHubSlots; q += 256)
-        if (s_hacc[q] != 0.f) red_keep(&F[s_hub[q]], s_hacc[q], keep);
+        if (s_hacc[q] != 0.f) red_keep(&F[__ldg(hub_ids + q)], s_hacc[q], keep);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -879,7 +908,8 @@ static Launch launch_shape(const di_graph *g) {
     l.pull_blocks = sms * (occ > 0 ? occ : 1);
     const int64_t n = g->n;
     auto cap = [&](int64_t want, int64_t lim) { return (int)(want < 1 ? 1 : (want < lim ? want : lim)); };
-    l.sel_blocks = cap((n + kSelChunk - 1) / kSelChunk, (int64_t)sms * 8);
+    DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select<T>, 256, 0));
+    l.sel_blocks = cap((n + kSelChunk - 1) / kSelChunk, (int64_t)sms * (occ > 0 ? occ : 1));
     l.red_blocks = cap((n + 255) / 256, (int64_t)(kReduceBlocks < sms * 4 ? kReduceBlocks : sms * 4));
     l.ew_blocks = cap((n + 255) / 256, (int64_t)sms * 8);
     // a pull block never needs more row groups than exist
@@ -937,7 +967,7 @@ static void launch_sweep_body(di_graph *g, const Launch &l, cudaStream_t s, cuda
             k_push_win<<<l.win_blocks, 256, 0, s>>>(
                 ws.front_id.as<int32_t>(), ws.front_s.as<float>(), ws.front_beg.as<int64_t>(),
                 ws.front_deg.as<int32_t>(), ws.heavy_id.as<int32_t>(), ws.heavy_s.as<float>(), g->rp_out.as<int64_t>(),
-                g->col_out.as<int32_t>(), ws.chunks.as<int4>(), g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl);
+                g->col_push.as<int32_t>(), ws.chunks.as<int4>(), g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl);
         } else {
             k_push<T><<<l.push_blocks, 256, 0, s>>>(ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
                                                     ws.front_beg.as<int64_t>(), ws.front_deg.as<int32_t>(),

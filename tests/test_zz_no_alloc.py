@@ -17,6 +17,14 @@ from gpu_util import lib
 
 pytestmark = pytest.mark.gpu
 TOL_REL = 1e-6
+# F* = B + P.H - H is a difference of terms of size ||B||_1 + ||H||_1 that cancel to ~tol; its link
+# sums are taken in double-float (unit roundoff 2^-44), so the computed F* carries an absolute
+# error of about 2^-44 times the terms it cancels, however small F* itself is
+DF_EPS = 2.0 ** -44
+
+
+def _slack(B, X):
+    return DF_EPS * (np.abs(B).sum() + 2.0 * np.abs(X).sum())
 
 
 def _setup():
@@ -45,10 +53,12 @@ def test_noalloc_residual_matches_solve_twice():
         di.di_residual_noalloc(n, rp_in, col_in, out_deg, Bt, d, X, norm, Fstar_out=Fs)
         torch.cuda.synchronize()
         got = float(norm.item())
-        assert abs(got - info["residual_l1"]) <= TOL_REL * info["residual_l1"], (got, info["residual_l1"])
-        ref, ref_norm = oracle.residual(og, B, d, X.cpu().numpy())
-        assert abs(got - ref_norm) <= TOL_REL * ref_norm
-        assert np.abs(Fs.cpu().numpy() - ref).sum() <= TOL_REL * ref_norm
+        Xh = X.cpu().numpy()
+        slack = _slack(B, Xh)
+        assert abs(got - info["residual_l1"]) <= max(TOL_REL * info["residual_l1"], slack), (got, info["residual_l1"])
+        ref, ref_norm = oracle.residual(og, B, d, Xh)
+        assert abs(got - ref_norm) <= max(TOL_REL * ref_norm, slack)
+        assert np.abs(Fs.cpu().numpy() - ref).sum() <= max(TOL_REL * ref_norm, slack)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
