@@ -149,7 +149,7 @@ constexpr int kHubSlots = 2048;     // shared-memory hub cache of the push kerne
 // Per-graph state for single-RHS solves and power iteration.
 struct Workspace {
     int fluid = -1;                 // di_fluid the buffers were sized for
-    DevBuf F, H, B, front_id, front_s, front_beg, front_deg, heavy_id, heavy_s, partials, ctl, y0, y1, chunks;
+    DevBuf F, H, B, front_id, front_s, heavy_id, heavy_s, partials, ctl, y0, y1, chunks;
     DevBuf Bdf, cdf, Xdf;           // power iteration in double-float: B, d/out, X
     double cdf_d = -1.0;            // damping factor cdf currently holds (-1: none)
     cudaGraphExec_t sweep_exec = nullptr;   // reduce -> WHILE{select, push, reduce}

@@ -193,18 +193,16 @@ __device__ __forceinline__ bool selects(double f, int32_t o, bool cyc, double th
 
 // Nodes are visited in chunks of kSelChunk consecutive ids per block iteration; the frontier
 // entries of a chunk are compacted with one atomic per chunk, so the frontier is id-sorted
-// within each chunk (the push then walks neighbouring rows together). Every entry carries its
-// row start and degree, so the push needs no dependent row-pointer gather.
+// within each chunk (the push then walks neighbouring rows together). An entry is the node id
+// and its share (8 bytes); the push reads the row bounds itself, from neighbouring row pointers.
 constexpr int kSelItems = 8;
 constexpr int kSelChunk = 256 * kSelItems;
-constexpr int kSelMinBlocks = 3;
+constexpr int kSelMinBlocks = 4;
 
 template <class T>
 __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, const int32_t *out_info,
-                                                            const int64_t *rp_out, int32_t n, SolveCtl *ctl,
-                                                            int32_t *front_id, T *front_s, int64_t *front_beg,
-                                                            int32_t *front_deg, int32_t *heavy_id, T *heavy_s,
-                                                            int4 *chunks) {
+                                                            int32_t n, SolveCtl *ctl, int32_t *front_id, T *front_s,
+                                                            int32_t *heavy_id, T *heavy_s, int4 *chunks) {
     __shared__ double scratch[32];
     __shared__ unsigned long long scratch_u[32];
     __shared__ int wcount[kSelItems][8];
@@ -222,8 +220,8 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
     unsigned long long pushed = 0, visited = 0;
     for (int64_t base = (int64_t)blockIdx.x * kSelChunk; base < n; base += (int64_t)gridDim.x * kSelChunk) {
         // The loads of a chunk are issued in two waves before any store, so each thread keeps
-        // every item's loads in flight at once: first F and the degree of all items, then H and
-        // the row start of the selected ones.
+        // every item's loads in flight at once: first F and the degree of all items, then H of
+        // the selected ones.
         T f[kSelItems];
         int32_t info[kSelItems];
 #pragma unroll
@@ -241,16 +239,11 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
         for (int j = 0; j < kSelItems; j++)
             if (base + j * 256 + threadIdx.x < n && selects(f[j], info[j] & 0x7fffffff, cyc, thr, thr_f)) sel |= 1u << j;
         double h[kSelItems];
-        int64_t rb[kSelItems];
 #pragma unroll
         for (int j = 0; j < kSelItems; j++) {
             const int64_t i = base + j * 256 + threadIdx.x;
             h[j] = 0.0;
-            rb[j] = 0;
-            if (sel >> j & 1u) {
-                h[j] = __ldcs(H + i);
-                rb[j] = __ldcs(rp_out + i);
-            }
+            if (sel >> j & 1u) h[j] = __ldcs(H + i);
         }
         unsigned ballots[kSelItems];
         T shares[kSelItems];
@@ -318,8 +311,6 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                 const int64_t i = base + j * 256 + threadIdx.x;
                 __stcs(front_id + p, (int32_t)i);
                 __stcs(front_s + p, shares[j]);
-                __stcs(front_beg + p, (long long)rb[j]);
-                __stcs(front_deg + p, info[j] & 0x7fffffff);
             }
         }
         __syncthreads();
@@ -347,8 +338,6 @@ constexpr int kPushVT = 8;
 
 template <class T>
 __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_id, const T *__restrict__ front_s,
-                                              const int64_t *__restrict__ front_beg,
-                                              const int32_t *__restrict__ front_deg,
                                               const int32_t *__restrict__ heavy_id, const T *__restrict__ heavy_s,
                                               const int64_t *__restrict__ rp_out, const int32_t *__restrict__ col_out,
                                               T *F, SolveCtl *ctl) {
@@ -384,10 +373,12 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
         const int64_t idx = b0 + lane;
         int deg = 0;
         if (idx < count) {
-            deg = __ldcs(front_deg + idx);
-            s_u[w][lane] = __ldcs(front_id + idx);
+            const int32_t u = __ldcs(front_id + idx);
+            const int64_t rb = __ldg(rp_out + u);
+            deg = (int)(__ldg(rp_out + u + 1) - rb);
+            s_u[w][lane] = u;
             s_s[w][lane] = __ldcs(front_s + idx);
-            s_beg[w][lane] = (int64_t)__ldcs(front_beg + idx);
+            s_beg[w][lane] = rb;
         }
         const int inc = warp_inclusive_scan(deg);
         const int total = __shfl_sync(kFull, inc, 31);
@@ -433,8 +424,6 @@ constexpr int kWin = kSelChunk + 2 * kHalo;     // 4096 floats, 16 KB
 constexpr int kWinMinEntries = 24;              // sparser segments push link by link
 
 __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__ front_id, const float *__restrict__ front_s,
-                                                  const int64_t *__restrict__ front_beg,
-                                                  const int32_t *__restrict__ front_deg,
                                                   const int32_t *__restrict__ heavy_id, const float *__restrict__ heavy_s,
                                                   const int64_t *__restrict__ rp_out,
                                                   const int32_t *__restrict__ col_push, const int4 *__restrict__ chunks,
@@ -505,10 +494,10 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
             float es = 0.f;
             int64_t ebeg = 0;
             if (b0 + lane < clen) {
-                deg = __ldcs(front_deg + idx);
                 eu = __ldcs(front_id + idx);
                 es = __ldcs(front_s + idx);
-                ebeg = (int64_t)__ldcs(front_beg + idx);
+                ebeg = __ldg(rp_out + eu);
+                deg = (int)(__ldg(rp_out + eu + 1) - ebeg);
             }
             const int inc = warp_inclusive_scan(deg);
             const int total = __shfl_sync(kFull, inc, 31);
@@ -931,8 +920,6 @@ static void ensure_workspace(di_graph *g) {
     ws.B.ensure(sizeof(double) * n);
     ws.front_id.ensure(sizeof(int32_t) * n);
     ws.front_s.ensure(sizeof(T) * n);
-    ws.front_beg.ensure(sizeof(int64_t) * n);
-    ws.front_deg.ensure(sizeof(int32_t) * n);
     ws.heavy_id.ensure(sizeof(int32_t) * (size_t)(g->n_heavy_out + 1));
     ws.heavy_s.ensure(sizeof(T) * (size_t)(g->n_heavy_out + 1));
     ws.partials.ensure(sizeof(double) * kReduceBlocks);
@@ -956,21 +943,18 @@ static void launch_sweep_body(di_graph *g, const Launch &l, cudaStream_t s, cuda
     KernelClock none(false, s);
     KernelClock &c = kc ? *kc : none;
     c.run(KC_SELECT, 1, [&] {
-        k_select<T><<<l.sel_blocks, 256, 0, s>>>(ws.F.as<T>(), ws.H.as<double>(), g->out_info.as<int32_t>(),
-                                                  g->rp_out.as<int64_t>(), g->n, ctl, ws.front_id.as<int32_t>(),
-                                                  ws.front_s.as<T>(), ws.front_beg.as<int64_t>(),
-                                                  ws.front_deg.as<int32_t>(), ws.heavy_id.as<int32_t>(),
-                                                  ws.heavy_s.as<T>(), ws.chunks.as<int4>());
+        k_select<T><<<l.sel_blocks, 256, 0, s>>>(ws.F.as<T>(), ws.H.as<double>(), g->out_info.as<int32_t>(), g->n,
+                                                  ctl, ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
+                                                  ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(), ws.chunks.as<int4>());
     });
     c.run(KC_PUSH, 1, [&] {
         if (sizeof(T) == 4) {
             k_push_win<<<l.win_blocks, 256, 0, s>>>(
-                ws.front_id.as<int32_t>(), ws.front_s.as<float>(), ws.front_beg.as<int64_t>(),
-                ws.front_deg.as<int32_t>(), ws.heavy_id.as<int32_t>(), ws.heavy_s.as<float>(), g->rp_out.as<int64_t>(),
+                ws.front_id.as<int32_t>(), ws.front_s.as<float>(), ws.heavy_id.as<int32_t>(), ws.heavy_s.as<float>(),
+                g->rp_out.as<int64_t>(),
                 g->col_push.as<int32_t>(), ws.chunks.as<int4>(), g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl);
         } else {
             k_push<T><<<l.push_blocks, 256, 0, s>>>(ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
-                                                    ws.front_beg.as<int64_t>(), ws.front_deg.as<int32_t>(),
                                                     ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(),
                                                     g->rp_out.as<int64_t>(), g->col_out.as<int32_t>(), ws.F.as<T>(),
                                                     ctl);
