@@ -206,25 +206,51 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
     float e_run = 0.f;
     unsigned long long pushed = 0, visited = 0, colv = 0;
     for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += (int64_t)gridDim.x * 256) {
-#pragma unroll 4
-        for (int j = 0; j < T; j++) {
-            const int64_t i = base + j * kNodesPerStep + tid / T;
-            bool sel = false, pushable = false;
-            int32_t o = 0;
-            float share = 0.f;
-            if (i < n) {
-                const int64_t idx = i * T + c;
-                const float f = F[idx];
-                const int32_t info = out_info[i];
-                o = info & 0x7fffffff;
-                const bool lp = info < 0;
-                sel = act && (cyc ? (f != 0.f) : (fabsf(f) > thr_f * (float)o));
+        // sub-steps in groups of kGroup: the F and degree loads of a group are issued before any
+        // of its stores, then H of the selected entries, so the loads of a group overlap
+        constexpr int kGroup = T < 8 ? T : 8;
+        for (int j0 = 0; j0 < T; j0 += kGroup) {
+            float f[kGroup];
+            int32_t info[kGroup];
+#pragma unroll
+            for (int q = 0; q < kGroup; q++) {
+                const int64_t i = base + (j0 + q) * kNodesPerStep + tid / T;
+                f[q] = 0.f;
+                info[q] = 0;
+                if (i < n) {
+                    f[q] = F[i * T + c];
+                    info[q] = out_info[i];
+                }
+            }
+            unsigned selm = 0;
+#pragma unroll
+            for (int q = 0; q < kGroup; q++) {
+                const int64_t i = base + (j0 + q) * kNodesPerStep + tid / T;
+                const float o_f = (float)(info[q] & 0x7fffffff);
+                if (i < n && act && (cyc ? (f[q] != 0.f) : (fabsf(f[q]) > thr_f * o_f))) selm |= 1u << q;
+            }
+            double h[kGroup];
+#pragma unroll
+            for (int q = 0; q < kGroup; q++) {
+                const int64_t i = base + (j0 + q) * kNodesPerStep + tid / T;
+                h[q] = (selm >> q & 1u) ? H[i * T + c] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < kGroup; q++) {
+                const int j = j0 + q;
+                const int64_t i = base + j * kNodesPerStep + tid / T;
+                const bool sel = selm >> q & 1u;
+                bool pushable = false;
+                const int32_t o = info[q] & 0x7fffffff;
+                float share = 0.f;
                 if (sel) {
+                    const int64_t idx = i * T + c;
+                    const bool lp = info[q] < 0;
                     F[idx] = 0.f;
                     // FP32 transit and share; FP64 only for H += transit
                     const float of = (float)o;
-                    const float tf = lp ? f * of / (of - d_f) : f;
-                    H[idx] += (double)tf;
+                    const float tf = lp ? f[q] * of / (of - d_f) : f[q];
+                    H[idx] = h[q] + (double)tf;
                     colv++;
                     if (o == 0) e_run += tf;
                     else {
@@ -232,18 +258,18 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
                         pushable = (o - (lp ? 1 : 0)) > 0;
                     }
                 }
-            }
-            const unsigned bsel = __ballot_sync(kFull, sel) & gmask;
-            const unsigned bpush = __ballot_sync(kFull, pushable) & gmask;
-            if (leader && bsel) {
-                visited++;
-                pushed += (unsigned long long)o;
-            }
-            const unsigned lb = __ballot_sync(kFull, leader && bpush != 0);
-            s_share[j][tid] = share;
-            if (lane == 0) {
-                s_lbs[j][warp] = lb;
-                wcount[j][warp] = __popc(lb);
+                const unsigned bsel = __ballot_sync(kFull, sel) & gmask;
+                const unsigned bpush = __ballot_sync(kFull, pushable) & gmask;
+                if (leader && bsel) {
+                    visited++;
+                    pushed += (unsigned long long)o;
+                }
+                const unsigned lb = __ballot_sync(kFull, leader && bpush != 0);
+                s_share[j][tid] = share;
+                if (lane == 0) {
+                    s_lbs[j][warp] = lb;
+                    wcount[j][warp] = __popc(lb);
+                }
             }
         }
         __syncthreads();
@@ -529,8 +555,9 @@ static BLaunch blaunch(const di_graph *g) {
     const int64_t n = g->n;
     auto cap = [&](int64_t want, int64_t lim) { return (int)(want < 1 ? 1 : (want < lim ? want : lim)); };
     l.ew = cap((n * T + 255) / 256, (int64_t)sms * 8);
-    l.sel = cap((n * T + 255) / 256, (int64_t)sms * 8);
     int occ = 0;
+    DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_select<T>, 256, 0));
+    l.sel = cap((n + 255) / 256, (int64_t)sms * (occ > 0 ? occ : 1));   // one wave of 256-node chunks
     DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_push<T>, 256, 0));
     l.push = sms * (occ > 0 ? occ : 1);
     l.red = cap((n * T + 255) / 256, (int64_t)(sms * 4 < kReduceBlocks ? sms * 4 : kReduceBlocks));
