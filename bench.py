@@ -40,7 +40,7 @@ MAX_SWEEPS = 20000
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     p.add_argument("--no-legs", action="store_true", help="skip the extra legs (DI-CYC, PI, d=0.95)")
@@ -88,9 +88,15 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # the timed region starts once the sampler has written its first line (nvidia-smi takes
+        # a moment to start), so every timed step is covered
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
 
     def stop(self):
         if not self.proc:
@@ -428,7 +434,10 @@ def run_gpu(args):
     # per-kernel timing: one solve with CUDA events around every kernel launch
     prof = step(profile=1)
     push_ms = prof["push_ms"] / max(prof["push_launches"], 1)
-    push_bytes = (12.0 * prof["pushed_edges"] + 24.0 * prof["frontier_entries"]) / max(prof["push_launches"], 1)
+    # algorithmic bytes of the push: 4 B link index + 8 B read-modify-write of F_j per pushed
+    # link; per frontier entry 4 B id + 4 B share + 8 B row start (the row end is the next node's
+    # row start, counted with that node)
+    push_bytes = (12.0 * prof["pushed_edges"] + 16.0 * prof["frontier_entries"]) / max(prof["push_launches"], 1)
     peak, peak_kind = peaks()
     achieved = push_bytes / (push_ms * 1e-3) / 1e9
     kernel_total = prof["select_ms"] + prof["push_ms"] + prof["reduce_ms"] + prof["refine_ms"]
@@ -499,7 +508,8 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "traffic_source": traffic_src, "kernel": "k_push_win", "peak_kind": peak_kind,
                      "bytes_per_launch": push_bytes, "ms_per_launch": push_ms,
-                     "kernel_share": prof["push_ms"] / kernel_total if kernel_total else None},
+                     "kernel_share": prof["push_ms"] / kernel_total if kernel_total else None,
+                     "profiled_solve_kernel_ms": {k: prof[k + "_ms"] for k in ("select", "push", "reduce", "refine")}},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "legs": legs,
