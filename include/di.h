@@ -225,7 +225,7 @@ typedef struct {
     double d;                    /* damping of every request; 0 means 0.85 */
     int32_t slots;               /* request slots per graph (columns of its tile): 4, 8, 16 or 32;
                                     0 means 32 */
-    int32_t sweeps_per_step;     /* sweeps between two admission / retirement points; 0 means 4 */
+    int32_t sweeps_per_step;     /* sweeps between two admission / retirement points; 0 means 8 */
     int32_t max_request_sweeps;  /* a request still above its tolerance after this many sweeps
                                     ends with DI_ERR_NOT_CONVERGED; 0 means 100000 */
     int32_t reserved;
@@ -239,8 +239,8 @@ typedef struct {
     int32_t graph, slot;
     double residual_l1;          /* final ||F||_1 of its column (exact FP64 when tol < 1e-6) */
     double queue_ms;             /* submit -> admitted into a slot */
-    double service_ms;           /* admitted -> history copied out */
-    double total_ms;             /* submit -> done */
+    double service_ms;           /* admitted -> history in host memory */
+    double total_ms;             /* submit -> history in host memory (done) */
 } di_request_info;
 
 /*
@@ -249,7 +249,10 @@ typedef struct {
  * B = (1 - d) / |S| on its seed set S (Section 1 problem, Section 2.3 DI-SOP sweeps, per-column
  * selection and retirement as in di_solve_batch). Requests that arrive while others are on the
  * GPU are admitted between sweep steps as slots free up, so their work overlaps; the workers of
- * different graphs run concurrently. The graphs must outlive the server.
+ * different graphs run concurrently. A finished request's history is copied into a pinned host
+ * buffer owned by the server (one per finished request not yet collected by di_server_wait, n
+ * doubles each); the request is done when that copy has completed. The graphs must outlive the
+ * server.
  * Errors: DI_ERR_INVALID_ARG, DI_ERR_OOM (mem_budget below 4 slots per graph), DI_ERR_CUDA.
  */
 di_status di_server_create(di_graph *const *graphs, int32_t n_graphs, const di_server_opts *opts,
@@ -266,9 +269,9 @@ di_status di_server_submit(di_server *srv, int32_t graph, const int32_t *seeds, 
 
 /*
  * di_server_wait — waits at most timeout_ms for a request. When it is done, copies its history H
- * (the approximation of X, n doubles) into X_out (host or device memory; NULL skips the copy),
- * fills *info (nullable), forgets the request and returns its status. DI_ERR_TIMEOUT leaves the
- * request pending (wait again later).
+ * (the approximation of X, n doubles) from the server's pinned buffer into X_out (host or device
+ * memory; NULL skips the copy), releases the buffer, fills *info (nullable), forgets the request
+ * and returns its status. DI_ERR_TIMEOUT leaves the request pending (wait again later).
  */
 di_status di_server_wait(di_server *srv, int64_t request_id, double *X_out, di_request_info *info,
                          int32_t timeout_ms);

@@ -10,7 +10,9 @@
 //   3. retire: a slot whose ||F_c||_1 fell to its tolerance is finished; for tolerances below
 //      1e-6 the exact FP64 residual of the tile (B + P.H - H) is recomputed first and a slot
 //      whose exact residual is still above its tolerance keeps sweeping from it;
-//   4. copy each finished column's history to the request and free its slot.
+//   4. copy each finished column's history out and zero the column, so the slot is clean for the
+//      next request; the copy to pinned host memory is followed on the stream by a host function
+//      that marks the request done, so the worker never waits for the copy.
 // Requests that arrive while others are on the GPU are admitted at the next step as slots
 // free up, so requests of different arrival times share sweeps, and the workers of different
 // graphs run concurrently on the device. Each column is an independent problem; batch-mates
@@ -33,17 +35,6 @@ double now_ms() {
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
-template <int T>
-__global__ void ks_cols_reset(float *F, double *H, double *Bn, int32_t n, uint32_t mask) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        for (int c = 0; c < T; c++) {
-            if (!(mask >> c & 1u)) continue;
-            F[i * T + c] = 0.f;
-            H[i * T + c] = 0.0;
-            Bn[i * T + c] = 0.0;
-        }
-    }
-}
 
 template <int T>
 __global__ void ks_seed_col(const int32_t *seeds, int cnt, int c, double share, float *F, double *Bn) {
@@ -54,10 +45,16 @@ __global__ void ks_seed_col(const int32_t *seeds, int cnt, int c, double share, 
     }
 }
 
+// a finished column: its history goes to out, and its fluid, history and B are zeroed
 template <int T>
-__global__ void ks_col_extract(const double *H, int32_t n, int c, double *out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = H[i * T + c];
+__global__ void ks_col_retire(float *F, double *H, double *Bn, int32_t n, int c, double *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t idx = i * T + c;
+        out[i] = H[idx];
+        H[idx] = 0.0;
+        F[idx] = 0.f;
+        Bn[idx] = 0.0;
+    }
 }
 
 struct Request {
@@ -68,7 +65,7 @@ struct Request {
     double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
     int slot = -1;
     int admit_sweep = 0;
-    std::vector<double> X;
+    double *X = nullptr;            // pinned host copy of the history (from the worker's pool)
     di_status status = DI_OK;
     int sweeps = 0;
     double residual = 0.0;
@@ -83,7 +80,7 @@ struct Worker;
 
 struct di_server {
     double d = 0.85;
-    int sweeps_per_step = 4;
+    int sweeps_per_step = 8;
     int max_request_sweeps = 100000;
     std::vector<std::unique_ptr<di::Worker>> workers;
     std::mutex mu;                       // requests map, completion signalling
@@ -104,7 +101,8 @@ struct Worker {
     BatchWorkspace w;
     cudaStream_t s = nullptr;
     DevBuf seeds_dev, col_out;
-    double *pinned = nullptr;            // one column of X on its way to the host
+    std::mutex pool_mu;
+    std::vector<double *> pool;          // free pinned host buffers of n doubles
     std::mutex mu;
     std::condition_variable cv;
     std::deque<std::shared_ptr<Request>> queue;
@@ -113,13 +111,50 @@ struct Worker {
     std::atomic<bool> failed{false};
 
     ~Worker() {
-        if (pinned) cudaFreeHost(pinned);
-        if (s) cudaStreamDestroy(s);
+        if (s) {
+            cudaStreamSynchronize(s);   // pending copies and their host functions
+            cudaStreamDestroy(s);
+        }
+        for (double *p : pool) cudaFreeHost(p);
+    }
+
+    double *take_buffer() {
+        {
+            std::lock_guard<std::mutex> lk(pool_mu);
+            if (!pool.empty()) {
+                double *p = pool.back();
+                pool.pop_back();
+                return p;
+            }
+        }
+        double *p = nullptr;
+        DI_CHECK_CUDA(cudaMallocHost(&p, sizeof(double) * (size_t)g->n));
+        return p;
+    }
+    void give_buffer(double *p) {
+        std::lock_guard<std::mutex> lk(pool_mu);
+        pool.push_back(p);
     }
 
     template <int TT>
     void step_loop();
     void run();
+
+    // runs on the CUDA runtime's thread once a result's copy to host memory has completed; it
+    // only takes the server's lock (no CUDA call)
+    struct Copied {
+        di_server *srv;
+        std::shared_ptr<Request> r;
+    };
+    static void CUDART_CB copied(void *p) {
+        std::unique_ptr<Copied> c(static_cast<Copied *>(p));
+        {
+            std::lock_guard<std::mutex> lk(c->srv->mu);
+            c->r->t_done = now_ms();
+            c->r->done = true;
+        }
+        c->srv->done_cv.notify_all();
+    }
 };
 
 template <int TT>
@@ -162,19 +197,21 @@ void Worker::step_loop() {
             }
         }
         if (!admitted.empty()) {
-            uint32_t mask = 0;
-            for (auto &r : admitted) mask |= 1u << r->slot;
-            ks_cols_reset<TT><<<l.ew, 256, 0, s>>>(w.F.as<float>(), w.H.as<double>(), w.Bn.as<double>(), n, mask);
+            // free slots are clean (a retiring column is zeroed), so admission only scatters the
+            // seeds; all admitted seed lists go up in one copy
+            std::vector<int32_t> all_seeds;
+            for (auto &r : admitted) all_seeds.insert(all_seeds.end(), r->seeds.begin(), r->seeds.end());
+            seeds_dev.ensure(sizeof(int32_t) * all_seeds.size());
+            DI_CHECK_CUDA(cudaMemcpyAsync(seeds_dev.p, all_seeds.data(), sizeof(int32_t) * all_seeds.size(),
+                                          cudaMemcpyHostToDevice, s));
+            DI_CHECK_CUDA(cudaStreamSynchronize(s));   // all_seeds is a local buffer
+            size_t at = 0;
             for (auto &r : admitted) {
                 const int cnt = (int)r->seeds.size();
-                seeds_dev.ensure(sizeof(int32_t) * (size_t)cnt);
-                DI_CHECK_CUDA(cudaMemcpyAsync(seeds_dev.p, r->seeds.data(), sizeof(int32_t) * (size_t)cnt,
-                                              cudaMemcpyHostToDevice, s));
-                ks_seed_col<TT><<<(cnt + 255) / 256, 256, 0, s>>>(seeds_dev.as<int32_t>(), cnt, r->slot,
+                ks_seed_col<TT><<<(cnt + 255) / 256, 256, 0, s>>>(seeds_dev.as<int32_t>() + at, cnt, r->slot,
                                                                    (1.0 - srv->d) / cnt, w.F.as<float>(),
                                                                    w.Bn.as<double>());
-                // the seed upload is synchronous with respect to the host buffer only after this
-                DI_CHECK_CUDA(cudaStreamSynchronize(s));
+                at += (size_t)cnt;
                 const int c = r->slot;
                 hc.active[c] = 1;
                 hc.tol[c] = r->tol;
@@ -221,25 +258,21 @@ void Worker::step_loop() {
                 hc.tol[c] = 0.5 * r->tol;
                 continue;
             }
-            // 4. the column's history goes to the request
-            ks_col_extract<TT><<<l.ew, 256, 0, s>>>(w.H.as<double>(), n, c, col_out.as<double>());
-            DI_CHECK_CUDA(cudaMemcpyAsync(pinned, col_out.p, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
-            DI_CHECK_CUDA(cudaStreamSynchronize(s));
-            r->X.assign(pinned, pinned + n);
+            // 4. the column's history goes to a pinned buffer of the request, the column is zeroed
+            // for its next request, and a host function marks the request done after the copy
+            r->X = take_buffer();
+            ks_col_retire<TT><<<l.ew, 256, 0, s>>>(w.F.as<float>(), w.H.as<double>(), w.Bn.as<double>(), n, c,
+                                                   col_out.as<double>());
+            DI_CHECK_CUDA(cudaMemcpyAsync(r->X, col_out.p, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
             r->sweeps = hc.sweeps - r->admit_sweep;
             r->residual = hc.r[c];
             r->status = hc.r[c] <= r->tol ? DI_OK : DI_ERR_NOT_CONVERGED;
             hc.active[c] = 0;
+            DI_CHECK_CUDA(cudaLaunchHostFunc(s, &Worker::copied, new Copied{srv, r}));
             {
                 std::lock_guard<std::mutex> lk(mu);
                 slot[c] = nullptr;
             }
-            {
-                std::lock_guard<std::mutex> lk(srv->mu);
-                r->t_done = now_ms();
-                r->done = true;
-            }
-            srv->done_cv.notify_all();
         }
     }
 }
@@ -285,6 +318,16 @@ di_server::~di_server() {
         w->cv.notify_all();
         if (w->th.joinable()) w->th.join();
     }
+    // copies still in flight and their host functions use this server's lock: finish them
+    // while the lock exists, then hand back the buffers of results nobody collected
+    for (auto &w : workers)
+        if (w->s) cudaStreamSynchronize(w->s);
+    for (auto &kv : requests)
+        if (kv.second->X) {
+            workers[kv.second->graph]->give_buffer(kv.second->X);
+            kv.second->X = nullptr;
+        }
+    workers.clear();
 }
 
 using namespace di;
@@ -317,7 +360,7 @@ di_status di_server_create(di_graph *const *graphs, int32_t n_graphs, const di_s
         }
         std::unique_ptr<di_server> srv(new di_server());
         srv->d = d;
-        srv->sweeps_per_step = o.sweeps_per_step > 0 ? o.sweeps_per_step : 4;
+        srv->sweeps_per_step = o.sweeps_per_step > 0 ? o.sweeps_per_step : 8;
         srv->max_request_sweeps = o.max_request_sweeps > 0 ? o.max_request_sweeps : 100000;
         for (int i = 0; i < n_graphs; i++) {
             DI_REQUIRE(graphs[i] != nullptr, DI_ERR_INVALID_ARG, "graph %d is NULL", i);
@@ -330,7 +373,6 @@ di_status di_server_create(di_graph *const *graphs, int32_t n_graphs, const di_s
             ensure_batch(graphs[i], w->w, T);
             w->col_out.ensure(sizeof(double) * (size_t)graphs[i]->n);
             DI_CHECK_CUDA(cudaStreamCreateWithFlags(&w->s, cudaStreamNonBlocking));
-            DI_CHECK_CUDA(cudaMallocHost(&w->pinned, sizeof(double) * (size_t)graphs[i]->n));
             srv->workers.push_back(std::move(w));
         }
         for (auto &w : srv->workers) {
@@ -402,10 +444,19 @@ di_status di_server_wait(di_server *srv, int64_t request_id, double *X_out, di_r
             info->service_ms = r->t_admit > 0 ? r->t_done - r->t_admit : 0.0;
             info->total_ms = r->t_done - r->t_submit;
         }
-        if (X_out && !r->X.empty()) {
-            cudaStream_t s = nullptr;
-            from_device(X_out, r->X.data(), sizeof(double) * r->X.size(), s);
-            DI_CHECK_CUDA(cudaStreamSynchronize(s));
+        if (r->X) {
+            Worker &w = *srv->workers[r->graph];
+            double *buf = r->X;
+            r->X = nullptr;
+            if (X_out) {
+                cudaStream_t s = nullptr;
+                const cudaError_t e = cudaMemcpyAsync(X_out, buf, sizeof(double) * (size_t)w.g->n, cudaMemcpyDefault, s);
+                const cudaError_t e2 = e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+                w.give_buffer(buf);
+                DI_CHECK_CUDA(e2);
+            } else {
+                w.give_buffer(buf);
+            }
         }
         DI_REQUIRE(r->status == DI_OK, r->status, "request %lld ended with status %d", (long long)request_id,
                    (int)r->status);
