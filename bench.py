@@ -261,6 +261,41 @@ def ppr_batch_leg(di, workloads, torch):
             "speedup": (k / batch_s) / (sample / solo_s), "max_residual": float(np.max(res))}
 
 
+def transposed_leg(di, workloads, torch, flush, name="web_n10m_t"):
+    """Another 10M-node graph: by default the benchmark graph with every link reversed (P
+    transposed, the paper's Dataset 1bis pattern); `web_n10m_e` is the graph where E dominates
+    (E/N about 0.87, like the paper's Dataset 2). DI-SOP with and without the E pre-diffusion,
+    and PI, from resident inputs."""
+    cfg = workloads.WORKLOADS[name]
+    n, src, dst = workloads.generate(cfg["spec"])
+    g = di.di_graph_create(n, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda())
+    del src, dst
+    d, tol = cfg["d"], cfg["tol"]
+    B = torch.full((n,), (1.0 - d) / n, dtype=torch.float64, device="cuda")
+    X = torch.empty(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()                                                   # warm-up of the same call
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        inf = fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), inf
+
+    out = {"graph": {k: g.stats[k] for k in ("n_nodes", "L", "D", "E", "e_levels", "max_in", "max_out")}}
+    for name, e in (("di_sop", 0), ("di_sop_e_prediffused", 1)):
+        ms, inf = timed(lambda: di.di_solve_ex(g, B, d, tol, schedule=di.DI_SOP, max_sweeps=MAX_SWEEPS,
+                                                e_prediffuse=e, X_out=X)[1])
+        out[name] = {"ms_to_residual": ms, "GTEPS": inf["pushed_edges"] / (ms * 1e-3) / 1e9, "sweeps": inf["sweeps"],
+                     "pushed_per_L": inf["pushed_edges"] / g.stats["L"], "residual_l1": inf["residual_l1"]}
+    ms, inf = timed(lambda: di.di_power_iter(g, B, d, tol, max_iters=MAX_SWEEPS, X_out=X)[1])
+    out["pi"] = {"ms_to_residual": ms, "iterations": inf["sweeps"], "residual_l1": inf["residual_l1"]}
+    return out
+
+
 def serving_leg(di, workloads, torch, rate_qps=600.0, n_req=300, slots=16, sweeps_per_step=8, plain=True):
     """Poisson stream of personalised PageRank requests over four resident graphs (N = 100k,
     500k, 2M, 5M), tolerances 1e-4/1e-6/1e-8, seed sets of 1..1000 nodes: the continuously
@@ -454,7 +489,8 @@ def run_gpu(args):
     legs = {}
     if not args.no_legs:
         for name, kw in (("di_cyc", dict(schedule=di.DI_CYC)), ("di_sop_d095", dict(d=0.95, Bx=torch.full(
-                (n,), (1.0 - 0.95) / n, dtype=torch.float64, device=dev)))):
+                (n,), (1.0 - 0.95) / n, dtype=torch.float64, device=dev))), ("di_sop_e_prediffused",
+                                                                             dict(e_prediffuse=1))):
             flush.fill_(1)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -474,6 +510,8 @@ def run_gpu(args):
         ms = a.elapsed_time(b)
         legs["pi"] = {"ms_to_residual": ms, "GTEPS": pinf["pushed_edges"] / (ms * 1e-3) / 1e9,
                       "iterations": pinf["sweeps"], "residual_l1": pinf["residual_l1"]}
+        legs["transposed"] = transposed_leg(di, workloads, torch, flush)
+        legs["e_dominated"] = transposed_leg(di, workloads, torch, flush, name="web_n10m_e")
     if not args.no_legs:
         legs["ppr_batch"] = ppr_batch_leg(di, workloads, torch)
         legs["serving"] = serving_leg(di, workloads, torch)

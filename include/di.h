@@ -83,7 +83,10 @@ typedef struct {
     int32_t profile;     /* 1: host-driven sweeps with CUDA events around every kernel launch;
                             fills the per-kernel times of di_solve_info (slower: one sync per
                             sweep) */
-    int32_t reserved;
+    int32_t e_prediffuse;/* di_solve_ex only; 1: before the sweeps, visit every node of E once in
+                            level order (Section 2.4: E converges in finitely many steps). Each
+                            node of E then holds its exact value, up to rounding, and receives no
+                            fluid afterwards, so no sweep selects it again. Default 0. */
 } di_solve_opts;
 
 /* Per-solve report. */
@@ -100,11 +103,12 @@ typedef struct {
     int64_t kernel_launches; /* kernels of this library launched by the call */
     int64_t frontier_entries;/* nodes handed to the push kernel (visited nodes with out-links) */
     /* per-kernel device time and launch counts; filled only when opts.profile = 1
-       (PI: push_* is the pull kernel, select_* the heavy-row pre-pass) */
+       (refine_* also holds the initialisation and the E pre-diffusion kernels;
+       PI: push_* is the pull kernel, select_* the heavy-row pre-pass) */
     double select_ms, push_ms, reduce_ms, refine_ms;
     int32_t select_launches, push_launches, reduce_launches, refine_launches;
     int32_t rhs_tile;        /* batched solves: columns per tile that were used */
-    int32_t reserved;
+    int32_t e_visits;        /* visits of the E pre-diffusion (opts.e_prediffuse) */
 } di_solve_info;
 
 /* Which internal array di_graph_export copies. */

@@ -42,6 +42,7 @@ class DiInfo(ctypes.Structure):
         ("e", ctypes.c_double),
         ("residual", ctypes.c_double),
         ("paper_error", ctypes.c_double),
+        ("e_visits", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -83,6 +84,9 @@ def _load():
     lib.or_di.restype = ctypes.c_int
     lib.or_di.argtypes = [i64, i64, vp, vp, vp, vp, dbl, dbl, ctypes.c_int, i64, vp, vp,
                           ctypes.POINTER(DiInfo)]
+    lib.or_di_e.restype = ctypes.c_int
+    lib.or_di_e.argtypes = [i64, i64, vp, vp, vp, vp, vp, ctypes.c_int32, vp, dbl, dbl, ctypes.c_int, i64, vp, vp,
+                            ctypes.POINTER(DiInfo)]
     lib.or_pi.restype = ctypes.c_int
     lib.or_pi.argtypes = [i64, vp, vp, vp, vp, dbl, dbl, i64, vp, ctypes.POINTER(PiInfo)]
     lib.or_pi_paper.restype = ctypes.c_int
@@ -163,6 +167,21 @@ def di(g: Graph, B, d: float, tol: float, schedule: int = SOP, max_cycles: int =
     info = DiInfo()
     rc = lib.or_di(g.n, g.L, g.rp_out.ctypes.data, g.col_out.ctypes.data, g.loop.ctypes.data, pb,
                    d, tol, schedule, max_cycles, H.ctypes.data, F.ctypes.data, ctypes.byref(info))
+    return H, F, info.as_dict(), rc == 0
+
+
+def di_e(g: Graph, B, d: float, tol: float, schedule: int = SOP, max_cycles: int = 100_000):
+    """D-iteration after the E-level pre-diffusion (every node of E visited once in level order,
+    Section 2.4). Returns (H, F, info dict, converged); info["e_visits"] counts the pre-pass."""
+    lib = _load()
+    B, pb = _c(B, np.float64)
+    e_mask, level, _, n_levels = zero_in(g)
+    H = np.zeros(g.n, np.float64)
+    F = np.zeros(g.n, np.float64)
+    info = DiInfo()
+    rc = lib.or_di_e(g.n, g.L, g.rp_out.ctypes.data, g.col_out.ctypes.data, g.loop.ctypes.data,
+                     e_mask.ctypes.data, level.ctypes.data, n_levels, pb, d, tol, schedule, max_cycles,
+                     H.ctypes.data, F.ctypes.data, ctypes.byref(info))
     return H, F, info.as_dict(), rc == 0
 
 

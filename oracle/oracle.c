@@ -20,6 +20,8 @@
  *   or_zero_in       E, the recursively defined zero-in-degree set (Section 2.4), by peeling.
  *   or_zero_in_naive E by its definition, iterated to the least fixpoint (small N only).
  *   or_di            DI-CYC and DI-SOP (Section 2.3, Section 2.5), one node visit at a time.
+ *   or_di_e          the same after one visit of every node of E in level order (E converges
+ *                    in finitely many steps, Section 2.4).
  *   or_pi            power iteration (Jacobi) on X = P.X + B (Section 2.3, Section 2.5 "PI").
  *   or_pi_paper      the paper's normalised PageRank power iteration (Section 2.5 "PI").
  *   or_residual      F* = B + P.H - H, the fluid that H still owes (used for a-posteriori bounds).
@@ -179,6 +181,7 @@ typedef struct {
     double e;              /* fluid absorbed by dangling nodes: sum of H over out[i] == 0 */
     double residual;       /* sum of F at exit */
     double paper_error;    /* residual / (1 - d - d*e), Section 2.5 DI-CYC */
+    int64_t e_visits;      /* visits of the E pre-diffusion (or_di_e) */
 } or_di_info;
 
 /*
@@ -217,11 +220,9 @@ static double sum_fluid(int64_t n, const double *F) {
  * nothing is run again as a DI-CYC cycle. The loop stops when sum F <= tol after a cycle, or
  * after max_cycles cycles (max_cycles < 0: no limit). Returns 0 when converged, 1 otherwise.
  */
-int or_di(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out, const uint8_t *loop,
-          const double *B, double d, double tol, int schedule, int64_t max_cycles,
-          double *H, double *F, or_di_info *info) {
-    memset(info, 0, sizeof(*info));
-    for (int64_t i = 0; i < n; i++) { H[i] = 0.0; F[i] = B[i]; }
+static int run_cycles(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out, const uint8_t *loop,
+                      double d, double tol, int schedule, int64_t max_cycles, double *H, double *F,
+                      or_di_info *info) {
     double r = sum_fluid(n, F);
     while (r > tol && (max_cycles < 0 || info->cycles < max_cycles)) {
         int64_t visits_before = info->visits;
@@ -246,6 +247,36 @@ int or_di(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out, c
     info->residual = r;
     info->paper_error = r / (1.0 - d - d * info->e);
     return r <= tol ? 0 : 1;
+}
+
+int or_di(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out, const uint8_t *loop,
+          const double *B, double d, double tol, int schedule, int64_t max_cycles,
+          double *H, double *F, or_di_info *info) {
+    memset(info, 0, sizeof(*info));
+    for (int64_t i = 0; i < n; i++) { H[i] = 0.0; F[i] = B[i]; }
+    return run_cycles(n, L, rp_out, col_out, loop, d, tol, schedule, max_cycles, H, F, info);
+}
+
+/*
+ * E-level pre-diffusion (Section 2.4: the nodes of E, the recursively zero-in-degree set,
+ * converge exactly in finitely many steps). Every in-neighbour of a node of E at level l lies in
+ * E at a level below l, and no node of E has a self-loop. So once every node of E below level l
+ * has been visited, the fluid of a level-l node is final. Visiting E once in level order (ids
+ * ascending within a level) gives every node of E its exact history, and no fluid reaches E
+ * afterwards. The cycles of or_di then run from that (H, F). e_mask and e_level are or_zero_in's.
+ */
+int or_di_e(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out, const uint8_t *loop,
+            const uint8_t *e_mask, const int32_t *e_level, int32_t n_levels, const double *B, double d,
+            double tol, int schedule, int64_t max_cycles, double *H, double *F, or_di_info *info) {
+    memset(info, 0, sizeof(*info));
+    for (int64_t i = 0; i < n; i++) { H[i] = 0.0; F[i] = B[i]; }
+    for (int32_t l = 0; l < n_levels; l++)
+        for (int64_t i = 0; i < n; i++)
+            if (e_mask[i] && e_level[i] == l) {
+                visit(i, d, rp_out, col_out, loop, H, F, info);
+                info->e_visits++;
+            }
+    return run_cycles(n, L, rp_out, col_out, loop, d, tol, schedule, max_cycles, H, F, info);
 }
 
 /* ------------------------------------------------------------------------------------------ */

@@ -55,7 +55,7 @@ class GraphStats(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("fluid", ctypes.c_int32), ("max_sweeps", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("host_loop", ctypes.c_int32), ("rhs_tile", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("e_prediffuse", ctypes.c_int32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -80,7 +80,7 @@ class SolveInfo(ctypes.Structure):
                 ("select_ms", ctypes.c_double), ("push_ms", ctypes.c_double), ("reduce_ms", ctypes.c_double),
                 ("refine_ms", ctypes.c_double), ("select_launches", ctypes.c_int32),
                 ("push_launches", ctypes.c_int32), ("reduce_launches", ctypes.c_int32),
-                ("refine_launches", ctypes.c_int32), ("rhs_tile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("refine_launches", ctypes.c_int32), ("rhs_tile", ctypes.c_int32), ("e_visits", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -258,10 +258,12 @@ def di_solve(g: Graph, B, d: float, tol: float, schedule: int = DI_SOP, max_swee
 
 
 def di_solve_ex(g: Graph, B, d: float, tol: float, schedule: int = DI_SOP, fluid: int = DI_FLUID_F32,
-                max_sweeps: int = 0, refine: int = 0, host_loop: int = 0, profile: int = 0, X_out=None):
+                max_sweeps: int = 0, refine: int = 0, host_loop: int = 0, profile: int = 0, e_prediffuse: int = 0,
+                X_out=None):
     """D-iteration with explicit options. Returns (X, info)."""
     X = X_out if X_out is not None else _like(B, g.n, np.float64)
-    o = SolveOpts(int(schedule), int(fluid), int(max_sweeps), int(refine), int(host_loop), 0, int(profile), 0)
+    o = SolveOpts(int(schedule), int(fluid), int(max_sweeps), int(refine), int(host_loop), 0, int(profile),
+                  int(e_prediffuse))
     info = SolveInfo()
     res = ctypes.c_double()
     _check(load().di_solve_ex(g.handle, _ptr(B, np.float64), float(d), float(tol), ctypes.byref(o),

@@ -623,17 +623,18 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
         DI_CHECK_CUDA(cudaStreamSynchronize(s));
     }
 
-    // E by peeling
+    // E by peeling; each level's frontier is appended to e_order, so e_order lists E grouped by
+    // level (level 0 first) for the pre-diffusion
     g->e_mask.ensure((size_t)n);
     g->e_level.ensure(sizeof(int32_t) * (size_t)n);
-    DevBuf left, fa, fb;
+    g->e_order.ensure(sizeof(int32_t) * (size_t)n);
+    g->e_level_off.assign(1, 0);
+    DevBuf left;
     left.ensure(sizeof(int32_t) * (size_t)n);
-    fa.ensure(sizeof(int32_t) * (size_t)n);
-    fb.ensure(sizeof(int32_t) * (size_t)n);
     int32_t *cnt_a = counts, *cnt_b = counts + 1;
+    int32_t *eo = g->e_order.as<int32_t>();
     k_e_init<<<grid_for(n, 256, dev), 256, 0, s>>>(g->in_deg.as<int32_t>(), n, left.as<int32_t>(),
-                                                 g->e_mask.as<uint8_t>(), g->e_level.as<int32_t>(), fa.as<int32_t>(),
-                                                 cnt_a);
+                                                 g->e_mask.as<uint8_t>(), g->e_level.as<int32_t>(), eo, cnt_a);
     DI_CHECK_CUDA(cudaGetLastError());
     int32_t *hcount = nullptr;
     DI_CHECK_CUDA(cudaMallocHost(&hcount, sizeof(int32_t)));
@@ -645,15 +646,16 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
             DI_CHECK_CUDA(cudaStreamSynchronize(s));
             int32_t c = *hcount;
             if (c == 0) break;
+            const int64_t at = e_total;   // this level's frontier: e_order[at, at + c)
             e_total += c;
+            g->e_level_off.push_back(e_total);
             level++;
             DI_CHECK_CUDA(cudaMemsetAsync(cnt_b, 0, sizeof(int32_t), s));
             int blocks = grid_for((int64_t)c * 32, 256, dev);
-            k_e_peel<<<blocks, 256, 0, s>>>(fa.as<int32_t>(), cnt_a, g->rp_out.as<int64_t>(), g->col_out.as<int32_t>(),
+            k_e_peel<<<blocks, 256, 0, s>>>(eo + at, cnt_a, g->rp_out.as<int64_t>(), g->col_out.as<int32_t>(),
                                             left.as<int32_t>(), g->e_mask.as<uint8_t>(), g->e_level.as<int32_t>(),
-                                            level, fb.as<int32_t>(), cnt_b);
+                                            level, eo + e_total, cnt_b);
             DI_CHECK_CUDA(cudaGetLastError());
-            std::swap(fa.p, fb.p);
             std::swap(cnt_a, cnt_b);
         }
     } catch (...) {

@@ -192,6 +192,8 @@ struct di_graph {
     di::DevBuf loop;               // uint8
     di::DevBuf e_mask;             // uint8
     di::DevBuf e_level;            // int32
+    di::DevBuf e_order;            // int32[N]: its first |E| entries list E grouped by level
+    std::vector<int64_t> e_level_off;  // host: level l of E is e_order[off[l], off[l + 1])
     // heavy rows of the in-CSR (in-degree > kPullHeavy), for the pull kernels
     int32_t n_heavy_in = 0;
     int32_t n_heavy_in_chunks = 0;

@@ -330,6 +330,93 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
     }
 }
 
+// E-level pre-diffusion (Section 2.4: E, the recursively zero-in-degree set, converges in
+// finitely many steps). One launch per level of E: every in-neighbour of a node of the level is
+// in E at a lower level and was visited by an earlier launch, so the node's fluid is final, and
+// no two nodes of a level are linked. One lane per node visits it (E holds no loop node) and
+// pushes its share over at most kEWarpLinks out-links itself; the warp pushes the links of
+// nodes with more, one node at a time; both keep kEUnroll index loads in flight before their
+// additions. As in the push, links into hubs (bit 31 of col_push)
+// collect in a per-block shared-memory cache, flushed once per block.
+constexpr int kEWarpLinks = 32;
+constexpr int kEUnroll = 8;   // index loads in flight before their additions
+
+template <class T>
+__global__ void __launch_bounds__(256) k_e_visit(const int32_t *nodes, int32_t count, const int32_t *out_info,
+                                                 const int64_t *rp_out, const int32_t *col_push,
+                                                 const int32_t *hub_ids, T *F, double *H, SolveCtl *ctl) {
+    __shared__ double scratch[32];
+    __shared__ unsigned long long scratch_u[32];
+    __shared__ T s_hacc[kHubSlots];
+    for (int q = threadIdx.x; q < kHubSlots; q += blockDim.x) s_hacc[q] = (T)0;
+    __syncthreads();
+    auto add = [&](int32_t jr, T v) {
+        if (jr < 0) atomicAdd(&s_hacc[hub_slot(jr & 0x7fffffff)], v);
+        else atomicAdd(&F[jr], v);
+    };
+    const double d = ctl->d;
+    const float d_f = (float)d;
+    const int lane = (int)lane_id();
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double e_loc = 0.0;
+    unsigned long long pushed = 0, visited = 0;
+    for (int64_t w0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; w0 < count; w0 += nwarps * 32) {
+        const int64_t idx = w0 + lane;
+        int32_t u = 0, o = 0;
+        int64_t b = 0;
+        T share = (T)0;
+        if (idx < count) {
+            u = nodes[idx];
+            const T f = F[u];
+            o = out_info[u] & 0x7fffffff;
+            b = rp_out[u];
+            double t;
+            visit_math(f, o, false, d, d_f, t, share);
+            F[u] = (T)0;
+            H[u] += t;
+            if (o == 0) e_loc += t;
+            visited++;
+            pushed += (unsigned long long)o;
+            if (o <= kEWarpLinks)
+                for (int64_t k0 = b; k0 < b + o; k0 += kEUnroll) {
+                    int32_t jr[kEUnroll];
+#pragma unroll
+                    for (int v = 0; v < kEUnroll; v++) jr[v] = k0 + v < b + o ? col_push[k0 + v] : 0;
+#pragma unroll
+                    for (int v = 0; v < kEUnroll; v++)
+                        if (k0 + v < b + o) add(jr[v], share);
+                }
+        }
+        unsigned big = __ballot_sync(kFull, idx < count && o > kEWarpLinks);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int64_t bb = __shfl_sync(kFull, b, src);
+            const int32_t oo = __shfl_sync(kFull, o, src);
+            const T ss = __shfl_sync(kFull, share, src);
+            for (int64_t k0 = bb + lane; k0 < bb + oo; k0 += 32 * kEUnroll) {
+                int32_t jr[kEUnroll];
+#pragma unroll
+                for (int v = 0; v < kEUnroll; v++) jr[v] = k0 + 32 * v < bb + oo ? col_push[k0 + 32 * v] : 0;
+#pragma unroll
+                for (int v = 0; v < kEUnroll; v++)
+                    if (k0 + 32 * v < bb + oo) add(jr[v], ss);
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kHubSlots; q += blockDim.x)
+        if (s_hacc[q] != (T)0) atomicAdd(&F[__ldg(hub_ids + q)], s_hacc[q]);
+    e_loc = block_sum(e_loc, scratch);
+    pushed = block_sum(pushed, scratch_u);
+    visited = block_sum(visited, scratch_u);
+    if (threadIdx.x == 0) {
+        if (e_loc != 0.0) atomicAdd(&ctl->e, e_loc);
+        if (pushed) atomicAdd(&ctl->pushed, pushed);
+        if (visited) atomicAdd(&ctl->visited, visited);
+    }
+}
+
 // Push, one warp per batch of 32 frontier entries (no block barriers): the warp scans the
 // entries' degrees, then each lane takes kPushVT contiguous links of the batch's concatenated
 // links per round, finds their owner once (binary search over the warp's 33 offsets in shared
@@ -1086,8 +1173,8 @@ static void check_common(di_graph *g, const double *B, double d, double tol, con
 
 template <class T>
 static void solve_impl(di_graph *g, const double *B, double d, double tol, int schedule, int max_sweeps, int refine,
-                       int host_loop, int profile, double *X_out, double *residual_out, di_solve_info *info,
-                       cudaStream_t s) {
+                       int host_loop, int profile, int e_prediffuse, double *X_out, double *residual_out,
+                       di_solve_info *info, cudaStream_t s) {
     ensure_workspace<T>(g);
     Workspace &ws = g->ws;
     const Launch l = launch_shape<T>(g);
@@ -1105,6 +1192,20 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
         kc.run(KC_REFINE, 1, [&] {
             k_init<T><<<l.ew_blocks, 256, 0, s>>>(ws.B.as<double>(), g->n, ws.F.as<T>(), ws.H.as<double>(), ctl);
         });
+        if (e_prediffuse) {
+            for (size_t lv = 0; lv + 1 < g->e_level_off.size(); lv++) {
+                const int64_t at = g->e_level_off[lv], cnt = g->e_level_off[lv + 1] - at;
+                const int64_t want = (cnt + 255) / 256, lim = (int64_t)g->dev.sms * 8;
+                const int blocks = (int)(want < lim ? want : lim);
+                kc.run(KC_REFINE, 1, [&] {
+                    k_e_visit<T><<<blocks, 256, 0, s>>>(g->e_order.as<int32_t>() + at, (int32_t)cnt,
+                                                        g->out_info.as<int32_t>(), g->rp_out.as<int64_t>(),
+                                                        g->col_push.as<int32_t>(), g->hub_ids.as<int32_t>(),
+                                                        ws.F.as<T>(), ws.H.as<double>(), ctl);
+                });
+            }
+            DI_CHECK_CUDA(cudaGetLastError());
+        }
         auto run_sweeps = [&]() {
             kc.run(KC_REDUCE, 1, [&] {
                 k_reduce<T><<<l.red_blocks, 256, 0, s>>>(ws.F.as<T>(), g->n, ws.partials.as<double>(), ctl,
@@ -1168,6 +1269,7 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
         info->push_launches = kc.count[KC_PUSH];
         info->reduce_launches = kc.count[KC_REDUCE];
         info->refine_launches = kc.count[KC_REFINE];
+        info->e_visits = e_prediffuse ? (int32_t)g->stats.E : 0;
     }
     if (residual_out) *residual_out = c.r;
     DI_REQUIRE(c.status == 0, DI_ERR_INVALID_ARG, "B has a negative or non-finite entry");
@@ -1190,10 +1292,12 @@ di_status solve_single(di_graph *g, const double *B, double d, double tol, const
         DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
         DeviceGuard dg(g->dev.device);
         if (o.fluid == DI_FLUID_F32)
-            solve_impl<float>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile, X_out,
+            solve_impl<float>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
+                              o.e_prediffuse != 0, X_out,
                               residual_out, info, s);
         else
-            solve_impl<double>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile, X_out,
+            solve_impl<double>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
+                               o.e_prediffuse != 0, X_out,
                                residual_out, info, s);
     });
 }

@@ -3,6 +3,9 @@
   pa_n10k : N=10k preferential-attachment graph, FP64 fluid, tol 1e-10: DI-CYC, DI-SOP and PI
             against the oracle's fixed point.
   web_n1m : N=1M web-like graph, FP32 fluid + FP64 refinement, tol 1e-8: DI-SOP, DI-CYC and PI.
+  web_n1m_t: the same graph with every link reversed (P transposed: hubs become heavy pushers,
+            dangling nodes become zero-in-degree nodes): build, DI-SOP with and without the E
+            pre-diffusion, DI-CYC and PI.
   web_n10m: N=10M, ~141M links: bit-exact graph build; DI-SOP at d=0.85 against the oracle's
             DI-SOP fixed point; d=0.95 certified by the oracle's exact residual of the GPU
             history (||X - H||_1 <= ||B + P.H - H||_1 / (1 - d), a bound that holds at any size).
@@ -48,6 +51,22 @@ def test_web_n1m_fp32_fluid():
     assert ok
     for sched in (di.DI_SOP, di.DI_CYC):
         X, info = di.di_solve_ex(g, B, d, tol, schedule=sched, fluid=di.DI_FLUID_F32)
+        assert info["residual_l1"] <= tol
+        assert rel_l1(X, ref) <= TOL_X
+    X, info = di.di_power_iter(g, B, d, tol)
+    assert rel_l1(X, ref) <= TOL_X
+
+
+def test_web_n1m_transposed():
+    cfg, n, src, dst, g, og = _setup("web_n1m_t")
+    assert_build_matches_oracle(g, og)
+    assert g.stats["max_out"] > 4096          # rows pushed by the heavy-node path
+    d, tol = cfg["d"], cfg["tol"]
+    B = oracle.uniform_B(n, d)
+    ref, _, _, ok = oracle.di(og, B, d, 1e-13, oracle.SOP)
+    assert ok
+    for kw in (dict(schedule=di.DI_SOP), dict(schedule=di.DI_SOP, e_prediffuse=1), dict(schedule=di.DI_CYC)):
+        X, info = di.di_solve_ex(g, B, d, tol, fluid=di.DI_FLUID_F32, **kw)
         assert info["residual_l1"] <= tol
         assert rel_l1(X, ref) <= TOL_X
     X, info = di.di_power_iter(g, B, d, tol)

@@ -2,7 +2,8 @@
 
 Each case plants one mistake in a copy of oracle/oracle.c (a dropped term, a wrong sign, a wrong
 index or operand), compiles the copy on the CPU and runs the whole pin suite
-(test_oracle_build.py, test_oracle_solve.py) against it. Every mutant must fail at least one pin.
+(test_oracle_build.py, test_oracle_solve.py, test_oracle_e.py) against it. Every mutant must fail
+at least one pin.
 """
 import os
 import subprocess
@@ -50,6 +51,10 @@ MUTANTS = {
     "peel_start": ("if (indeg[v] == 0) { queue[tail++]", "if (indeg[v] <= 1) { queue[tail++]"),
     # residual with the wrong sign of H
     "residual_sign": ("Fstar[i] = acc - H[i];", "Fstar[i] = acc + H[i];"),
+    # E pre-diffusion in id order, ignoring the levels
+    "e_prepass_id_order": ("if (e_mask[i] && e_level[i] == l) {", "if (e_mask[i] && l == 0) {"),
+    # E pre-diffusion skips the last level
+    "e_prepass_short": ("for (int32_t l = 0; l < n_levels; l++)", "for (int32_t l = 0; l + 1 < n_levels; l++)"),
 }
 
 
@@ -68,7 +73,8 @@ def test_pins_catch_planted_mistake(name, tmp_path):
         proc = subprocess.run(
             [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
              os.path.join(ROOT, "tests", "test_oracle_build.py"),
-             os.path.join(ROOT, "tests", "test_oracle_solve.py")],
+             os.path.join(ROOT, "tests", "test_oracle_solve.py"),
+             os.path.join(ROOT, "tests", "test_oracle_e.py")],
             cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
     except subprocess.TimeoutExpired:
         return  # a mutant that no longer converges within the cycle cap is caught too

@@ -85,6 +85,7 @@ class GraphSpec:
     chain_max: int = 10
     p_loop: float = 0.1
     seed: int = BASE_SEED
+    transpose: bool = False        # reverse every link (the graph of P transposed)
 
     def with_seed(self, seed: int) -> "GraphSpec":
         return replace(self, seed=seed)
@@ -93,7 +94,7 @@ class GraphSpec:
         return asdict(self)
 
 
-# The five workloads. Seeds are BASE_SEED + workload index.
+# The workloads. Seeds are BASE_SEED + index of the untransposed workload.
 WORKLOADS = {
     # plain DI-CYC + DI-SOP + PI in FP64 on a 10k-node preferential-attachment graph
     "pa_n10k": dict(spec=GraphSpec(n=10_000, p_dangling=0.15, cap=500, mean_out=0.0, p_local=0.0,
@@ -111,6 +112,19 @@ WORKLOADS = {
     "ppr_n2m_k256": dict(spec=GraphSpec(n=2_000_000, p_dangling=0.2, cap=5000, mean_out=18.75, p_local=0.7,
                                         chain_frac=0.1, seed=BASE_SEED + 3),
                          d=0.85, tol=1e-6, fluid="f32", k=256, max_seeds=1000),
+    # the 1M- and 10M-node graphs with every link reversed (P transposed): the heavy-tailed
+    # in-degrees become out-degrees, and the dangling nodes become zero-in-degree nodes of E
+    "web_n1m_t": dict(spec=GraphSpec(n=1_000_000, p_dangling=0.2, cap=5000, mean_out=10.0, p_local=0.7,
+                                     chain_frac=0.1, seed=BASE_SEED + 1, transpose=True),
+                      d=0.85, tol=1e-8, fluid="f32"),
+    "web_n10m_t": dict(spec=GraphSpec(n=10_000_000, p_dangling=0.2, cap=5000, mean_out=18.75, p_local=0.7,
+                                      chain_frac=0.1, seed=BASE_SEED + 2, transpose=True),
+                       d=0.85, tol=1e-8, fluid="f32"),
+    # a web-like graph where E dominates (E/N about 0.87, 22 levels; the paper's Dataset 2 has
+    # E/N = 0.91): 87% of the nodes sit on zero-in-degree chains of 20 that feed a small core
+    "web_n10m_e": dict(spec=GraphSpec(n=10_000_000, p_dangling=0.02, cap=5000, mean_out=18.75, p_local=0.7,
+                                      chain_frac=0.87, chain_min=20, chain_max=20, seed=BASE_SEED + 5),
+                       d=0.85, tol=1e-8, fluid="f32"),
     # serving: four resident graphs
     "serve_4g": dict(specs=[GraphSpec(n=n, p_dangling=0.2, cap=5000, mean_out=18.75, p_local=0.7,
                                       chain_frac=0.1, seed=BASE_SEED + 4 + 1000 * i)
@@ -134,6 +148,8 @@ def generate(spec: GraphSpec):
     got = lib.gen_graph_fill(ctypes.byref(p), src.ctypes.data, dst.ctypes.data)
     if got != total:
         raise RuntimeError(f"generator wrote {got} of {total} links")
+    if spec.transpose:
+        return spec.n, dst, src
     return spec.n, src, dst
 
 
