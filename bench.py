@@ -293,6 +293,8 @@ def transposed_leg(di, workloads, torch, flush, name="web_n10m_t"):
                      "pushed_per_L": inf["pushed_edges"] / g.stats["L"], "residual_l1": inf["residual_l1"]}
     ms, inf = timed(lambda: di.di_power_iter(g, B, d, tol, max_iters=MAX_SWEEPS, X_out=X)[1])
     out["pi"] = {"ms_to_residual": ms, "iterations": inf["sweeps"], "residual_l1": inf["residual_l1"]}
+    ms, inf = timed(lambda: di.di_power_iter_push(g, B, d, tol, max_iters=MAX_SWEEPS, X_out=X)[1])
+    out["pi_push"] = {"ms_to_residual": ms, "iterations": inf["sweeps"], "residual_l1": inf["residual_l1"]}
     return out
 
 
@@ -510,6 +512,15 @@ def run_gpu(args):
         ms = a.elapsed_time(b)
         legs["pi"] = {"ms_to_residual": ms, "GTEPS": pinf["pushed_edges"] / (ms * 1e-3) / 1e9,
                       "iterations": pinf["sweeps"], "residual_l1": pinf["residual_l1"]}
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, qinf = di.di_power_iter_push(g, B, D, TOL, max_iters=MAX_SWEEPS, X_out=X)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        legs["pi_push"] = {"ms_to_residual": ms, "GTEPS": qinf["pushed_edges"] / (ms * 1e-3) / 1e9,
+                           "iterations": qinf["sweeps"], "residual_l1": qinf["residual_l1"]}
         legs["transposed"] = transposed_leg(di, workloads, torch, flush)
         legs["e_dominated"] = transposed_leg(di, workloads, torch, flush, name="web_n10m_e")
     if not args.no_legs:

@@ -187,6 +187,23 @@ di_status di_power_iter(di_graph *g, const double *B, double d, double tol, int3
                         double *X_out, double *residual_out, di_solve_info *info, void *stream);
 
 /*
+ * di_power_iter_push — power iteration per column PI' (Section 2.5 "PI'": column vectors l_out,
+ * i.e. a push over the out-links), the same Jacobi iteration as di_power_iter with the same
+ * stopping rule ||X_(k+1) - X_k||_1 <= tol (the paper's tables give PI and PI' equal iteration
+ * counts). It pushes the increments X_(k+1) - X_k = P (X_k - X_(k-1)) with the D-iteration's
+ * push kernels, a self-link being a plain link: the k-th sweep is iteration k.
+ *   fluid  DI_FLUID_F64: FP64 increments; the iterates and the iteration count are PI's.
+ *          DI_FLUID_F32: FP32 increments (faster push) with FP64 X; the reported residual is
+ *          the exact FP64 ||B + P.X - X||_1 (= the next increment), with continuation sweeps
+ *          until it is <= tol, which adds iterations when FP32 rounding of the increments
+ *          exceeds tol.
+ * Other arguments and errors as di_power_iter; info->sweeps counts iterations.
+ */
+di_status di_power_iter_push(di_graph *g, const double *B, double d, double tol, int32_t max_iters,
+                             int32_t fluid, double *X_out, double *residual_out, di_solve_info *info,
+                             void *stream);
+
+/*
  * di_solve_batch — k independent D-iterations on one graph in one multi-RHS sweep loop: every
  * column r solves X_r = P.X_r + B_r and stops at its own tolerance tol[r]. Each column keeps its
  * own selection rule (Section 2.3; DI-SOP: |F_ir| > (r_r / L) * out_i); a node's out-links are

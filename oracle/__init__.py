@@ -89,6 +89,8 @@ def _load():
                             ctypes.POINTER(DiInfo)]
     lib.or_pi.restype = ctypes.c_int
     lib.or_pi.argtypes = [i64, vp, vp, vp, vp, dbl, dbl, i64, vp, ctypes.POINTER(PiInfo)]
+    lib.or_pi_push.restype = ctypes.c_int
+    lib.or_pi_push.argtypes = [i64, vp, vp, vp, dbl, dbl, i64, vp, ctypes.POINTER(PiInfo)]
     lib.or_pi_paper.restype = ctypes.c_int
     lib.or_pi_paper.argtypes = [i64, vp, vp, vp, dbl, dbl, i64, vp, ctypes.POINTER(PiInfo)]
     lib.or_residual.restype = dbl
@@ -193,6 +195,18 @@ def pi(g: Graph, B, d: float, tol: float, max_iters: int = 100000):
     info = PiInfo()
     rc = lib.or_pi(g.n, g.rp_in.ctypes.data, g.col_in.ctypes.data, g.outdeg.ctypes.data, pb, d, tol,
                    max_iters, X.ctypes.data, ctypes.byref(info))
+    return X, info.as_dict(), rc == 0
+
+
+def pi_push(g: Graph, B, d: float, tol: float, max_iters: int = 100000):
+    """Power iteration per column (PI'): the Jacobi iteration formed by scattering over the
+    out-links. Returns (X, info dict, converged)."""
+    lib = _load()
+    B, pb = _c(B, np.float64)
+    X = np.zeros(g.n, np.float64)
+    info = PiInfo()
+    rc = lib.or_pi_push(g.n, g.rp_out.ctypes.data, g.col_out.ctypes.data, pb, d, tol, max_iters, X.ctypes.data,
+                        ctypes.byref(info))
     return X, info.as_dict(), rc == 0
 
 

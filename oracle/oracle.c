@@ -23,6 +23,7 @@
  *   or_di_e          the same after one visit of every node of E in level order (E converges
  *                    in finitely many steps, Section 2.4).
  *   or_pi            power iteration (Jacobi) on X = P.X + B (Section 2.3, Section 2.5 "PI").
+ *   or_pi_push       the same iteration per column, scattering over l_out (Section 2.5 "PI'").
  *   or_pi_paper      the paper's normalised PageRank power iteration (Section 2.5 "PI").
  *   or_residual      F* = B + P.H - H, the fluid that H still owes (used for a-posteriori bounds).
  */
@@ -307,6 +308,36 @@ int or_pi(int64_t n, const int64_t *rp_in, const int32_t *col_in, const int32_t 
                 acc += d * X[j] / (double)outdeg[j];
             }
             Xn[i] = acc;
+        }
+        res = 0.0;
+        for (int64_t i = 0; i < n; i++) { res += fabs(Xn[i] - X[i]); X[i] = Xn[i]; }
+        info->iterations++;
+    }
+    info->residual = res;
+    free(Xn);
+    return res <= tol ? 0 : 1;
+}
+
+/*
+ * Power iteration per column (Section 2.5 "PI'"): the same Jacobi iteration on X = P.X + B as
+ * or_pi, formed by the columns of P: X_new = B, then every node i with out_i > 0 adds
+ * d * X[i] / out_i to each of its out-neighbours (its own self-link included, as a plain entry
+ * of P). Stops on PI's criterion ||X_new - X||_1 <= tol (the printed PI' scales its threshold
+ * twice; the paper's tables give PI and PI' the same iteration counts).
+ */
+int or_pi_push(int64_t n, const int64_t *rp_out, const int32_t *col_out, const double *B, double d, double tol,
+               int64_t max_iters, double *X, or_pi_info *info) {
+    double *Xn = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    memset(info, 0, sizeof(*info));
+    for (int64_t i = 0; i < n; i++) X[i] = 0.0;
+    double res = INFINITY;
+    while (res > tol && info->iterations < max_iters) {
+        for (int64_t i = 0; i < n; i++) Xn[i] = B[i];
+        for (int64_t i = 0; i < n; i++) {
+            int64_t o = rp_out[i + 1] - rp_out[i];
+            if (o == 0) continue;
+            double transit = d * X[i] / (double)o;
+            for (int64_t k = rp_out[i]; k < rp_out[i + 1]; k++) Xn[col_out[k]] += transit;
         }
         res = 0.0;
         for (int64_t i = 0; i < n; i++) { res += fabs(Xn[i] - X[i]); X[i] = Xn[i]; }

@@ -19,7 +19,7 @@ __all__ = [
     "build", "load", "DiError", "Graph",
     "DI_CYC", "DI_SOP", "DI_FLUID_F32", "DI_FLUID_F64",
     "di_graph_create", "di_graph_destroy", "di_graph_stats_get", "di_graph_export",
-    "di_solve", "di_solve_ex", "di_power_iter", "di_solve_batch", "di_ppr_batch", "di_residual_noalloc",
+    "di_solve", "di_solve_ex", "di_power_iter", "di_power_iter_push", "di_solve_batch", "di_ppr_batch", "di_residual_noalloc",
     "di_server_create", "di_server_submit", "di_server_wait", "di_server_destroy", "Server",
     "di_last_error", "di_version",
 ]
@@ -119,6 +119,8 @@ def load(path: str | None = None):
     lib.di_solve_ex.argtypes = [vp, vp, dbl, dbl, ctypes.POINTER(SolveOpts), vp, vp, ctypes.POINTER(SolveInfo), vp]
     lib.di_power_iter.restype = st
     lib.di_power_iter.argtypes = [vp, vp, dbl, dbl, i32, vp, vp, ctypes.POINTER(SolveInfo), vp]
+    lib.di_power_iter_push.restype = st
+    lib.di_power_iter_push.argtypes = [vp, vp, dbl, dbl, i32, i32, vp, vp, ctypes.POINTER(SolveInfo), vp]
     lib.di_solve_batch.restype = st
     lib.di_solve_batch.argtypes = [vp, i32, vp, dbl, vp, ctypes.POINTER(SolveOpts), vp, vp, ctypes.POINTER(SolveInfo), vp]
     lib.di_ppr_batch.restype = st
@@ -277,6 +279,18 @@ def di_power_iter(g: Graph, B, d: float, tol: float, max_iters: int = 0, X_out=N
     info = SolveInfo()
     res = ctypes.c_double()
     _check(load().di_power_iter(g.handle, _ptr(B, np.float64), float(d), float(tol), int(max_iters),
+                                _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)), info)
+    return X, info.as_dict()
+
+
+def di_power_iter_push(g: Graph, B, d: float, tol: float, max_iters: int = 0, fluid: int = DI_FLUID_F32,
+                       X_out=None):
+    """Power iteration per column (PI', a push over the out-links): the Jacobi iteration on
+    X = P.X + B with the same stopping rule as di_power_iter. Returns (X, info)."""
+    X = X_out if X_out is not None else _like(B, g.n, np.float64)
+    info = SolveInfo()
+    res = ctypes.c_double()
+    _check(load().di_power_iter_push(g.handle, _ptr(B, np.float64), float(d), float(tol), int(max_iters), int(fluid),
                                 _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)), info)
     return X, info.as_dict()
 

@@ -130,6 +130,8 @@ struct SolveCtl {
     uint32_t ticket;          // last-block-done counter of the reductions
     int32_t body_runs;        // executions of the WHILE body (kernel-launch accounting)
     int32_t chunk_next;       // dynamic work counter over the segments
+    int32_t plain_loops;      // 1: a self-link is a plain link (power iteration per column), no
+                              //    closed form for loop nodes
     unsigned long long front_total;  // frontier entries over all sweeps
 };
 

@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
     if (ctl->done) return;
     const double r = ctl->r, d = ctl->d;
     const bool cyc = ctl->schedule == DI_CYC || ctl->force_cyc;
+    const bool plain_loops = ctl->plain_loops != 0;
     const double thr = ctl->L > 0.0 ? r / ctl->L : 0.0;
     const float thr_f = (float)thr, d_f = (float)d;
     const uint64_t keep = policy_evict_last();
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
             T share = (T)0;
             const int32_t o = info[j] & 0x7fffffff;
             if (sel >> j & 1u) {
-                const bool lp = info[j] < 0;
+                const bool lp = !plain_loops && info[j] < 0;
                 st_keep(F + i, (T)0, keep);
                 double t;
                 visit_math(f[j], o, lp, d, d_f, t, share);
@@ -433,6 +434,7 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
     __shared__ int32_t s_u[8][32];
     __shared__ T s_s[8][32];
     if (ctl->done) return;
+    const bool loops = ctl->plain_loops != 0;   // self-links pushed as plain links
     const uint64_t pol = policy_evict_last();
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5;
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
             const int64_t cb = b + c * kChunk, ce = min(cb + kChunk, e);
             for (int64_t k = cb + lane; k < ce; k += 32) {
                 const int32_t j = __ldcs(col_out + k);
-                if (j != u) red_keep(&F[j], sh, pol);
+                if (j != u || loops) red_keep(&F[j], sh, pol);
             }
         }
     }
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
             }
 #pragma unroll
             for (int v = 0; v < kPushVT; v++)
-                if (own[v] >= 0 && j[v] != s_u[w][own[v]]) red_keep(&F[j[v]], s_s[w][own[v]], pol);
+                if (own[v] >= 0 && (j[v] != s_u[w][own[v]] || loops)) red_keep(&F[j[v]], s_s[w][own[v]], pol);
         }
         __syncwarp();
     }
@@ -522,6 +524,7 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
     __shared__ int4 s_rec[8][32];
     __shared__ int s_chunk, s_batch;
     if (ctl->done) return;
+    const bool loops = ctl->plain_loops != 0;   // self-links pushed as plain links
     const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5;
@@ -547,7 +550,7 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
             const int64_t cb = b + c * kChunk, ce = min(cb + kChunk, e);
             for (int64_t k = cb + lane; k < ce; k += 32) {
                 const int32_t jr = ld_stream(col_push + k, stream);
-                if ((jr & 0x7fffffff) != u) far_add(jr, sh);
+                if ((jr & 0x7fffffff) != u || loops) far_add(jr, sh);
             }
         }
     }
@@ -608,7 +611,7 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                 for (int v = 0; v < kPushVT; v++) {
                     const int e = e0 + v;
                     jr[v] = 0;
-                    uu[v] = 0;   // target 0 and source 0 reads as a loop link: skipped
+                    uu[v] = 0;
                     ss[v] = 0.f;
                     if (e < total) {
                         if (e >= next) {
@@ -625,7 +628,7 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
 #pragma unroll
                 for (int v = 0; v < kPushVT; v++) {
                     const int32_t j = jr[v] & 0x7fffffff;
-                    if (j == uu[v]) continue;
+                    if (e0 + v >= total || (j == uu[v] && !loops)) continue;
                     const unsigned off = (unsigned)(j - lo);
                     if (use_win && off < (unsigned)kWin) atomicAdd(&s_win[off], ss[v]);
                     else far_add(jr[v], ss[v]);
@@ -1147,9 +1150,11 @@ static void launch_refine(di_graph *g, const Launch &l, double d, cudaStream_t s
     DI_CHECK_CUDA(cudaGetLastError());
 }
 
-static void write_ctl(di_graph *g, double d, double tol, int schedule, int max_sweeps, cudaStream_t s) {
+static void write_ctl(di_graph *g, double d, double tol, int schedule, int max_sweeps, int plain_loops,
+                      cudaStream_t s) {
     SolveCtl &c = *g->ws.ctl_host;
     memset(&c, 0, sizeof(c));
+    c.plain_loops = plain_loops;
     c.d = d;
     c.tol = tol;
     c.L = (double)g->L;
@@ -1173,14 +1178,14 @@ static void check_common(di_graph *g, const double *B, double d, double tol, con
 
 template <class T>
 static void solve_impl(di_graph *g, const double *B, double d, double tol, int schedule, int max_sweeps, int refine,
-                       int host_loop, int profile, int e_prediffuse, double *X_out, double *residual_out,
-                       di_solve_info *info, cudaStream_t s) {
+                       int host_loop, int profile, int e_prediffuse, int plain_loops, double *X_out,
+                       double *residual_out, di_solve_info *info, cudaStream_t s) {
     ensure_workspace<T>(g);
     Workspace &ws = g->ws;
     const Launch l = launch_shape<T>(g);
     SolveCtl *ctl = ws.ctl.as<SolveCtl>();
     to_device(ws.B.p, B, sizeof(double) * (size_t)g->n, s);
-    write_ctl(g, d, tol, schedule, max_sweeps, s);
+    write_ctl(g, d, tol, schedule, max_sweeps, plain_loops, s);
     if (profile) host_loop = 1;
     KernelClock kc(profile != 0, s);
     cudaEvent_t e0, e1;
@@ -1293,12 +1298,34 @@ di_status solve_single(di_graph *g, const double *B, double d, double tol, const
         DeviceGuard dg(g->dev.device);
         if (o.fluid == DI_FLUID_F32)
             solve_impl<float>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
-                              o.e_prediffuse != 0, X_out,
+                              o.e_prediffuse != 0, 0, X_out,
                               residual_out, info, s);
         else
             solve_impl<double>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
-                               o.e_prediffuse != 0, X_out,
+                               o.e_prediffuse != 0, 0, X_out,
                                residual_out, info, s);
+    });
+}
+
+// Power iteration per column (PI', Section 2.5): in increment form the Jacobi iterate obeys
+// X_(k+1) - X_k = P (X_k - X_(k-1)), so a DI-CYC sweep that pushes every node's increment over
+// its out-links, the self-link as a plain link (no loop closed form), is PI' iteration k: H holds
+// X_k and ||F||_1 is PI's ||X_(k+1) - X_k||_1. FP64 increments give PI's iterates and counts;
+// FP32 increments are followed by the exact FP64 residual B + P.H - H (that same difference
+// computed exactly) and continuation sweeps from it.
+di_status power_iter_push(di_graph *g, const double *B, double d, double tol, int32_t max_iters, int32_t fluid,
+                          double *X_out, double *residual_out, di_solve_info *info, cudaStream_t s) {
+    return guarded([&] {
+        check_common(g, B, d, tol, X_out);
+        DI_REQUIRE(fluid == DI_FLUID_F32 || fluid == DI_FLUID_F64, DI_ERR_INVALID_ARG, "unknown fluid %d", fluid);
+        int mi = max_iters <= 0 ? 100000 : (max_iters > 1000000 ? 1000000 : max_iters);
+        std::unique_lock<std::mutex> lk(g->mu, std::try_to_lock);
+        DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
+        DeviceGuard dg(g->dev.device);
+        if (fluid == DI_FLUID_F32)
+            solve_impl<float>(g, B, d, tol, DI_CYC, mi, 1, 0, 0, 0, 1, X_out, residual_out, info, s);
+        else
+            solve_impl<double>(g, B, d, tol, DI_CYC, mi, 0, 0, 0, 0, 1, X_out, residual_out, info, s);
     });
 }
 
@@ -1315,7 +1342,7 @@ di_status power_iter(di_graph *g, const double *B, double d, double tol, int32_t
         Workspace &ws = g->ws;
         const Launch l = launch_shape<T>(g);
         to_device(ws.B.p, B, sizeof(double) * (size_t)g->n, s);
-        write_ctl(g, d, tol, DI_CYC, mi, s);
+        write_ctl(g, d, tol, DI_CYC, mi, 0, s);
         cudaEvent_t e0, e1;
         DI_CHECK_CUDA(cudaEventCreate(&e0));
         DI_CHECK_CUDA(cudaEventCreate(&e1));
@@ -1368,6 +1395,12 @@ di_status di_solve(di_graph *g, const double *B, double d, double tol, int32_t s
 di_status di_solve_ex(di_graph *g, const double *B, double d, double tol, const di_solve_opts *opts, double *X_out,
                       double *residual_out, di_solve_info *info, void *stream) {
     return di::solve_single(g, B, d, tol, opts, X_out, residual_out, info, (cudaStream_t)stream);
+}
+
+di_status di_power_iter_push(di_graph *g, const double *B, double d, double tol, int32_t max_iters,
+                             int32_t fluid, double *X_out, double *residual_out, di_solve_info *info,
+                             void *stream) {
+    return di::power_iter_push(g, B, d, tol, max_iters, fluid, X_out, residual_out, info, (cudaStream_t)stream);
 }
 
 di_status di_power_iter(di_graph *g, const double *B, double d, double tol, int32_t max_iters, double *X_out,

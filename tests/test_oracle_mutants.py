@@ -51,6 +51,11 @@ MUTANTS = {
     "peel_start": ("if (indeg[v] == 0) { queue[tail++]", "if (indeg[v] <= 1) { queue[tail++]"),
     # residual with the wrong sign of H
     "residual_sign": ("Fstar[i] = acc - H[i];", "Fstar[i] = acc + H[i];"),
+    # PI' skips the self-link (treats a loop like the D-iteration's closed form)
+    "pi_push_skips_loop": ("for (int64_t k = rp_out[i]; k < rp_out[i + 1]; k++) Xn[col_out[k]] += transit;",
+                           "for (int64_t k = rp_out[i]; k < rp_out[i + 1]; k++) if (col_out[k] != i) Xn[col_out[k]] += transit;"),
+    # PI' divides by out + 1
+    "pi_push_divisor": ("double transit = d * X[i] / (double)o;", "double transit = d * X[i] / (double)(o + 1);"),
     # E pre-diffusion in id order, ignoring the levels
     "e_prepass_id_order": ("if (e_mask[i] && e_level[i] == l) {", "if (e_mask[i] && l == 0) {"),
     # E pre-diffusion skips the last level

@@ -265,3 +265,30 @@ def test_pi_iteration_count_geometric():
     assert ok
     assert n * b * D ** (k - 1) <= tol < n * b * D ** (k - 2)
     assert info["residual"] == pytest.approx(n * b * D ** (k - 1), rel=1e-9)
+
+
+# ---------------------------------------------------------------- PI' (power iteration per column)
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pi_push_iterates_equal_pull_iterates_and_dense(seed):
+    # the column form scatters d X_i / out_i over l_out; the row form gathers it over l_in; both
+    # are the same Jacobi iterate of X = P.X + B (Section 2.5 PI and PI'), here checked iterate by
+    # iterate, and their fixed point is the dense solve's
+    n = [20, 60, 150, 200, 90, 120][seed]
+    d = [0.85, 0.95, 0.5, 0.85, 0.99, 0.7][seed]
+    spec = workloads.GraphSpec(n=n, p_dangling=0.15, cap=25, mean_out=4.0, p_local=0.5, window=10,
+                               chain_frac=0.1, p_loop=0.3, seed=1100 + seed)
+    n, src, dst = workloads.generate(spec)
+    g = oracle.build(n, src, dst)
+    assert g.O > 0                              # self-links take part as plain entries of P
+    B = workloads.uniform(1200 + seed, 1, n) + 0.01
+    for k in (1, 2, 3, 7):
+        Xr, _, _ = oracle.pi(g, B, d, 0.0, max_iters=k)
+        Xc, ic, _ = oracle.pi_push(g, B, d, 0.0, max_iters=k)
+        assert ic["iterations"] == k
+        assert np.abs(Xc - Xr).sum() <= 1e-13 * np.abs(Xr).sum()
+    Xc, ic, ok = oracle.pi_push(g, B, d, 1e-13 * B.sum())
+    Xr, ir, ok2 = oracle.pi(g, B, d, 1e-13 * B.sum())
+    assert ok and ok2 and abs(ic["iterations"] - ir["iterations"]) <= 1
+    X = np.linalg.solve(dense_I_minus_P(n, src, dst, d), B)
+    assert rel_l1(Xc, X) <= 1e-11
