@@ -187,6 +187,27 @@ di_status di_power_iter(di_graph *g, const double *B, double d, double tol, int3
                         double *X_out, double *residual_out, di_solve_info *info, void *stream);
 
 /*
+ * di_solve_resume — D-iteration from a given state (H0, F0) instead of (0, B) (Section 2.5: the
+ * visit keeps X = H + (I - P)^-1 F for any state, so a run can stop and continue).
+ *   B       double[n] (host or device), >= 0 and finite: the problem X = P.X + B.
+ *   H0      double[n] (host or device), finite: the starting history.
+ *   F0      double[n] (host or device) or NULL. A run's final fluid (F_out below) resumes that
+ *           run. NULL starts from the exact residual F0 = B + P.H0 - H0, which makes any
+ *           approximate solution H0 (for instance the solution for an earlier B) a warm start.
+ *           The fluid may be negative: a node is selected on |F_i|.
+ *   F_out   double[n] (host or device) or NULL: the final fluid, the checkpoint that, with X_out
+ *           as H0, resumes this run. After refinement it is the exact residual, rounded to the
+ *           fluid's type.
+ *   opts    as di_solve_ex (nullable).
+ * X_out, residual_out, info, stream and errors as di_solve_ex. With refinement (the default for
+ * FP32 fluid) the result is X = P.X + B's whatever F0 was; without it, the run converges to
+ * H0 + (I - P)^-1 F0, which is X only when F0 is a state of this problem.
+ */
+di_status di_solve_resume(di_graph *g, const double *B, const double *H0, const double *F0, double d, double tol,
+                          const di_solve_opts *opts, double *X_out, double *F_out, double *residual_out,
+                          di_solve_info *info, void *stream);
+
+/*
  * di_power_iter_push — power iteration per column PI' (Section 2.5 "PI'": column vectors l_out,
  * i.e. a push over the out-links), the same Jacobi iteration as di_power_iter with the same
  * stopping rule ||X_(k+1) - X_k||_1 <= tol (the paper's tables give PI and PI' equal iteration

@@ -87,6 +87,8 @@ def _load():
     lib.or_di_e.restype = ctypes.c_int
     lib.or_di_e.argtypes = [i64, i64, vp, vp, vp, vp, vp, ctypes.c_int32, vp, dbl, dbl, ctypes.c_int, i64, vp, vp,
                             ctypes.POINTER(DiInfo)]
+    lib.or_di_from.restype = ctypes.c_int
+    lib.or_di_from.argtypes = [i64, i64, vp, vp, vp, vp, vp, dbl, dbl, ctypes.c_int, i64, vp, vp, ctypes.POINTER(DiInfo)]
     lib.or_pi.restype = ctypes.c_int
     lib.or_pi.argtypes = [i64, vp, vp, vp, vp, dbl, dbl, i64, vp, ctypes.POINTER(PiInfo)]
     lib.or_pi_push.restype = ctypes.c_int
@@ -184,6 +186,19 @@ def di_e(g: Graph, B, d: float, tol: float, schedule: int = SOP, max_cycles: int
     rc = lib.or_di_e(g.n, g.L, g.rp_out.ctypes.data, g.col_out.ctypes.data, g.loop.ctypes.data,
                      e_mask.ctypes.data, level.ctypes.data, n_levels, pb, d, tol, schedule, max_cycles,
                      H.ctypes.data, F.ctypes.data, ctypes.byref(info))
+    return H, F, info.as_dict(), rc == 0
+
+
+def di_from(g: Graph, H0, F0, d: float, tol: float, schedule: int = SOP, max_cycles: int = 100_000):
+    """D-iteration from the state (H0, F0) instead of (0, B). Returns (H, F, info dict, converged)."""
+    lib = _load()
+    H0, p_h = _c(H0, np.float64)
+    F0, p_f = _c(F0, np.float64)
+    H = np.zeros(g.n, np.float64)
+    F = np.zeros(g.n, np.float64)
+    info = DiInfo()
+    rc = lib.or_di_from(g.n, g.L, g.rp_out.ctypes.data, g.col_out.ctypes.data, g.loop.ctypes.data, p_h, p_f, d,
+                        tol, schedule, max_cycles, H.ctypes.data, F.ctypes.data, ctypes.byref(info))
     return H, F, info.as_dict(), rc == 0
 
 

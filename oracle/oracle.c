@@ -22,6 +22,8 @@
  *   or_di            DI-CYC and DI-SOP (Section 2.3, Section 2.5), one node visit at a time.
  *   or_di_e          the same after one visit of every node of E in level order (E converges
  *                    in finitely many steps, Section 2.4).
+ *   or_di_from       the same from a given state (H, F) instead of (0, B): resuming a
+ *                    checkpoint, or a warm start whose fluid is the exact residual of H.
  *   or_pi            power iteration (Jacobi) on X = P.X + B (Section 2.3, Section 2.5 "PI").
  *   or_pi_push       the same iteration per column, scattering over l_out (Section 2.5 "PI'").
  *   or_pi_paper      the paper's normalised PageRank power iteration (Section 2.5 "PI").
@@ -208,18 +210,22 @@ static void visit(int64_t i, double d, const int64_t *rp_out, const int32_t *col
     info->pushed_edges += o;
 }
 
+/* ||F||_1; with F >= 0 (every run from H = 0, F = B) this is the paper's sum of the fluid */
 static double sum_fluid(int64_t n, const double *F) {
     double r = 0.0;
-    for (int64_t i = 0; i < n; i++) r += F[i];
+    for (int64_t i = 0; i < n; i++) r += fabs(F[i]);
     return r;
 }
 
 /*
  * D-iteration from H = 0, F = B (Section 2.5). schedule 0 = DI-CYC: in each cycle visit
- * i = 0..N-1 when F_i > 0. schedule 1 = DI-SOP: r = sum F is taken once at the start of the
- * cycle and i is visited when F_i > (r / L) * out_i (Section 2.3); a DI-SOP cycle that visits
- * nothing is run again as a DI-CYC cycle. The loop stops when sum F <= tol after a cycle, or
+ * i = 0..N-1 when F_i != 0. schedule 1 = DI-SOP: r = ||F||_1 is taken once at the start of the
+ * cycle and i is visited when |F_i| > (r / L) * out_i (Section 2.3); a DI-SOP cycle that visits
+ * nothing is run again as a DI-CYC cycle. The loop stops when ||F||_1 <= tol after a cycle, or
  * after max_cycles cycles (max_cycles < 0: no limit). Returns 0 when converged, 1 otherwise.
+ * With F >= 0, as in every run from (0, B), the tests read exactly as the paper's F_i > 0,
+ * F_i > (r / L) * out_i and sum F; a resumed state may carry negative fluid (a warm start whose
+ * H overshoots X), which the visit moves like any other by linearity.
  */
 static int run_cycles(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out, const uint8_t *loop,
                       double d, double tol, int schedule, int64_t max_cycles, double *H, double *F,
@@ -231,16 +237,16 @@ static int run_cycles(int64_t n, int64_t L, const int64_t *rp_out, const int32_t
             double r_cycle = r;
             for (int64_t i = 0; i < n; i++) {
                 double out_i = (double)(rp_out[i + 1] - rp_out[i]);
-                if (F[i] > (r_cycle / (double)L) * out_i) visit(i, d, rp_out, col_out, loop, H, F, info);
+                if (fabs(F[i]) > (r_cycle / (double)L) * out_i) visit(i, d, rp_out, col_out, loop, H, F, info);
             }
             if (info->visits == visits_before) {
                 info->fallback_cycles++;
                 for (int64_t i = 0; i < n; i++)
-                    if (F[i] > 0.0) visit(i, d, rp_out, col_out, loop, H, F, info);
+                    if (F[i] != 0.0) visit(i, d, rp_out, col_out, loop, H, F, info);
             }
         } else {
             for (int64_t i = 0; i < n; i++)
-                if (F[i] > 0.0) visit(i, d, rp_out, col_out, loop, H, F, info);
+                if (F[i] != 0.0) visit(i, d, rp_out, col_out, loop, H, F, info);
         }
         info->cycles++;
         r = sum_fluid(n, F);
@@ -255,6 +261,19 @@ int or_di(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out, c
           double *H, double *F, or_di_info *info) {
     memset(info, 0, sizeof(*info));
     for (int64_t i = 0; i < n; i++) { H[i] = 0.0; F[i] = B[i]; }
+    return run_cycles(n, L, rp_out, col_out, loop, d, tol, schedule, max_cycles, H, F, info);
+}
+
+/*
+ * D-iteration from a given state (H0, F0) (copied into H, F): the identity X = H + (I - P)^-1 F
+ * holds for the state of any run, so resuming a run's checkpoint continues it exactly, and
+ * F0 = B + P.H0 - H0 turns any approximate solution H0 into a warm start for B.
+ */
+int or_di_from(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out, const uint8_t *loop,
+               const double *H0, const double *F0, double d, double tol, int schedule, int64_t max_cycles,
+               double *H, double *F, or_di_info *info) {
+    memset(info, 0, sizeof(*info));
+    for (int64_t i = 0; i < n; i++) { H[i] = H0[i]; F[i] = F0[i]; }
     return run_cycles(n, L, rp_out, col_out, loop, d, tol, schedule, max_cycles, H, F, info);
 }
 

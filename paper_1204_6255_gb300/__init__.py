@@ -19,7 +19,7 @@ __all__ = [
     "build", "load", "DiError", "Graph",
     "DI_CYC", "DI_SOP", "DI_FLUID_F32", "DI_FLUID_F64",
     "di_graph_create", "di_graph_destroy", "di_graph_stats_get", "di_graph_export",
-    "di_solve", "di_solve_ex", "di_power_iter", "di_power_iter_push", "di_solve_batch", "di_ppr_batch", "di_residual_noalloc",
+    "di_solve", "di_solve_ex", "di_solve_resume", "di_power_iter", "di_power_iter_push", "di_solve_batch", "di_ppr_batch", "di_residual_noalloc",
     "di_server_create", "di_server_submit", "di_server_wait", "di_server_destroy", "Server",
     "di_last_error", "di_version",
 ]
@@ -119,6 +119,9 @@ def load(path: str | None = None):
     lib.di_solve_ex.argtypes = [vp, vp, dbl, dbl, ctypes.POINTER(SolveOpts), vp, vp, ctypes.POINTER(SolveInfo), vp]
     lib.di_power_iter.restype = st
     lib.di_power_iter.argtypes = [vp, vp, dbl, dbl, i32, vp, vp, ctypes.POINTER(SolveInfo), vp]
+    lib.di_solve_resume.restype = st
+    lib.di_solve_resume.argtypes = [vp, vp, vp, vp, dbl, dbl, ctypes.POINTER(SolveOpts), vp, vp, vp,
+                                    ctypes.POINTER(SolveInfo), vp]
     lib.di_power_iter_push.restype = st
     lib.di_power_iter_push.argtypes = [vp, vp, dbl, dbl, i32, i32, vp, vp, ctypes.POINTER(SolveInfo), vp]
     lib.di_solve_batch.restype = st
@@ -270,6 +273,22 @@ def di_solve_ex(g: Graph, B, d: float, tol: float, schedule: int = DI_SOP, fluid
     res = ctypes.c_double()
     _check(load().di_solve_ex(g.handle, _ptr(B, np.float64), float(d), float(tol), ctypes.byref(o),
                               _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)), info)
+    return X, info.as_dict()
+
+
+def di_solve_resume(g: Graph, B, H0, d: float, tol: float, F0=None, F_out=None, schedule: int = DI_SOP,
+                    fluid: int = DI_FLUID_F32, max_sweeps: int = 0, refine: int = 0, host_loop: int = 0,
+                    profile: int = 0, e_prediffuse: int = 0, X_out=None):
+    """D-iteration from the state (H0, F0) (F0 None: the exact residual of H0, a warm start).
+    Returns (X, info); the final fluid goes to F_out when given."""
+    X = X_out if X_out is not None else _like(B, g.n, np.float64)
+    o = SolveOpts(int(schedule), int(fluid), int(max_sweeps), int(refine), int(host_loop), 0, int(profile),
+                  int(e_prediffuse))
+    info = SolveInfo()
+    res = ctypes.c_double()
+    _check(load().di_solve_resume(g.handle, _ptr(B, np.float64), _ptr(H0, np.float64), _ptr(F0, np.float64),
+                                  float(d), float(tol), ctypes.byref(o), _ptr(X, np.float64), _ptr(F_out, np.float64),
+                                  ctypes.byref(res), ctypes.byref(info), _stream(B, X)), info)
     return X, info.as_dict()
 
 

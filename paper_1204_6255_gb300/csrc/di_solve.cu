@@ -43,6 +43,29 @@ __global__ void k_init(const double *B, int32_t n, T *F, double *H, SolveCtl *ct
     if (bad) ctl->status = 1;
 }
 
+// Resumed solve: B is checked like k_init does, H already holds the given history, and F takes
+// the given fluid (staged as FP64) unless F0 is NULL (the caller then forms the exact residual).
+template <class T>
+__global__ void k_resume_init(const double *B, const double *F0, int32_t n, T *F, const double *H, SolveCtl *ctl) {
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double b = B[i];
+        if (!(b >= 0.0) || isinf(b) || !isfinite(H[i])) bad = true;
+        if (F0) {
+            const double f = F0[i];
+            if (!isfinite(f)) bad = true;
+            F[i] = (T)f;
+        }
+    }
+    if (bad) ctl->status = 1;
+}
+
+template <class T>
+__global__ void k_fluid_to_double(const T *F, int32_t n, double *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)F[i];
+}
+
 // Last-block-done FP64 sum of the per-block partials; returns true in the finishing block,
 // where `total` holds the grand total (thread 0 only needs it).
 __device__ __forceinline__ bool finish_sum(double s, double *partials, SolveCtl *ctl, double *scratch, double &total) {
@@ -1179,7 +1202,8 @@ static void check_common(di_graph *g, const double *B, double d, double tol, con
 template <class T>
 static void solve_impl(di_graph *g, const double *B, double d, double tol, int schedule, int max_sweeps, int refine,
                        int host_loop, int profile, int e_prediffuse, int plain_loops, double *X_out,
-                       double *residual_out, di_solve_info *info, cudaStream_t s) {
+                       double *residual_out, di_solve_info *info, cudaStream_t s, const double *H0 = nullptr,
+                       const double *F0 = nullptr, double *F_out = nullptr) {
     ensure_workspace<T>(g);
     Workspace &ws = g->ws;
     const Launch l = launch_shape<T>(g);
@@ -1194,9 +1218,25 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
     int rounds = 0;
     try {
         DI_CHECK_CUDA(cudaEventRecord(e0, s));
-        kc.run(KC_REFINE, 1, [&] {
-            k_init<T><<<l.ew_blocks, 256, 0, s>>>(ws.B.as<double>(), g->n, ws.F.as<T>(), ws.H.as<double>(), ctl);
-        });
+        if (!H0) {
+            kc.run(KC_REFINE, 1, [&] {
+                k_init<T><<<l.ew_blocks, 256, 0, s>>>(ws.B.as<double>(), g->n, ws.F.as<T>(), ws.H.as<double>(), ctl);
+            });
+        } else {
+            // resumed state: H from the caller; F from the caller (staged as FP64 in y0) or, when
+            // F0 is NULL, the exact residual B + P.H - H of the given history
+            to_device(ws.H.p, H0, sizeof(double) * (size_t)g->n, s);
+            double *stage = nullptr;
+            if (F0) {
+                stage = reinterpret_cast<double *>(ws.y0.p);
+                to_device(stage, F0, sizeof(double) * (size_t)g->n, s);
+            }
+            kc.run(KC_REFINE, 1, [&] {
+                k_resume_init<T><<<l.ew_blocks, 256, 0, s>>>(ws.B.as<double>(), stage, g->n, ws.F.as<T>(),
+                                                             ws.H.as<double>(), ctl);
+            });
+            if (!F0) kc.run(KC_REFINE, g->n_heavy_in_chunks > 0 ? 3 : 2, [&] { launch_refine<T>(g, l, d, s); });
+        }
         if (e_prediffuse) {
             for (size_t lv = 0; lv + 1 < g->e_level_off.size(); lv++) {
                 const int64_t at = g->e_level_off[lv], cnt = g->e_level_off[lv + 1] - at;
@@ -1243,6 +1283,13 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
         }
         DI_CHECK_CUDA(cudaEventRecord(e1, s));
         from_device(X_out, ws.H.p, sizeof(double) * (size_t)g->n, s);
+        if (F_out) {
+            // the final fluid (after refinement: the exact residual, rounded to the fluid's type)
+            double *stage = reinterpret_cast<double *>(ws.y0.p);
+            k_fluid_to_double<T><<<l.ew_blocks, 256, 0, s>>>(ws.F.as<T>(), g->n, stage);
+            DI_CHECK_CUDA(cudaGetLastError());
+            from_device(F_out, stage, sizeof(double) * (size_t)g->n, s);
+        }
         read_ctl(g, s);
     } catch (...) {
         cudaEventDestroy(e0);
@@ -1313,6 +1360,31 @@ di_status solve_single(di_graph *g, const double *B, double d, double tol, const
 // X_k and ||F||_1 is PI's ||X_(k+1) - X_k||_1. FP64 increments give PI's iterates and counts;
 // FP32 increments are followed by the exact FP64 residual B + P.H - H (that same difference
 // computed exactly) and continuation sweeps from it.
+di_status solve_resume(di_graph *g, const double *B, const double *H0, const double *F0, double d, double tol,
+                       const di_solve_opts *opts, double *X_out, double *F_out, double *residual_out,
+                       di_solve_info *info, cudaStream_t s) {
+    return guarded([&] {
+        check_common(g, B, d, tol, X_out);
+        DI_REQUIRE(H0 != nullptr, DI_ERR_INVALID_ARG, "H0 is NULL");
+        di_solve_opts o;
+        memset(&o, 0, sizeof(o));
+        if (opts) o = *opts;
+        DI_REQUIRE(o.schedule == DI_CYC || o.schedule == DI_SOP, DI_ERR_INVALID_ARG, "unknown schedule %d", o.schedule);
+        DI_REQUIRE(o.fluid == DI_FLUID_F32 || o.fluid == DI_FLUID_F64, DI_ERR_INVALID_ARG, "unknown fluid %d", o.fluid);
+        int max_sweeps = o.max_sweeps <= 0 ? 100000 : (o.max_sweeps > 1000000 ? 1000000 : o.max_sweeps);
+        int refine = o.refine == 0 ? (o.fluid == DI_FLUID_F32) : (o.refine > 0);
+        std::unique_lock<std::mutex> lk(g->mu, std::try_to_lock);
+        DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
+        DeviceGuard dg(g->dev.device);
+        if (o.fluid == DI_FLUID_F32)
+            solve_impl<float>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
+                              o.e_prediffuse != 0, 0, X_out, residual_out, info, s, H0, F0, F_out);
+        else
+            solve_impl<double>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
+                               o.e_prediffuse != 0, 0, X_out, residual_out, info, s, H0, F0, F_out);
+    });
+}
+
 di_status power_iter_push(di_graph *g, const double *B, double d, double tol, int32_t max_iters, int32_t fluid,
                           double *X_out, double *residual_out, di_solve_info *info, cudaStream_t s) {
     return guarded([&] {
@@ -1395,6 +1467,12 @@ di_status di_solve(di_graph *g, const double *B, double d, double tol, int32_t s
 di_status di_solve_ex(di_graph *g, const double *B, double d, double tol, const di_solve_opts *opts, double *X_out,
                       double *residual_out, di_solve_info *info, void *stream) {
     return di::solve_single(g, B, d, tol, opts, X_out, residual_out, info, (cudaStream_t)stream);
+}
+
+di_status di_solve_resume(di_graph *g, const double *B, const double *H0, const double *F0, double d, double tol,
+                          const di_solve_opts *opts, double *X_out, double *F_out, double *residual_out,
+                          di_solve_info *info, void *stream) {
+    return di::solve_resume(g, B, H0, F0, d, tol, opts, X_out, F_out, residual_out, info, (cudaStream_t)stream);
 }
 
 di_status di_power_iter_push(di_graph *g, const double *B, double d, double tol, int32_t max_iters,

@@ -2,8 +2,8 @@
 
 Each case plants one mistake in a copy of oracle/oracle.c (a dropped term, a wrong sign, a wrong
 index or operand), compiles the copy on the CPU and runs the whole pin suite
-(test_oracle_build.py, test_oracle_solve.py, test_oracle_e.py) against it. Every mutant must fail
-at least one pin.
+(test_oracle_build.py, test_oracle_solve.py, test_oracle_e.py, test_oracle_resume.py) against it.
+Every mutant must fail at least one pin.
 """
 import os
 import subprocess
@@ -30,7 +30,7 @@ MUTANTS = {
     # dangling mass e never accumulated
     "e_dropped": ("info->e += transit;", "info->e += 0.0;"),
     # DI-SOP threshold without the out-degree factor
-    "sop_no_out": ("if (F[i] > (r_cycle / (double)L) * out_i)", "if (F[i] > (r_cycle / (double)L))"),
+    "sop_no_out": ("if (fabs(F[i]) > (r_cycle / (double)L) * out_i)", "if (fabs(F[i]) > (r_cycle / (double)L))"),
     # DI-SOP tie fallback missing (stalls, then stops on the cycle cap)
     "sop_no_fallback": ("if (info->visits == visits_before) {", "if (0) {"),
     # PI divides by the in-degree of the neighbour
@@ -56,6 +56,12 @@ MUTANTS = {
                            "for (int64_t k = rp_out[i]; k < rp_out[i + 1]; k++) if (col_out[k] != i) Xn[col_out[k]] += transit;"),
     # PI' divides by out + 1
     "pi_push_divisor": ("double transit = d * X[i] / (double)o;", "double transit = d * X[i] / (double)(o + 1);"),
+    # resumed run ignores the given history
+    "resume_drops_H0": ("for (int64_t i = 0; i < n; i++) { H[i] = H0[i]; F[i] = F0[i]; }",
+                        "for (int64_t i = 0; i < n; i++) { H[i] = 0.0; F[i] = F0[i]; }"),
+    # DI-CYC visits only positive fluid (a signed resumed state never drains)
+    "cyc_positive_only": ("        } else {\n            for (int64_t i = 0; i < n; i++)\n                if (F[i] != 0.0)",
+                          "        } else {\n            for (int64_t i = 0; i < n; i++)\n                if (F[i] > 0.0)"),
     # E pre-diffusion in id order, ignoring the levels
     "e_prepass_id_order": ("if (e_mask[i] && e_level[i] == l) {", "if (e_mask[i] && l == 0) {"),
     # E pre-diffusion skips the last level
@@ -79,7 +85,8 @@ def test_pins_catch_planted_mistake(name, tmp_path):
             [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
              os.path.join(ROOT, "tests", "test_oracle_build.py"),
              os.path.join(ROOT, "tests", "test_oracle_solve.py"),
-             os.path.join(ROOT, "tests", "test_oracle_e.py")],
+             os.path.join(ROOT, "tests", "test_oracle_e.py"),
+             os.path.join(ROOT, "tests", "test_oracle_resume.py")],
             cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
     except subprocess.TimeoutExpired:
         return  # a mutant that no longer converges within the cycle cap is caught too
