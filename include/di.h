@@ -40,7 +40,8 @@ typedef enum {
     DI_ERR_CUDA = 4,             /* a CUDA runtime call failed */
     DI_ERR_NOT_CONVERGED = 5,    /* the sweep cap was reached; outputs hold the current state */
     DI_ERR_BUSY = 6,             /* the graph's workspace is in use by another thread */
-    DI_ERR_TIMEOUT = 7           /* a bounded wait ran out */
+    DI_ERR_TIMEOUT = 7,          /* a bounded wait ran out */
+    DI_ERR_CORRUPT = 8           /* di_csr_validate / di_graph_validate found an inconsistency */
 } di_status;
 
 /* Node selection rule of a sweep (Section 2.3). */
@@ -320,6 +321,36 @@ di_status di_server_wait(di_server *srv, int64_t request_id, double *X_out, di_r
 
 /* Stops the workers (requests not finished end with DI_ERR_BUSY) and frees the server. */
 void di_server_destroy(di_server *srv);
+
+/* ------------------------------------------------------------------------------------------
+ * Diagnostics (host code, not on the solve path).
+ * ------------------------------------------------------------------------------------------ */
+
+/*
+ * di_csr_validate — checks graph arrays in host memory, laid out as di_graph_export returns
+ * them, against the build's invariants:
+ *   - each CSR runs from 0 to L, with non-decreasing row pointers, ids in [0, n), and every row
+ *     strictly ascending (sorted and free of duplicates);
+ *   - the in-CSR is the transpose of the out-CSR (order-independent checksums of the link set);
+ *   - the degrees are the row lengths, and loop[i] is set exactly when row i holds i;
+ *   - E and its levels follow Section 2.4's definition: i is in E exactly when all of its
+ *     in-neighbours are, with level 1 + their largest level (0 without in-neighbours), and -1
+ *     outside E.
+ * out_deg, in_deg, loop, e_mask and e_level may be NULL to skip their checks. Returns DI_OK, or
+ * DI_ERR_CORRUPT with di_last_error() naming the first inconsistency; DI_ERR_INVALID_ARG for a
+ * NULL CSR array or bad sizes. Time O(n + L); no GPU needed.
+ */
+di_status di_csr_validate(int32_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out,
+                          const int64_t *rp_in, const int32_t *col_in, const int32_t *out_deg,
+                          const int32_t *in_deg, const uint8_t *loop, const uint8_t *e_mask,
+                          const int32_t *e_level);
+
+/*
+ * di_graph_validate — copies every array of a built graph to the host and runs di_csr_validate
+ * on them. It also checks the push kernels' copy of the out-links, where bit 31 marks the links
+ * into a hub, and |E| against the statistics. Same returns; DI_ERR_CUDA if a copy fails.
+ */
+di_status di_graph_validate(const di_graph *g);
 
 /*
  * di_residual_noalloc — the exact residual F* = B + P.H - H of a history H and its norm

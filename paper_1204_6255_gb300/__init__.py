@@ -21,7 +21,7 @@ __all__ = [
     "di_graph_create", "di_graph_destroy", "di_graph_stats_get", "di_graph_export",
     "di_solve", "di_solve_ex", "di_solve_resume", "di_power_iter", "di_power_iter_push", "di_solve_batch", "di_ppr_batch", "di_residual_noalloc",
     "di_server_create", "di_server_submit", "di_server_wait", "di_server_destroy", "Server",
-    "di_last_error", "di_version",
+    "di_csr_validate", "di_graph_validate", "di_last_error", "di_version",
 ]
 
 DI_CYC, DI_SOP = 0, 1
@@ -122,6 +122,10 @@ def load(path: str | None = None):
     lib.di_solve_resume.restype = st
     lib.di_solve_resume.argtypes = [vp, vp, vp, vp, dbl, dbl, ctypes.POINTER(SolveOpts), vp, vp, vp,
                                     ctypes.POINTER(SolveInfo), vp]
+    lib.di_csr_validate.restype = st
+    lib.di_csr_validate.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.di_graph_validate.restype = st
+    lib.di_graph_validate.argtypes = [vp]
     lib.di_power_iter_push.restype = st
     lib.di_power_iter_push.argtypes = [vp, vp, dbl, dbl, i32, i32, vp, vp, ctypes.POINTER(SolveInfo), vp]
     lib.di_solve_batch.restype = st
@@ -411,6 +415,21 @@ def di_server_wait(srv: Server, request_id: int, X_out=None, timeout_ms: int = 6
 
 def di_server_destroy(srv: Server):
     srv.close()
+
+
+def di_csr_validate(n: int, L: int, rp_out, col_out, rp_in, col_in, out_deg=None, in_deg=None, loop=None,
+                    e_mask=None, e_level=None):
+    """Checks graph arrays (host numpy, as di_graph_export returns them) against the build's
+    invariants; raises DiError (status 8) naming the first inconsistency."""
+    _check(load().di_csr_validate(int(n), int(L), _ptr(rp_out, np.int64), _ptr(col_out, np.int32),
+                                  _ptr(rp_in, np.int64), _ptr(col_in, np.int32), _ptr(out_deg, np.int32),
+                                  _ptr(in_deg, np.int32), _ptr(loop, np.uint8), _ptr(e_mask, np.uint8),
+                                  _ptr(e_level, np.int32)))
+
+
+def di_graph_validate(g: Graph):
+    """Checks every array of a built graph (copied to the host); raises DiError on an inconsistency."""
+    _check(load().di_graph_validate(g.handle))
 
 
 def di_last_error() -> str:

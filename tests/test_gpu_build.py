@@ -27,6 +27,7 @@ def test_build_random_graphs(n, m, device):
     n, src, dst = workloads.small_random_graph(n, m, seed=n * 7 + m)
     g = _graph(n, src, dst, device)
     assert_build_matches_oracle(g, oracle.build(n, src, dst))
+    di.di_graph_validate(g)
 
 
 def test_build_all_duplicates_and_self_loops():
@@ -66,6 +67,7 @@ def test_build_workloads(name):
     n, src, dst = workloads.generate(spec)
     g = _graph(n, src, dst)
     assert_build_matches_oracle(g, oracle.build(n, src, dst))
+    di.di_graph_validate(g)
 
 
 def test_build_rejects_bad_ids_and_sizes():

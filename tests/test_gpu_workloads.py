@@ -76,6 +76,7 @@ def test_web_n1m_transposed():
 def test_web_n10m_full_size():
     cfg, n, src, dst, g, og = _setup("web_n10m")
     assert_build_matches_oracle(g, og)
+    di.di_graph_validate(g)
     tol = cfg["tol"]
     d = 0.85
     B = oracle.uniform_B(n, d)
