@@ -8,7 +8,11 @@
 //   -> out-CSR (rows by origin, destinations ascending) + loop flags
 //   -> re-pack as dst << bits | src and stable-sort on the dst field only, which keeps origins
 //      ascending inside each row -> in-CSR
-//   -> degrees, statistics, and E by level-synchronous peeling (Section 2.4).
+//   -> degrees, statistics, and E by level-synchronous peeling (Section 2.4), recording E grouped
+//      by level for the E pre-diffusion
+//   -> for the push kernels: a hash table of the highest in-degree nodes (hubs) and a copy of
+//      the out-links with bit 31 set on links into a hub; for the pull kernels: the rows with
+//      more in-links than one warp should walk, split into chunks.
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>

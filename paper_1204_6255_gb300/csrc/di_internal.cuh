@@ -124,7 +124,6 @@ struct SolveCtl {
     // latest selection: one atomic reserves both for a select chunk
     unsigned long long front_chunks;
     int32_t heavy_count;      // heavy frontier entries written by the latest selection
-    int32_t batch_next;       // dynamic work counter of the push kernel
     int32_t done;             // 1 when the stop test has fired
     int32_t status;           // 0 ok; 1 bad right-hand side
     uint32_t ticket;          // last-block-done counter of the reductions

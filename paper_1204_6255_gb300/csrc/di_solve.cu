@@ -1,26 +1,32 @@
 // Single right-hand-side D-iteration and power iteration on the GPU.
 //
 // A sweep (Section 2.3 DI-CYC / DI-SOP, Section 2.5) is three kernels:
-//   k_select  reads F and out[], picks the nodes of the sweep (DI-CYC: F_i != 0; DI-SOP:
-//             |F_i| > (r / L) * out_i with r = ||F||_1 taken at the sweep start), and performs the
-//             node part of every visit: F_i -> 0, transit (F_i * out_i / (out_i - d) for a loop
-//             node), H_i += transit, dangling mass e. Visited nodes with out-links are appended to
-//             the frontier with their per-link share d * transit / out_i.
-//   k_push    scatters each frontier entry's share onto its out-neighbours j != i with fire-and-
-//             forget atomic adds into F (the `l_out` loop of Section 2.5). Warps take batches of
-//             32 frontier entries and walk their concatenated out-links 32 at a time, so the col
-//             index loads of consecutive lanes are contiguous within each row; nodes with more
-//             than kPushHeavy links are spread over every warp of the grid.
-//   k_reduce  r = sum |F_i| in FP64 (warp shuffle, block, then the last block to finish sums
-//             the block partials in a fixed order), and the stop test r <= tol. It writes the
-//             WHILE-node condition, so the whole sweep loop runs from one CUDA graph launch.
+//   k_select    reads F and out[], picks the nodes of the sweep (DI-CYC: F_i != 0; DI-SOP:
+//               |F_i| > (r / L) * out_i with r = ||F||_1 taken at the sweep start), and performs
+//               the node part of every visit: F_i -> 0, transit (F_i * out_i / (out_i - d) for a
+//               loop node), H_i += transit, dangling mass e. Visited nodes with out-links become
+//               frontier entries (node id, per-link share d * transit / out_i), id-sorted within
+//               segments of kSelChunk nodes; nodes with more than kPushHeavy links go to a
+//               separate heavy list.
+//   k_push_win  (FP32 fluid) scatters the shares onto the out-neighbours j != i (the l_out loop
+//               of Section 2.5): a block takes a segment, adds the links that land near it into
+//               a shared-memory window and the links into hubs into a shared-memory hub cache,
+//               and sends the rest to F with L2 reductions; heavy nodes are spread over every
+//               warp of the grid. k_push does the same for FP64 fluid without the caches.
+//   k_reduce    r = sum |F_i| in FP64 (FP32 runs, warp shuffle, block, then the last block to
+//               finish sums the block partials in a fixed order), and the stop test r <= tol.
+//               It writes the WHILE-node condition, so the whole sweep loop runs from one CUDA
+//               graph launch.
 // All selected nodes diffuse concurrently; the result is a valid D-iteration in another
-// diffusion order, which reaches the same fixed point.
+// diffusion order, which reaches the same fixed point. Around the sweeps: k_e_visit (the E-level
+// pre-diffusion, one launch per level of E), the exact FP64 residual refinement, and resumed
+// solves from a given (H, F).
 //
 // Power iteration (Section 2.5 "PI", Jacobi on X = P.X + B) and the exact FP64 residual
-// F* = B + P.H - H both use k_pull: a warp takes 32 consecutive rows of the in-CSR, walks their
-// contiguous in-links 32 at a time and reduces per row with a segmented warp scan; rows with
-// more than kPullHeavy in-links are summed chunk-wise by k_pull_heavy first.
+// F* = B + P.H - H both use k_pull: a warp takes 32 consecutive rows of the in-CSR; each lane
+// walks a run of kPullVT contiguous in-links, and a segmented scan joins the rows that span
+// lanes. Rows with more than kPullHeavy in-links are summed chunk-wise by k_pull_heavy first.
+// Power iteration per column (PI') runs the sweep kernels above with self-links as plain links.
 #include <cmath>
 #include <cstring>
 
@@ -137,7 +143,6 @@ __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl,
         ctl->front_total += (unsigned long long)(front_entries(ctl->front_chunks) + ctl->heavy_count);
         ctl->front_chunks = 0;
         ctl->heavy_count = 0;
-        ctl->batch_next = 0;
         ctl->chunk_next = 0;
         if (set_cond) ctl->body_runs++;
         bool cont = ctl->status == 0 && tot > ctl->tol && ctl->sweeps < ctl->max_sweeps;
