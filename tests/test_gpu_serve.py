@@ -127,3 +127,27 @@ def test_server_errors():
     with pytest.raises(di.DiError) as e:
         di.di_server_create([g], d=D, slots=4, mem_budget=1000)
     assert e.value.status == 3
+
+
+def test_destroy_with_requests_in_flight():
+    # results being copied out and requests still queued when the server goes away: the
+    # destructor drains the in-flight copies and fails the rest, and the graphs stay usable
+    graphs = _graphs((50000, 8000), seed=8181)
+    srv = di.di_server_create([g for g, _ in graphs], d=D, slots=4, sweeps_per_step=2)
+    for i in range(24):
+        gi = i % 2
+        off, seeds = workloads.seed_sets(graphs[gi][0].n, 1, 100, seed=3000 + i)
+        di.di_server_submit(srv, gi, seeds, 1e-8)
+    time.sleep(0.05)
+    t = time.perf_counter()
+    srv.close()
+    assert time.perf_counter() - t < 30.0
+    g, og = graphs[1]
+    srv = di.di_server_create([g], d=D, slots=4)
+    seeds = np.array([1, 2, 3], np.int32)
+    X = np.empty(g.n)
+    rid = di.di_server_submit(srv, 0, seeds, 1e-8)
+    _, info = di.di_server_wait(srv, rid, X_out=X, timeout_ms=60000)
+    ref, _, _, ok = oracle.di(og, oracle.ppr_B(g.n, seeds, D), D, 1e-13, oracle.SOP)
+    assert ok and np.abs(ref - X).sum() <= 1e-8 / (1 - D) * (1 + 1e-6) + 1e-12
+    srv.close()
