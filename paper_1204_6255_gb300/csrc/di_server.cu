@@ -18,6 +18,7 @@
 // graphs run concurrently on the device. Each column is an independent problem; batch-mates
 // only change which nodes a sweep visits, not the fixed point.
 #include <chrono>
+#include <cstring>
 #include <condition_variable>
 #include <deque>
 #include <memory>
@@ -88,6 +89,8 @@ struct di_server {
     std::unordered_map<int64_t, std::shared_ptr<di::Request>> requests;
     int64_t next_id = 1;
     std::atomic<bool> stop{false};
+    std::mutex copy_mu;                  // results copied to device memory by di_server_wait
+    cudaStream_t copy_stream = nullptr;  // non-blocking: such a copy waits on no other work
     ~di_server();
 };
 
@@ -328,6 +331,7 @@ di_server::~di_server() {
             kv.second->X = nullptr;
         }
     workers.clear();
+    if (copy_stream) cudaStreamDestroy(copy_stream);
 }
 
 using namespace di;
@@ -448,15 +452,25 @@ di_status di_server_wait(di_server *srv, int64_t request_id, double *X_out, di_r
             Worker &w = *srv->workers[r->graph];
             double *buf = r->X;
             r->X = nullptr;
+            const size_t bytes = sizeof(double) * (size_t)w.g->n;
+            cudaError_t e = cudaSuccess;
             if (X_out) {
-                cudaStream_t s = nullptr;
-                const cudaError_t e = cudaMemcpyAsync(X_out, buf, sizeof(double) * (size_t)w.g->n, cudaMemcpyDefault, s);
-                const cudaError_t e2 = e == cudaSuccess ? cudaStreamSynchronize(s) : e;
-                w.give_buffer(buf);
-                DI_CHECK_CUDA(e2);
-            } else {
-                w.give_buffer(buf);
+                cudaPointerAttributes a;
+                const bool device = cudaPointerGetAttributes(&a, X_out) == cudaSuccess &&
+                                    (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+                cudaGetLastError();
+                if (!device) {
+                    std::memcpy(X_out, buf, bytes);   // pinned host buffer to host memory
+                } else {
+                    std::lock_guard<std::mutex> lk(srv->copy_mu);
+                    DeviceGuard dg(w.g->dev.device);
+                    if (!srv->copy_stream) e = cudaStreamCreateWithFlags(&srv->copy_stream, cudaStreamNonBlocking);
+                    if (e == cudaSuccess) e = cudaMemcpyAsync(X_out, buf, bytes, cudaMemcpyHostToDevice, srv->copy_stream);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(srv->copy_stream);
+                }
             }
+            w.give_buffer(buf);
+            DI_CHECK_CUDA(e);
         }
         DI_REQUIRE(r->status == DI_OK, r->status, "request %lld ended with status %d", (long long)request_id,
                    (int)r->status);

@@ -151,3 +151,21 @@ def test_destroy_with_requests_in_flight():
     ref, _, _, ok = oracle.di(og, oracle.ppr_B(g.n, seeds, D), D, 1e-13, oracle.SOP)
     assert ok and np.abs(ref - X).sum() <= 1e-8 / (1 - D) * (1 + 1e-6) + 1e-12
     srv.close()
+
+
+def test_result_into_device_memory():
+    import torch
+    graphs = _graphs((6000,), seed=9191)
+    g, og = graphs[0]
+    srv = di.di_server_create([g], d=D, slots=4)
+    seeds = np.array([7, 70, 700], np.int32)
+    Xd = torch.full((g.n,), -1.0, dtype=torch.float64, device="cuda")
+    Xh = np.empty(g.n)
+    a = di.di_server_submit(srv, 0, seeds, 1e-9)
+    b = di.di_server_submit(srv, 0, seeds, 1e-9)
+    di.di_server_wait(srv, a, X_out=Xd, timeout_ms=60000)
+    di.di_server_wait(srv, b, X_out=Xh, timeout_ms=60000)
+    srv.close()
+    ref, _, _, ok = oracle.di(og, oracle.ppr_B(g.n, seeds, D), D, 1e-14, oracle.SOP)
+    bound = 1e-9 / (1 - D) * (1 + 1e-6) + 1e-12
+    assert ok and np.abs(Xd.cpu().numpy() - ref).sum() <= bound and np.abs(Xh - ref).sum() <= bound
