@@ -129,6 +129,9 @@ struct SolveCtl {
     uint32_t ticket;          // last-block-done counter of the reductions
     int32_t body_runs;        // executions of the WHILE body (kernel-launch accounting)
     int32_t chunk_next;       // dynamic work counter over the segments
+    double absorbed;          // fluid the visits of the current sweep removed from sum F (FP64)
+    int32_t track;            // 1: F >= 0 throughout, so sum F after a sweep = before - absorbed
+    int32_t reduce_est;       // 1: this sweep's reduction may take r from the tracked sum
     int32_t plain_loops;      // 1: a self-link is a plain link (power iteration per column), no
                               //    closed form for loop nodes
     unsigned long long front_total;  // frontier entries over all sweeps

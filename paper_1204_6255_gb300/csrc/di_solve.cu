@@ -131,12 +131,22 @@ template <class T>
 __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl, cudaGraphConditionalHandle h,
                          int set_cond) {
     __shared__ double scratch[32];
-    const double s = abs_sum(F, n);
     double tot;
-    if (!finish_sum(s, partials, ctl, scratch, tot)) return;
+    if (ctl->reduce_est) {
+        // fluid is nonnegative, so sum |F| after the sweep is the sum before it less what the
+        // visits absorbed (the select decided this per sweep; see there for when)
+        if (blockIdx.x != 0 || threadIdx.x != 0) return;
+        tot = ctl->r - ctl->absorbed;
+        if (tot < 0.0) tot = 0.0;
+    } else {
+        const double s = abs_sum(F, n);
+        if (!finish_sum(s, partials, ctl, scratch, tot)) return;
+    }
     if (threadIdx.x == 0) {
         ctl->ticket = 0;
         ctl->r = tot;
+        ctl->absorbed = 0.0;
+        ctl->reduce_est = 0;
         int sel = ctl->last_selected;
         ctl->force_cyc = (sel == 0 && tot > 0.0) ? 1 : 0;   // a DI-SOP sweep found no node
         ctl->last_selected = 0;
@@ -224,6 +234,8 @@ __device__ __forceinline__ bool selects(double f, int32_t o, bool cyc, double th
 // within each chunk (the push then walks neighbouring rows together). An entry is the node id
 // and its share (8 bytes); the push reads the row bounds itself, from neighbouring row pointers.
 constexpr int kSelItems = 8;
+constexpr int kTrackResync = 8;      // an exact reduction at least every kTrackResync sweeps
+constexpr double kTrackBand = 16.0;  // ... and at every sweep once r <= kTrackBand * tol
 constexpr int kSelChunk = 256 * kSelItems;
 constexpr int kSelMinBlocks = 4;
 
@@ -245,6 +257,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
     const unsigned lane = lane_id(), lt = lanemask_lt();
     const int warp = threadIdx.x >> 5;
     float e_run = 0.f;   // dangling mass of this thread, widened at the end
+    float ab_run = 0.f;  // fluid absorbed by this thread's visits (FP32: FP64 is slow here)
     double e_loc = 0.0;
     unsigned long long pushed = 0, visited = 0;
     for (int64_t base = (int64_t)blockIdx.x * kSelChunk; base < n; base += (int64_t)gridDim.x * kSelChunk) {
@@ -290,6 +303,8 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                 __stcs(H + i, h[j] + t);
                 visited++;
                 pushed += (unsigned long long)o;
+                // F loses f and regains the share on each link pushed (all but a closed-form loop)
+                ab_run += (float)f[j] - (float)share * (float)(o - (lp ? 1 : 0));
                 if (o == 0) {
                     if (sizeof(T) == 4) e_run += (float)t; else e_loc += t;
                 } else if (o > kPushHeavy) {
@@ -346,16 +361,24 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
     }
     e_loc += (double)e_run;
     e_loc = block_sum(e_loc, scratch);
+    const double absorbed = block_sum((double)ab_run, scratch);
     pushed = block_sum(pushed, scratch_u);
     visited = block_sum(visited, scratch_u);
     if (threadIdx.x == 0) {
         if (e_loc != 0.0) atomicAdd(&ctl->e, e_loc);
+        if (absorbed != 0.0) atomicAdd(&ctl->absorbed, absorbed);
         if (pushed) atomicAdd(&ctl->pushed, pushed);
         if (visited) {
             atomicAdd(&ctl->visited, visited);
             atomicAdd(&ctl->last_selected, (int)visited);
         }
-        if (blockIdx.x == 0) atomicAdd(&ctl->sweeps, 1);
+        if (blockIdx.x == 0) {
+            const int sw = atomicAdd(&ctl->sweeps, 1) + 1;
+            // this sweep's reduction takes r from the tracked sum while r is well above tol,
+            // except every kTrackResync-th sweep (the FP32 atomics' rounding is not tracked);
+            // near the tolerance every reduction sums F, so the stop test is on the exact sum
+            ctl->reduce_est = (ctl->track && r > kTrackBand * ctl->tol && sw % kTrackResync != 0) ? 1 : 0;
+        }
     }
 }
 
@@ -1179,10 +1202,11 @@ static void launch_refine(di_graph *g, const Launch &l, double d, cudaStream_t s
 }
 
 static void write_ctl(di_graph *g, double d, double tol, int schedule, int max_sweeps, int plain_loops,
-                      cudaStream_t s) {
+                      cudaStream_t s, int track = 0) {
     SolveCtl &c = *g->ws.ctl_host;
     memset(&c, 0, sizeof(c));
     c.plain_loops = plain_loops;
+    c.track = track;
     c.d = d;
     c.tol = tol;
     c.L = (double)g->L;
@@ -1214,7 +1238,10 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
     const Launch l = launch_shape<T>(g);
     SolveCtl *ctl = ws.ctl.as<SolveCtl>();
     to_device(ws.B.p, B, sizeof(double) * (size_t)g->n, s);
-    write_ctl(g, d, tol, schedule, max_sweeps, plain_loops, s);
+    // r may be tracked between exact reductions only while the fluid is certainly nonnegative:
+    // FP32 sweeps from (0, B) until the first refinement (whose exact residual may be signed);
+    // a refined solve's final residual is exact in any case
+    write_ctl(g, d, tol, schedule, max_sweeps, plain_loops, s, (sizeof(T) == 4 && refine && !H0) ? 1 : 0);
     if (profile) host_loop = 1;
     KernelClock kc(profile != 0, s);
     cudaEvent_t e0, e1;
@@ -1284,6 +1311,8 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
             // continuation sweeps aim at half the tolerance, so the next exact residual lands below it
             const double half = 0.5 * tol;
             DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->tol, &half, sizeof(double), cudaMemcpyHostToDevice, s));
+            static const int32_t no_track = 0;
+            DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->track, &no_track, sizeof(int32_t), cudaMemcpyHostToDevice, s));
             run_sweeps();
         }
         DI_CHECK_CUDA(cudaEventRecord(e1, s));
