@@ -124,6 +124,7 @@ struct SolveCtl {
     // latest selection: one atomic reserves both for a select chunk
     unsigned long long front_chunks;
     int32_t heavy_count;      // heavy frontier entries written by the latest selection
+    int32_t heavy_chunks;     // kHeavyChunk-link chunks of those entries
     int32_t done;             // 1 when the stop test has fired
     int32_t status;           // 0 ok; 1 bad right-hand side
     uint32_t ticket;          // last-block-done counter of the reductions
@@ -144,7 +145,8 @@ __host__ __device__ inline int32_t front_entries(unsigned long long fc) {
 }
 __host__ __device__ inline int32_t front_segments(unsigned long long fc) { return (int32_t)(fc >> kFrontBits); }
 
-constexpr int kPushHeavy = 4096;    // out-degree above which a node's edges are split over warps
+constexpr int kPushHeavy = 4096;
+constexpr int kHeavyChunk = 1024;   // links per work unit of a heavy node's push    // out-degree above which a node's edges are split over warps
 constexpr int kPullHeavy = 8192;    // in-degree above which a row's edges are split over warps
 constexpr int kPullChunk = 4096;    // edges per heavy-row chunk of the pull
 constexpr int kReduceBlocks = 1024; // partial sums of the last-block-done reductions
@@ -154,6 +156,7 @@ constexpr int kHubSlots = 2048;     // shared-memory hub cache of the push kerne
 struct Workspace {
     int fluid = -1;                 // di_fluid the buffers were sized for
     DevBuf F, H, B, front_id, front_s, heavy_id, heavy_s, partials, ctl, y0, y1, chunks;
+    DevBuf heavy_cstart, heavy_chunk;   // heavy entry -> first chunk; chunk -> heavy entry
     DevBuf Bdf, cdf, Xdf;           // power iteration in double-float: B, d/out, X
     double cdf_d = -1.0;            // damping factor cdf currently holds (-1: none)
     cudaGraphExec_t sweep_exec = nullptr;   // reduce -> WHILE{select, push, reduce}

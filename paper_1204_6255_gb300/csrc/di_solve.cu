@@ -153,6 +153,7 @@ __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl,
         ctl->front_total += (unsigned long long)(front_entries(ctl->front_chunks) + ctl->heavy_count);
         ctl->front_chunks = 0;
         ctl->heavy_count = 0;
+        ctl->heavy_chunks = 0;
         ctl->chunk_next = 0;
         if (set_cond) ctl->body_runs++;
         bool cont = ctl->status == 0 && tot > ctl->tol && ctl->sweeps < ctl->max_sweeps;
@@ -242,7 +243,8 @@ constexpr int kSelMinBlocks = 4;
 template <class T>
 __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, const int32_t *out_info,
                                                             int32_t n, SolveCtl *ctl, int32_t *front_id, T *front_s,
-                                                            int32_t *heavy_id, T *heavy_s, int4 *chunks) {
+                                                            int32_t *heavy_id, T *heavy_s, int32_t *heavy_cstart,
+                                                            int32_t *heavy_chunk, int4 *chunks) {
     __shared__ double scratch[32];
     __shared__ unsigned long long scratch_u[32];
     __shared__ int wcount[kSelItems][8];
@@ -324,9 +326,15 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                 if ((int)lane == leader) p0 = atomicAdd(&ctl->heavy_count, __popc(bh));
                 p0 = __shfl_sync(kFull, p0, leader);
                 if (heavy) {
+                    // the node's links are pushed in kHeavyChunk-link chunks over all warps; the
+                    // chunk list maps each chunk back to its entry
                     const int p = p0 + __popc(bh & lt);
                     heavy_id[p] = (int32_t)i;
                     heavy_s[p] = share;
+                    const int nch = (o + kHeavyChunk - 1) / kHeavyChunk;
+                    const int cs = atomicAdd(&ctl->heavy_chunks, nch);
+                    heavy_cstart[p] = cs;
+                    for (int c = 0; c < nch; c++) heavy_chunk[cs + c] = p;
                 }
             }
         }
@@ -478,6 +486,8 @@ constexpr int kPushVT = 8;
 template <class T>
 __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_id, const T *__restrict__ front_s,
                                               const int32_t *__restrict__ heavy_id, const T *__restrict__ heavy_s,
+                                              const int32_t *__restrict__ heavy_cstart,
+                                              const int32_t *__restrict__ heavy_chunk,
                                               const int64_t *__restrict__ rp_out, const int32_t *__restrict__ col_out,
                                               T *F, SolveCtl *ctl) {
     __shared__ int s_off[8][33];
@@ -491,20 +501,17 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
 
-    // nodes with more than kPushHeavy links: their links in chunks over all warps
-    const int hc = ctl->heavy_count;
-    constexpr int kChunk = 1024;
-    for (int h = 0; h < hc; h++) {
-        const int32_t u = heavy_id[h];
-        const T sh = heavy_s[h];
-        const int64_t b = rp_out[u], e = rp_out[u + 1];
-        const int64_t nch = (e - b + kChunk - 1) / kChunk;
-        for (int64_t c = gwarp; c < nch; c += nwarps) {
-            const int64_t cb = b + c * kChunk, ce = min(cb + kChunk, e);
-            for (int64_t k = cb + lane; k < ce; k += 32) {
-                const int32_t j = __ldcs(col_out + k);
-                if (j != u || loops) red_keep(&F[j], sh, pol);
-            }
+    // nodes with more than kPushHeavy links: their chunks over all warps
+    const int hch = ctl->heavy_chunks;
+    for (int64_t c = gwarp; c < hch; c += nwarps) {
+        const int p = heavy_chunk[c];
+        const int32_t u = heavy_id[p];
+        const T sh = heavy_s[p];
+        const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * kHeavyChunk;
+        const int64_t ce = min(cb + (int64_t)kHeavyChunk, rp_out[u + 1]);
+        for (int64_t k = cb + lane; k < ce; k += 32) {
+            const int32_t j = __ldcs(col_out + k);
+            if (j != u || loops) red_keep(&F[j], sh, pol);
         }
     }
 
@@ -565,6 +572,8 @@ constexpr int kWinMinEntries = 24;              // sparser segments push link by
 
 __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__ front_id, const float *__restrict__ front_s,
                                                   const int32_t *__restrict__ heavy_id, const float *__restrict__ heavy_s,
+                                                  const int32_t *__restrict__ heavy_cstart,
+                                                  const int32_t *__restrict__ heavy_chunk,
                                                   const int64_t *__restrict__ rp_out,
                                                   const int32_t *__restrict__ col_push, const int4 *__restrict__ chunks,
                                                   const int32_t *__restrict__ hub_ids, float *F, SolveCtl *ctl) {
@@ -589,20 +598,17 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
         else red_keep(&F[jr], v, keep);
     };
 
-    // nodes with more than kPushHeavy links: their links in chunks over all warps
-    const int hc = ctl->heavy_count;
-    constexpr int kChunk = 1024;
-    for (int h = 0; h < hc; h++) {
-        const int32_t u = heavy_id[h];
-        const float sh = heavy_s[h];
-        const int64_t b = rp_out[u], e = rp_out[u + 1];
-        const int64_t nch = (e - b + kChunk - 1) / kChunk;
-        for (int64_t c = gwarp; c < nch; c += nwarps) {
-            const int64_t cb = b + c * kChunk, ce = min(cb + kChunk, e);
-            for (int64_t k = cb + lane; k < ce; k += 32) {
-                const int32_t jr = ld_stream(col_push + k, stream);
-                if ((jr & 0x7fffffff) != u || loops) far_add(jr, sh);
-            }
+    // nodes with more than kPushHeavy links: their chunks over all warps
+    const int hch = ctl->heavy_chunks;
+    for (int64_t c = gwarp; c < hch; c += nwarps) {
+        const int p = heavy_chunk[c];
+        const int32_t u = heavy_id[p];
+        const float sh = heavy_s[p];
+        const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * kHeavyChunk;
+        const int64_t ce = min(cb + (int64_t)kHeavyChunk, rp_out[u + 1]);
+        for (int64_t k = cb + lane; k < ce; k += 32) {
+            const int32_t jr = ld_stream(col_push + k, stream);
+            if ((jr & 0x7fffffff) != u || loops) far_add(jr, sh);
         }
     }
 
@@ -1063,6 +1069,9 @@ static void ensure_workspace(di_graph *g) {
     ws.front_s.ensure(sizeof(T) * n);
     ws.heavy_id.ensure(sizeof(int32_t) * (size_t)(g->n_heavy_out + 1));
     ws.heavy_s.ensure(sizeof(T) * (size_t)(g->n_heavy_out + 1));
+    ws.heavy_cstart.ensure(sizeof(int32_t) * (size_t)(g->n_heavy_out + 1));
+    // a heavy node has at most out / kHeavyChunk + 1 chunks
+    ws.heavy_chunk.ensure(sizeof(int32_t) * (size_t)(g->L / kHeavyChunk + g->n_heavy_out + 1));
     ws.partials.ensure(sizeof(double) * kReduceBlocks);
     ws.ctl.ensure(sizeof(SolveCtl));
     ws.y0.ensure(sizeof(float2) * n);
@@ -1086,17 +1095,20 @@ static void launch_sweep_body(di_graph *g, const Launch &l, cudaStream_t s, cuda
     c.run(KC_SELECT, 1, [&] {
         k_select<T><<<l.sel_blocks, 256, 0, s>>>(ws.F.as<T>(), ws.H.as<double>(), g->out_info.as<int32_t>(), g->n,
                                                   ctl, ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
-                                                  ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(), ws.chunks.as<int4>());
+                                                  ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(),
+                                                  ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(),
+                                                  ws.chunks.as<int4>());
     });
     c.run(KC_PUSH, 1, [&] {
         if (sizeof(T) == 4) {
             k_push_win<<<l.win_blocks, 256, 0, s>>>(
                 ws.front_id.as<int32_t>(), ws.front_s.as<float>(), ws.heavy_id.as<int32_t>(), ws.heavy_s.as<float>(),
-                g->rp_out.as<int64_t>(),
+                ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(), g->rp_out.as<int64_t>(),
                 g->col_push.as<int32_t>(), ws.chunks.as<int4>(), g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl);
         } else {
             k_push<T><<<l.push_blocks, 256, 0, s>>>(ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
                                                     ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(),
+                                                    ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(),
                                                     g->rp_out.as<int64_t>(), g->col_out.as<int32_t>(), ws.F.as<T>(),
                                                     ctl);
         }
