@@ -147,7 +147,7 @@ def push_traffic():
     if fields.get("source_sha256") != sha:
         return None, "stale: kernel source changed since the capture"
     try:
-        return float(fields["dram_bytes_per_launch"]), PUSH_PROFILE
+        return float(fields["dram_bytes_per_launch"]), os.path.relpath(PUSH_PROFILE, ROOT)
     except (KeyError, ValueError):
         return None, None
 
