@@ -10,6 +10,7 @@ struct BatchWorkspace {
     int tuned_T = 0;                 // autotuned tile width (0 = not tuned yet)
     double probe_rate[4] = {0, 0, 0, 0};   // column-link updates per second of each width
     DevBuf F, H, Bn, front_id, front_s, heavy_partial, partials, ctl, stage, y;
+    DevBuf heavy_cstart, heavy_chunk;   // entry -> first chunk; chunk -> entry (heavy nodes)
     cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};   // per tile width
     cudaStream_t capture_stream = nullptr;
     void *ctl_host = nullptr;

@@ -39,6 +39,7 @@ struct BatchCtl {
     int32_t force_cyc;
     int32_t last_selected;
     int32_t front_count;
+    int32_t heavy_chunks;            // kHeavyChunk-link chunks of the entries with > kPushHeavy links
     int32_t batch_next;
     int32_t body_runs;
     uint32_t ticket;
@@ -158,6 +159,7 @@ static __device__ __forceinline__ void batch_stop_test(BatchCtl *ctl, cudaGraphC
     ctl->last_selected = 0;
     ctl->front_total += (unsigned long long)ctl->front_count;
     ctl->front_count = 0;
+    ctl->heavy_chunks = 0;
     ctl->batch_next = 0;
     if (set_cond) ctl->body_runs++;
     const bool cont = ctl->status == 0 && any && ctl->sweeps < ctl->max_sweeps;
@@ -176,7 +178,8 @@ __global__ void __launch_bounds__(256) kb_reduce(const float *F, int32_t n, doub
 // frontier is id-sorted within each 256-node chunk.
 template <int T>
 __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int32_t *out_info, int32_t n,
-                                                 BatchCtl *ctl, int32_t *front_id, float *front_s) {
+                                                 BatchCtl *ctl, int32_t *front_id, float *front_s,
+                                                 int32_t *heavy_cstart, int32_t *heavy_chunk) {
     constexpr int kNodesPerStep = 256 / T;
     __shared__ double s_thr[T];
     __shared__ int s_act[T];
@@ -186,6 +189,7 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
     __shared__ int chunk_base;
     __shared__ float s_share[T][256];       // per sub-step share of every lane
     __shared__ unsigned s_lbs[T][8];        // per sub-step leader ballot of every warp
+    __shared__ int32_t s_hdeg[T][256 / T];  // per sub-step and node: out-degree if above kPushHeavy, else 0
     if (ctl->done) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool cyc = ctl->schedule == DI_CYC || ctl->force_cyc;
@@ -265,6 +269,7 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
                     pushed += (unsigned long long)o;
                 }
                 const unsigned lb = __ballot_sync(kFull, leader && bpush != 0);
+                if (leader) s_hdeg[j][tid / T] = o > kPushHeavy ? o : 0;
                 s_share[j][tid] = share;
                 if (lane == 0) {
                     s_lbs[j][warp] = lb;
@@ -291,7 +296,18 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
             if (lb & (1u << gbase)) {
                 const int pos = cb + wcount[j][warp] + __popc(lb & below);
                 front_s[(int64_t)pos * T + c] = s_share[j][tid];
-                if (leader) front_id[pos] = (int32_t)(base + j * kNodesPerStep + tid / T);
+                if (leader) {
+                    const int32_t node = (int32_t)(base + j * kNodesPerStep + tid / T);
+                    front_id[pos] = node;
+                    // a node with many links is pushed in chunks over all warps (see kb_push)
+                    const int32_t o = s_hdeg[j][tid / T];
+                    if (o > 0) {
+                        const int nch = (o + kHeavyChunk - 1) / kHeavyChunk;
+                        const int cs = atomicAdd(&ctl->heavy_chunks, nch);
+                        heavy_cstart[pos] = cs;
+                        for (int q = 0; q < nch; q++) heavy_chunk[cs + q] = pos;
+                    }
+                }
             }
         }
         __syncthreads();
@@ -339,6 +355,8 @@ static __device__ __forceinline__ void red_add_v4(float *p, float4 v) {
 // walks 128/T links per step, each link index loaded once for its T fluids.
 template <int T>
 __global__ void __launch_bounds__(256) kb_push(const int32_t *__restrict__ front_id, const float *__restrict__ front_s,
+                                               const int32_t *__restrict__ heavy_cstart,
+                                               const int32_t *__restrict__ heavy_chunk,
                                                const int64_t *__restrict__ rp_out, const int32_t *__restrict__ col_out,
                                                float *F, BatchCtl *ctl) {
     if (ctl->done) return;
@@ -358,6 +376,7 @@ __global__ void __launch_bounds__(256) kb_push(const int32_t *__restrict__ front
             const int32_t u = front_id[p];
             const int64_t beg = rp_out[u];
             const int deg = (int)(rp_out[u + 1] - beg);
+            if (deg > kPushHeavy) continue;   // pushed below, in chunks over all warps
             const float4 s = reinterpret_cast<const float4 *>(front_s + (int64_t)p * T)[q];
             const bool any = (s.x != 0.f) || (s.y != 0.f) || (s.z != 0.f) || (s.w != 0.f);
             if (!any) continue;
@@ -365,6 +384,22 @@ __global__ void __launch_bounds__(256) kb_push(const int32_t *__restrict__ front
                 const int32_t j = col_out[beg + e];
                 if (j != u) red_add_v4(F + (int64_t)j * T + 4 * q, s);
             }
+        }
+    }
+    // nodes with more than kPushHeavy links: kHeavyChunk-link chunks over all warps
+    const int hch = ctl->heavy_chunks;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < hch; c += nwarps) {
+        const int p = heavy_chunk[c];
+        const int32_t u = front_id[p];
+        const float4 s = reinterpret_cast<const float4 *>(front_s + (int64_t)p * T)[q];
+        const bool any = (s.x != 0.f) || (s.y != 0.f) || (s.z != 0.f) || (s.w != 0.f);
+        const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * kHeavyChunk;
+        const int64_t ce = min(cb + (int64_t)kHeavyChunk, rp_out[u + 1]);
+        if (!any) continue;
+        for (int64_t e = cb + es; e < ce; e += EPI) {
+            const int32_t j = col_out[e];
+            if (j != u) red_add_v4(F + (int64_t)j * T + 4 * q, s);
         }
     }
 }
@@ -532,6 +567,9 @@ static void ensure_batch(di_graph *g, BatchWorkspace &w, int T) {
         w.H.ensure(sizeof(double) * n * T);
         w.Bn.ensure(sizeof(double) * n * T);
         w.front_id.ensure(sizeof(int32_t) * n);
+        w.heavy_cstart.ensure(sizeof(int32_t) * n);
+        // a heavy node has at most out / kHeavyChunk + 1 chunks, and each node is one entry per sweep
+        w.heavy_chunk.ensure(sizeof(int32_t) * (size_t)(g->L / kHeavyChunk + g->n_heavy_out + 1));
         w.front_s.ensure(sizeof(float) * n * T);
         w.heavy_partial.ensure(sizeof(float2) * (size_t)(g->n_heavy_in_chunks + 1) * T);
         w.y.ensure(sizeof(float2) * n * T);
@@ -570,9 +608,11 @@ static void batch_body(di_graph *g, BatchWorkspace &w, const BLaunch &l, cudaStr
                        int set_cond) {
     BatchCtl *ctl = w.ctl.as<BatchCtl>();
     kb_select<T><<<l.sel, 256, 0, s>>>(w.F.as<float>(), w.H.as<double>(), g->out_info.as<int32_t>(), g->n, ctl,
-                                       w.front_id.as<int32_t>(), w.front_s.as<float>());
-    kb_push<T><<<l.push, 256, 0, s>>>(w.front_id.as<int32_t>(), w.front_s.as<float>(), g->rp_out.as<int64_t>(),
-                                      g->col_out.as<int32_t>(), w.F.as<float>(), ctl);
+                                       w.front_id.as<int32_t>(), w.front_s.as<float>(), w.heavy_cstart.as<int32_t>(),
+                                       w.heavy_chunk.as<int32_t>());
+    kb_push<T><<<l.push, 256, 0, s>>>(w.front_id.as<int32_t>(), w.front_s.as<float>(), w.heavy_cstart.as<int32_t>(),
+                                      w.heavy_chunk.as<int32_t>(), g->rp_out.as<int64_t>(), g->col_out.as<int32_t>(),
+                                      w.F.as<float>(), ctl);
     kb_reduce<T><<<l.red, 256, 0, s>>>(w.F.as<float>(), g->n, w.partials.as<double>(), ctl, h, set_cond);
 }
 

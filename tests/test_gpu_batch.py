@@ -139,3 +139,24 @@ def test_first_batch_call_with_explicit_tile_and_host_loop():
     for r in range(5):
         ref = _oracle_X(og, oracle.ppr_B(n, seeds[off[r]:off[r + 1]], D))
         assert rel_l1(X1[r], ref) <= TOL_X and rel_l1(X2[r], ref) <= TOL_X
+
+
+@pytest.mark.parametrize("tile", [8, 32])
+def test_batch_with_nodes_of_many_out_links(tile):
+    # two nodes with more out-links than one warp should walk (pushed in chunks over all warps)
+    lib()
+    n, src, dst = workloads.small_random_graph(20000, 80000, seed=111)
+    fan = workloads.u64(112, 1, 14000) % np.uint64(n)
+    hub_src = np.concatenate([np.full(9000, 5, np.int32), np.full(5000, 17, np.int32)])
+    src = np.concatenate([src, hub_src])
+    dst = np.concatenate([dst, fan.astype(np.int32)])
+    g = di.di_graph_create(n, src, dst)
+    og = oracle.build(n, src, dst)
+    assert int(og.outdeg[5]) > 4096 and int(og.outdeg[17]) > 4096
+    off = np.array([0, 1, 3, 6], np.int64)
+    seeds = np.array([5, 17, 900, 5, 17, 3000], np.int32)
+    X, res, info = di.di_ppr_batch(g, off, seeds, D, 1e-10, rhs_tile=tile)
+    assert np.all(res <= 1e-10)
+    for r in range(3):
+        ref = _oracle_X(og, oracle.ppr_B(n, seeds[off[r]:off[r + 1]], D))
+        assert rel_l1(X[r], ref) <= TOL_X, r
