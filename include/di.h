@@ -80,7 +80,7 @@ typedef struct {
                             sweeping from it until ||F*||_1 <= tol (at most 4 rounds). */
     int32_t host_loop;   /* 1: drive sweeps from the host (one sync per sweep) instead of a CUDA
                             graph WHILE node; default 0 */
-    int32_t rhs_tile;    /* batched solves: RHS per tile (0: autotuned; else 1..64) */
+    int32_t rhs_tile;    /* batched solves: RHS per tile, 4, 8, 16 or 32 (0: autotuned per graph) */
     int32_t profile;     /* 1: host-driven sweeps with CUDA events around every kernel launch;
                             fills the per-kernel times of di_solve_info (slower: one sync per
                             sweep) */
