@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(256) k_e_visit(const int32_t *nodes, int32_t c
 // entries' degrees, then each lane takes kPushVT contiguous links of the batch's concatenated
 // links per round, finds their owner once (binary search over the warp's 33 offsets in shared
 // memory) and keeps kPushVT independent index loads in flight before its atomic adds.
-constexpr int kPushVT = 8;
+constexpr int kPushVT = 4;   // measured on GB300: 4 beats 2, 8 and 16 (fewer registers, more blocks)
 
 template <class T>
 __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_id, const T *__restrict__ front_s,
