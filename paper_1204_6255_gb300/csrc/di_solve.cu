@@ -212,12 +212,14 @@ __device__ __forceinline__ void st_keep(double *p, double v, uint64_t pol) {
 
 // Node part of a visit: transit (loop closed form) and the per-link share d * transit / out.
 // FP32 fluid: the arithmetic stays in FP32 (this part's FP64 rate is a small fraction of its
-// FP32 rate); the transit is widened to FP64 only to be added to H.
-__device__ __forceinline__ void visit_math(float f, int32_t o, bool lp, double d, float d_f, double &t, float &share) {
+// FP32 rate); the transit is widened to FP64 only to be added to H. One quotient serves both:
+// q = f / (out - d) for a loop node (transit q * out, share q * d), q = f / out otherwise
+// (transit f, share q * d); the fast FP32 division is within 2 ulp.
+__device__ __forceinline__ void visit_math(float f, int32_t o, bool lp, double, float d_f, double &t, float &share) {
     const float of = (float)o;
-    const float tf = lp ? f * of / (of - d_f) : f;
-    t = (double)tf;
-    share = o ? tf * d_f / of : 0.f;
+    const float q = o ? __fdividef(f, lp ? of - d_f : of) : 0.f;
+    share = q * d_f;
+    t = (double)(lp ? q * of : f);
 }
 __device__ __forceinline__ void visit_math(double f, int32_t o, bool lp, double d, float, double &t, double &share) {
     t = lp ? f * (double)o / ((double)o - d) : f;
@@ -230,15 +232,19 @@ __device__ __forceinline__ bool selects(double f, int32_t o, bool cyc, double th
     return cyc ? (f != 0.0) : (fabs(f) > thr * (double)o);
 }
 
-// Nodes are visited in chunks of kSelChunk consecutive ids per block iteration; the frontier
+// Nodes are visited in chunks of kSelChunk consecutive ids per block iteration; warp w of the
+// block owns the kSelWarpNodes consecutive ids from base + w * kSelWarpNodes. The frontier
 // entries of a chunk are compacted with one atomic per chunk, so the frontier is id-sorted
 // within each chunk (the push then walks neighbouring rows together). An entry is the node id
 // and its share (8 bytes); the push reads the row bounds itself, from neighbouring row pointers.
 constexpr int kSelItems = 8;
 constexpr int kTrackResync = 8;      // an exact reduction at least every kTrackResync sweeps
 constexpr double kTrackBand = 16.0;  // ... and at every sweep once r <= kTrackBand * tol
-constexpr int kSelChunk = 256 * kSelItems;
+constexpr int kSelWarpNodes = 32 * kSelItems;
+constexpr int kSelChunk = 8 * kSelWarpNodes;   // 256 threads
 constexpr int kSelMinBlocks = 4;
+template <class T>
+constexpr int kSelBatch = sizeof(T) == 4 ? 4 : 2;   // packed rounds of 32 visits whose history loads fly together
 
 template <class T>
 __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, const int32_t *out_info,
@@ -247,30 +253,41 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                                                             int32_t *heavy_chunk, int4 *chunks) {
     __shared__ double scratch[32];
     __shared__ unsigned long long scratch_u[32];
-    __shared__ int wcount[kSelItems][8];
-    __shared__ int chunk_base;
+    // Per warp, the selected nodes of its range packed in id order: fluid, degree word and
+    // offset within the range. After their visits the same slots hold the warp's frontier
+    // entries (share, offset), again in id order.
+    __shared__ T s_f[8][kSelWarpNodes];
+    __shared__ int32_t s_info[8][kSelWarpNodes];
+    __shared__ uint8_t s_off[8][kSelWarpNodes];
+    __shared__ int s_wcount[8], s_wbase[8];
+    __shared__ int s_chunk_base;
+    __shared__ double s_thr;
     if (ctl->done) return;
-    const double r = ctl->r, d = ctl->d;
+    if (threadIdx.x == 0) s_thr = ctl->L > 0.0 ? ctl->r / ctl->L : 0.0;
+    __syncthreads();
+    const double r = ctl->r, d = ctl->d, thr = s_thr;
     const bool cyc = ctl->schedule == DI_CYC || ctl->force_cyc;
     const bool plain_loops = ctl->plain_loops != 0;
-    const double thr = ctl->L > 0.0 ? r / ctl->L : 0.0;
     const float thr_f = (float)thr, d_f = (float)d;
     const uint64_t keep = policy_evict_last();
     const unsigned lane = lane_id(), lt = lanemask_lt();
     const int warp = threadIdx.x >> 5;
+    T *wf = s_f[warp];
+    int32_t *winfo = s_info[warp];
+    uint8_t *woff = s_off[warp];
     float e_run = 0.f;   // dangling mass of this thread, widened at the end
     float ab_run = 0.f;  // fluid absorbed by this thread's visits (FP32: FP64 is slow here)
     double e_loc = 0.0;
-    unsigned long long pushed = 0, visited = 0;
+    unsigned long long pushed = 0;
+    unsigned visited = 0;
     for (int64_t base = (int64_t)blockIdx.x * kSelChunk; base < n; base += (int64_t)gridDim.x * kSelChunk) {
-        // The loads of a chunk are issued in two waves before any store, so each thread keeps
-        // every item's loads in flight at once: first F and the degree of all items, then H of
-        // the selected ones.
+        const int64_t wb = base + (int64_t)warp * kSelWarpNodes;
+        // F and the degree word of the warp's nodes: every load is issued before any is used
         T f[kSelItems];
         int32_t info[kSelItems];
 #pragma unroll
         for (int j = 0; j < kSelItems; j++) {
-            const int64_t i = base + j * 256 + threadIdx.x;
+            const int64_t i = wb + j * 32 + lane;
             f[j] = (T)0;
             info[j] = 0;
             if (i < n) {
@@ -278,107 +295,133 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                 info[j] = __ldcs(out_info + i);
             }
         }
-        unsigned sel = 0;
-#pragma unroll
-        for (int j = 0; j < kSelItems; j++)
-            if (base + j * 256 + threadIdx.x < n && selects(f[j], info[j] & 0x7fffffff, cyc, thr, thr_f)) sel |= 1u << j;
-        double h[kSelItems];
+        // pack the selected nodes, so the visits below run on full warps
+        int cnt = 0;
 #pragma unroll
         for (int j = 0; j < kSelItems; j++) {
-            const int64_t i = base + j * 256 + threadIdx.x;
-            h[j] = 0.0;
-            if (sel >> j & 1u) h[j] = __ldcs(H + i);
+            const bool s = wb + j * 32 + lane < n && selects(f[j], info[j] & 0x7fffffff, cyc, thr, thr_f);
+            const unsigned b = __ballot_sync(kFull, s);
+            if (s) {
+                const int p = cnt + __popc(b & lt);
+                wf[p] = f[j];
+                winfo[p] = info[j];
+                woff[p] = (uint8_t)(j * 32 + lane);
+            }
+            cnt += __popc(b);
         }
-        unsigned ballots[kSelItems];
-        T shares[kSelItems];
+        __syncwarp();
+        int nlight = 0;
+        for (int r0 = 0; r0 < cnt; r0 += 32 * kSelBatch<T>) {
+            T pf[kSelBatch<T>];
+            int32_t pinfo[kSelBatch<T>];
+            int poff[kSelBatch<T>];
+            double ph[kSelBatch<T>];
 #pragma unroll
-        for (int j = 0; j < kSelItems; j++) {
-            const int64_t i = base + j * 256 + threadIdx.x;
-            bool light = false, heavy = false;
-            T share = (T)0;
-            const int32_t o = info[j] & 0x7fffffff;
-            if (sel >> j & 1u) {
-                const bool lp = !plain_loops && info[j] < 0;
-                st_keep(F + i, (T)0, keep);
-                double t;
-                visit_math(f[j], o, lp, d, d_f, t, share);
-                __stcs(H + i, h[j] + t);
-                visited++;
-                pushed += (unsigned long long)o;
-                // F loses f and regains the share on each link pushed (all but a closed-form loop)
-                ab_run += (float)f[j] - (float)share * (float)(o - (lp ? 1 : 0));
-                if (o == 0) {
-                    if (sizeof(T) == 4) e_run += (float)t; else e_loc += t;
-                } else if (o > kPushHeavy) {
-                    heavy = true;
-                } else if (o - (lp ? 1 : 0) > 0) {
-                    light = true;
+            for (int v = 0; v < kSelBatch<T>; v++) {
+                const int k = r0 + v * 32 + lane;
+                pf[v] = (T)0;
+                pinfo[v] = 0;
+                poff[v] = 0;
+                ph[v] = 0.0;
+                if (k < cnt) {
+                    pf[v] = wf[k];
+                    pinfo[v] = winfo[k];
+                    poff[v] = woff[k];
+                    ph[v] = __ldcs(H + wb + poff[v]);
                 }
             }
-            shares[j] = share;
-            ballots[j] = __ballot_sync(kFull, light);
-            if (lane == 0) wcount[j][warp] = __popc(ballots[j]);
-            // heavy nodes are rare: one atomic per warp that has any
-            const unsigned bh = __ballot_sync(kFull, heavy);
-            if (bh) {
-                const int leader = __ffs(bh) - 1;
-                int p0 = 0;
-                if ((int)lane == leader) p0 = atomicAdd(&ctl->heavy_count, __popc(bh));
-                p0 = __shfl_sync(kFull, p0, leader);
-                if (heavy) {
-                    // the node's links are pushed in kHeavyChunk-link chunks over all warps; the
-                    // chunk list maps each chunk back to its entry
-                    const int p = p0 + __popc(bh & lt);
-                    heavy_id[p] = (int32_t)i;
-                    heavy_s[p] = share;
-                    const int nch = (o + kHeavyChunk - 1) / kHeavyChunk;
-                    const int cs = atomicAdd(&ctl->heavy_chunks, nch);
-                    heavy_cstart[p] = cs;
-                    for (int c = 0; c < nch; c++) heavy_chunk[cs + c] = p;
+            // every slot of these rounds is in registers before entries overwrite slots below
+            __syncwarp();
+#pragma unroll
+            for (int v = 0; v < kSelBatch<T>; v++) {
+                const int k = r0 + v * 32 + lane;
+                const int64_t i = wb + poff[v];
+                bool light = false, heavy = false;
+                T share = (T)0;
+                const int32_t o = pinfo[v] & 0x7fffffff;
+                if (k < cnt) {
+                    const bool lp = !plain_loops && pinfo[v] < 0;
+                    st_keep(F + i, (T)0, keep);
+                    double t;
+                    visit_math(pf[v], o, lp, d, d_f, t, share);
+                    __stcs(H + i, ph[v] + t);
+                    visited++;
+                    pushed += (unsigned long long)o;
+                    // F loses f and regains the share on each link pushed (all but a closed-form loop)
+                    ab_run += (float)pf[v] - (float)share * (float)(o - (lp ? 1 : 0));
+                    if (o == 0) {
+                        if (sizeof(T) == 4) e_run += (float)t; else e_loc += t;
+                    } else if (o > kPushHeavy) {
+                        heavy = true;
+                    } else if (o - (lp ? 1 : 0) > 0) {
+                        light = true;
+                    }
+                }
+                const unsigned bl = __ballot_sync(kFull, light);
+                if (light) {
+                    const int p = nlight + __popc(bl & lt);
+                    wf[p] = share;
+                    woff[p] = (uint8_t)poff[v];
+                }
+                nlight += __popc(bl);
+                // heavy nodes are rare: one atomic per warp that has any
+                const unsigned bh = __ballot_sync(kFull, heavy);
+                if (bh) {
+                    const int leader = __ffs(bh) - 1;
+                    int p0 = 0;
+                    if ((int)lane == leader) p0 = atomicAdd(&ctl->heavy_count, __popc(bh));
+                    p0 = __shfl_sync(kFull, p0, leader);
+                    if (heavy) {
+                        // the node's links are pushed in kHeavyChunk-link chunks over all warps;
+                        // the chunk list maps each chunk back to its entry
+                        const int p = p0 + __popc(bh & lt);
+                        heavy_id[p] = (int32_t)i;
+                        heavy_s[p] = share;
+                        const int nch = (o + kHeavyChunk - 1) / kHeavyChunk;
+                        const int cs = atomicAdd(&ctl->heavy_chunks, nch);
+                        heavy_cstart[p] = cs;
+                        for (int c = 0; c < nch; c++) heavy_chunk[cs + c] = p;
+                    }
                 }
             }
         }
+        // one atomic reserves the chunk's frontier entries and its segment slot
+        if (lane == 0) s_wcount[warp] = nlight;
         __syncthreads();
         if (threadIdx.x == 0) {
             int run = 0;
-            for (int j = 0; j < kSelItems; j++)
-                for (int w = 0; w < 8; w++) {
-                    const int c = wcount[j][w];
-                    wcount[j][w] = run;
-                    run += c;
-                }
-            chunk_base = 0;
+#pragma unroll
+            for (int w = 0; w < 8; w++) {
+                s_wbase[w] = run;
+                run += s_wcount[w];
+            }
+            s_chunk_base = 0;
             if (run) {
                 const unsigned long long fc = atomicAdd(&ctl->front_chunks, (1ull << kFrontBits) | (unsigned)run);
-                chunk_base = front_entries(fc);
-                chunks[front_segments(fc)] = make_int4((int)base, chunk_base, run, 0);
+                s_chunk_base = front_entries(fc);
+                chunks[front_segments(fc)] = make_int4((int)base, s_chunk_base, run, 0);
             }
         }
         __syncthreads();
-        const int cb = chunk_base;
-#pragma unroll
-        for (int j = 0; j < kSelItems; j++) {
-            if (ballots[j] & (1u << lane)) {
-                const int p = cb + wcount[j][warp] + __popc(ballots[j] & lt);
-                const int64_t i = base + j * 256 + threadIdx.x;
-                __stcs(front_id + p, (int32_t)i);
-                __stcs(front_s + p, shares[j]);
-            }
+        const int cb = s_chunk_base + s_wbase[warp];
+        for (int k = lane; k < nlight; k += 32) {
+            __stcs(front_id + cb + k, (int32_t)(wb + woff[k]));
+            __stcs(front_s + cb + k, wf[k]);
         }
-        __syncthreads();
+        __syncwarp();   // the next chunk's packing reuses the slots
     }
     e_loc += (double)e_run;
     e_loc = block_sum(e_loc, scratch);
     const double absorbed = block_sum((double)ab_run, scratch);
     pushed = block_sum(pushed, scratch_u);
-    visited = block_sum(visited, scratch_u);
+    const unsigned long long nvis = block_sum((unsigned long long)visited, scratch_u);
     if (threadIdx.x == 0) {
         if (e_loc != 0.0) atomicAdd(&ctl->e, e_loc);
         if (absorbed != 0.0) atomicAdd(&ctl->absorbed, absorbed);
         if (pushed) atomicAdd(&ctl->pushed, pushed);
-        if (visited) {
-            atomicAdd(&ctl->visited, visited);
-            atomicAdd(&ctl->last_selected, (int)visited);
+        if (nvis) {
+            atomicAdd(&ctl->visited, nvis);
+            atomicAdd(&ctl->last_selected, (int)nvis);
         }
         if (blockIdx.x == 0) {
             const int sw = atomicAdd(&ctl->sweeps, 1) + 1;
