@@ -27,6 +27,7 @@
 // walks a run of kPullVT contiguous in-links, and a segmented scan joins the rows that span
 // lanes. Rows with more than kPullHeavy in-links are summed chunk-wise by k_pull_heavy first.
 // Power iteration per column (PI') runs the sweep kernels above with self-links as plain links.
+#include <climits>
 #include <cmath>
 #include <cstring>
 
@@ -520,11 +521,13 @@ __global__ void __launch_bounds__(256) k_e_visit(const int32_t *nodes, int32_t c
     }
 }
 
-// Push, one warp per batch of 32 frontier entries (no block barriers): the warp scans the
-// entries' degrees, then each lane takes kPushVT contiguous links of the batch's concatenated
+// Push, one warp per batch of 32 frontier entries (no block barriers). Rows of kPushRow links or
+// more go one at a time over the whole warp, 32 consecutive links per load. For the others the
+// warp scans their degrees, then each lane takes kPushVT contiguous links of their concatenated
 // links per round, finds their owner once (binary search over the warp's 33 offsets in shared
 // memory) and keeps kPushVT independent index loads in flight before its atomic adds.
 constexpr int kPushVT = 4;   // measured on GB300: 4 beats 2, 8 and 16 (fewer registers, more blocks)
+constexpr int kPushRow = 64; // rows at least this long are pushed warp-wide (measured: 64 beats 16 and 32)
 
 template <class T>
 __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_id, const T *__restrict__ front_s,
@@ -689,12 +692,45 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                 ebeg = __ldg(rp_out + eu);
                 deg = (int)(__ldg(rp_out + eu + 1) - ebeg);
             }
-            const int inc = warp_inclusive_scan(deg);
+            // rows of kPushRow links or more: one row at a time over the whole warp, 32
+            // consecutive links per load, no owner lookup
+            const bool row = deg >= kPushRow;
+            for (unsigned rows = __ballot_sync(kFull, row); rows; rows &= rows - 1) {
+                const int src = __ffs(rows) - 1;
+                const int64_t rb = __shfl_sync(kFull, ebeg, src);
+                const int rd = __shfl_sync(kFull, deg, src);
+                const int32_t ru = __shfl_sync(kFull, eu, src);
+                const float rs = __shfl_sync(kFull, es, src);
+                for (int k0 = lane; k0 < rd; k0 += 32 * kPushVT) {
+                    int32_t jr[kPushVT];
+#pragma unroll
+                    for (int v = 0; v < kPushVT; v++) jr[v] = k0 + 32 * v < rd ? ld_stream(col_push + rb + k0 + 32 * v, stream) : 0;
+#pragma unroll
+                    for (int v = 0; v < kPushVT; v++) {
+                        const int32_t j = jr[v] & 0x7fffffff;
+                        if (k0 + 32 * v >= rd || (j == ru && !loops)) continue;
+                        const unsigned off = (unsigned)(j - lo);
+                        if (use_win && off < (unsigned)kWin) atomicAdd(&s_win[off], rs);
+                        else far_add(jr[v], rs);
+                    }
+                }
+            }
+            // the other entries, compacted (each has at least one link): kPushVT contiguous links
+            // per lane over their concatenated rows
+            const int dsm = row ? 0 : deg;
+            const unsigned small = __ballot_sync(kFull, dsm > 0);
+            if (!small) continue;
+            const int inc = warp_inclusive_scan(dsm);
             const int total = __shfl_sync(kFull, inc, 31);
-            const int64_t rbase = ebeg - (inc - deg);   // link e of the batch sits at col_push[rbase + e]
-            s_off[w][lane] = inc - deg;
-            if (lane == 31) s_off[w][32] = total;
-            s_rec[w][lane] = make_int4((int)(uint32_t)(uint64_t)rbase, (int)((uint64_t)rbase >> 32), eu, __float_as_int(es));
+            const int64_t rbase = ebeg - (inc - dsm);   // link e of the batch sits at col_push[rbase + e]
+            s_off[w][lane + 1] = INT_MAX;
+            __syncwarp();
+            if (dsm > 0) {
+                const int pos = __popc(small & lanemask_lt());
+                s_off[w][pos] = inc - dsm;
+                s_rec[w][pos] = make_int4((int)(uint32_t)(uint64_t)rbase, (int)((uint64_t)rbase >> 32), eu, __float_as_int(es));
+            }
+            if (lane == 0) s_off[w][__popc(small)] = total;
             __syncwarp();
             for (int e0 = lane * kPushVT; e0 < total; e0 += 32 * kPushVT) {
                 int k = 0;   // last entry with s_off[k] <= e0
