@@ -211,16 +211,38 @@ __device__ __forceinline__ void st_keep(double *p, double v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
 }
 
+// Exact FP32 -> FP64 widening on the integer units (IEEE 754 binary32 to binary64: the exponent
+// is rebiased from 127 to 1023 and the fraction extended with zeros; a subnormal is normalised
+// first; infinities and NaN keep the all-ones exponent).
+__device__ __forceinline__ double widen(float x) {
+    const uint32_t b = __float_as_uint(x);
+    uint32_t e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    if (e == 0xffu) {
+        e = 0x7ffu - 896u;
+    } else if (e == 0u) {
+        if (m == 0u) {
+            e = 0u - 896u;   // signed zero
+        } else {
+            const int s = __clz(m) - 8;   // moves the leading one to bit 23
+            m = (m << s) & 0x7fffffu;
+            e = 1u - (uint32_t)s;
+        }
+    }
+    const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
+    return __hiloint2double((int)hi, (int)(m << 29));
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 // Node part of a visit: transit (loop closed form) and the per-link share d * transit / out.
 // FP32 fluid: the arithmetic stays in FP32 (this part's FP64 rate is a small fraction of its
 // FP32 rate); the transit is widened to FP64 only to be added to H. One quotient serves both:
 // q = f / (out - d) for a loop node (transit q * out, share q * d), q = f / out otherwise
 // (transit f, share q * d); the fast FP32 division is within 2 ulp.
-__device__ __forceinline__ void visit_math(float f, int32_t o, bool lp, double, float d_f, double &t, float &share) {
+__device__ __forceinline__ void visit_math(float f, int32_t o, bool lp, double, float d_f, float &t, float &share) {
     const float of = (float)o;
     const float q = o ? __fdividef(f, lp ? of - d_f : of) : 0.f;
     share = q * d_f;
-    t = (double)(lp ? q * of : f);
+    t = lp ? q * of : f;
 }
 __device__ __forceinline__ void visit_math(double f, int32_t o, bool lp, double d, float, double &t, double &share) {
     t = lp ? f * (double)o / ((double)o - d) : f;
@@ -276,9 +298,8 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
     T *wf = s_f[warp];
     int32_t *winfo = s_info[warp];
     uint8_t *woff = s_off[warp];
-    float e_run = 0.f;   // dangling mass of this thread, widened at the end
+    T e_run = (T)0;      // dangling mass of this thread
     float ab_run = 0.f;  // fluid absorbed by this thread's visits (FP32: FP64 is slow here)
-    double e_loc = 0.0;
     unsigned long long pushed = 0;
     unsigned visited = 0;
     for (int64_t base = (int64_t)blockIdx.x * kSelChunk; base < n; base += (int64_t)gridDim.x * kSelChunk) {
@@ -343,15 +364,15 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                 if (k < cnt) {
                     const bool lp = !plain_loops && pinfo[v] < 0;
                     st_keep(F + i, (T)0, keep);
-                    double t;
+                    T t;
                     visit_math(pf[v], o, lp, d, d_f, t, share);
-                    __stcs(H + i, ph[v] + t);
+                    __stcs(H + i, ph[v] + widen(t));
                     visited++;
                     pushed += (unsigned long long)o;
                     // F loses f and regains the share on each link pushed (all but a closed-form loop)
                     ab_run += (float)pf[v] - (float)share * (float)(o - (lp ? 1 : 0));
                     if (o == 0) {
-                        if (sizeof(T) == 4) e_run += (float)t; else e_loc += t;
+                        e_run += t;
                     } else if (o > kPushHeavy) {
                         heavy = true;
                     } else if (o - (lp ? 1 : 0) > 0) {
@@ -411,11 +432,21 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
         }
         __syncwarp();   // the next chunk's packing reuses the slots
     }
-    e_loc += (double)e_run;
-    e_loc = block_sum(e_loc, scratch);
-    const double absorbed = block_sum((double)ab_run, scratch);
+    // warp sums in the fluid's type, block sums in FP64 by one thread
+    const T e_w = warp_sum(e_run);
+    const float ab_w = warp_sum(ab_run);
+    if (lane == 0) {
+        scratch[warp] = (double)e_w;
+        scratch[8 + warp] = (double)ab_w;
+    }
     pushed = block_sum(pushed, scratch_u);
     const unsigned long long nvis = block_sum((unsigned long long)visited, scratch_u);
+    double e_loc = 0.0, absorbed = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < 8; w++) {
+            e_loc += scratch[w];
+            absorbed += scratch[8 + w];
+        }
     if (threadIdx.x == 0) {
         if (e_loc != 0.0) atomicAdd(&ctl->e, e_loc);
         if (absorbed != 0.0) atomicAdd(&ctl->absorbed, absorbed);
@@ -474,11 +505,11 @@ __global__ void __launch_bounds__(256) k_e_visit(const int32_t *nodes, int32_t c
             const T f = F[u];
             o = out_info[u] & 0x7fffffff;
             b = rp_out[u];
-            double t;
+            T t;
             visit_math(f, o, false, d, d_f, t, share);
             F[u] = (T)0;
-            H[u] += t;
-            if (o == 0) e_loc += t;
+            H[u] += widen(t);
+            if (o == 0) e_loc += widen(t);
             visited++;
             pushed += (unsigned long long)o;
             if (o <= kEWarpLinks)

@@ -80,3 +80,17 @@ def test_ragged_node_counts(n):
     for r, sd in enumerate(([0], [n - 1, n // 2])):
         pr, _, _, ok = oracle.di(og, oracle.ppr_B(n, np.array(sd), D), D, 1e-15, oracle.SOP)
         assert ok and rel_l1(X[r], pr) <= 1e-6
+
+
+def test_fp32_transit_widened_exactly():
+    """With no links each node's history is its own B after one visit: the FP32 transit is
+    widened to FP64 exactly, for normal and subnormal FP32 values alike."""
+    vals = np.array([1.5, 0.15625, 2.0 ** 100, 2.0 ** -126, 2.0 ** -127, 2.0 ** -140, 2.0 ** -149,
+                     3 * 2.0 ** -149, (2 - 2.0 ** -23) * 2.0 ** -100, 0.0], np.float64)
+    B = vals.astype(np.float32).astype(np.float64)   # every value exact in FP32
+    assert np.array_equal(B, vals)
+    g = _no_links(B.size)
+    for sched in (di.DI_CYC, di.DI_SOP):
+        for e in (0, 1):
+            X, info = di.di_solve_ex(g, B, D, 1e-300, schedule=sched, fluid=di.DI_FLUID_F32, e_prediffuse=e)
+            assert np.array_equal(X, B), (sched, e, X, B)
