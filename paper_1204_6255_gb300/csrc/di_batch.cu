@@ -40,6 +40,7 @@ static void solve_tile(di_graph *g, int c0, int ncols, double d, const double *t
     hc.schedule = schedule;
     hc.max_sweeps = max_sweeps;
     hc.last_selected = -1;
+    hc.split = refine ? 1 : 0;
     for (int c = 0; c < ncols; c++) {
         hc.tol[c] = tol_host[c0 + c];
         hc.active[c] = 1;
@@ -77,13 +78,17 @@ static void solve_tile(di_graph *g, int c0, int ncols, double d, const double *t
         // reactivate the columns whose exact residual is above their tolerance
         bool again = false;
         for (int c = 0; c < ncols; c++) {
-            const bool a = hc.r[c] > hc.tol[c];
+            const bool a = hc.r[c] > tol_host[c0 + c];
             hc.active[c] = a ? 1 : 0;
             again = again || a;
         }
         if (!again || hc.status || hc.sweeps >= max_sweeps || rounds >= 4) break;
-        // continuation sweeps aim at half the tolerance, so the next exact residual lands below it
-        for (int c = 0; c < ncols; c++) hc.tol[c] = 0.5 * tol_host[c0 + c];
+        // continuation sweeps aim just under the tolerance after a column's halfway refinement
+        // (its fluid's rounding since then is far below tol), else at half of it
+        for (int c = 0; c < ncols; c++) {
+            const bool after_split = rounds == 1 && hc.tol[c] > tol_host[c0 + c];
+            hc.tol[c] = (after_split ? kAimAfterSplit : 0.5) * tol_host[c0 + c];
+        }
         DI_CHECK_CUDA(cudaMemcpyAsync(ctl->tol, hc.tol, sizeof(hc.tol), cudaMemcpyHostToDevice, s));
         DI_CHECK_CUDA(cudaMemcpyAsync(ctl->active, hc.active, sizeof(hc.active), cudaMemcpyHostToDevice, s));
         int zero = 0;

@@ -136,6 +136,8 @@ struct SolveCtl {
     int32_t plain_loops;      // 1: a self-link is a plain link (power iteration per column), no
                               //    closed form for loop nodes
     unsigned long long front_total;  // frontier entries over all sweeps
+    int32_t split;            // 1: the first reduction raises tol to sqrt(tol * r), the point of
+                              //    the first refinement of a refined FP32 solve
 };
 
 // Fixed tuning of the single-RHS kernels.
@@ -146,6 +148,9 @@ __host__ __device__ inline int32_t front_entries(unsigned long long fc) {
 __host__ __device__ inline int32_t front_segments(unsigned long long fc) { return (int32_t)(fc >> kFrontBits); }
 
 constexpr int kPushHeavy = 4096;
+// A refined FP32 solve refines first where ||F||_1 reaches sqrt(tol * ||F_0||_1) (halfway on a log
+// scale); its continuation sweeps then aim at kAimAfterSplit * tol.
+constexpr double kAimAfterSplit = 0.9;
 constexpr int kHeavyChunk = 1024;   // links per work unit of a heavy node's push    // out-degree above which a node's edges are split over warps
 constexpr int kPullHeavy = 8192;    // in-degree above which a row's edges are split over warps
 constexpr int kPullChunk = 4096;    // edges per heavy-row chunk of the pull

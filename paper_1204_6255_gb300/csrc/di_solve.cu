@@ -134,7 +134,7 @@ __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl,
     __shared__ double scratch[32];
     double tot;
     if (ctl->reduce_est) {
-        // fluid is nonnegative, so sum |F| after the sweep is the sum before it less what the
+        // with nonnegative fluid, sum |F| after the sweep is the sum before it less what the
         // visits absorbed (the select decided this per sweep; see there for when)
         if (blockIdx.x != 0 || threadIdx.x != 0) return;
         tot = ctl->r - ctl->absorbed;
@@ -157,6 +157,13 @@ __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl,
         ctl->heavy_chunks = 0;
         ctl->chunk_next = 0;
         if (set_cond) ctl->body_runs++;
+        if (ctl->split) {
+            // first reduction of a refined FP32 solve: its sweeps stop halfway (geometrically)
+            // between ||B||_1 and tol, where an exact residual replaces the fluid
+            ctl->split = 0;
+            const double mid = sqrt(ctl->tol * tot);
+            if (mid > ctl->tol) ctl->tol = mid;
+        }
         bool cont = ctl->status == 0 && tot > ctl->tol && ctl->sweeps < ctl->max_sweeps;
         ctl->done = cont ? 0 : 1;
         if (set_cond) cudaGraphSetConditional(h, cont ? 1u : 0u);
@@ -1324,11 +1331,12 @@ static void launch_refine(di_graph *g, const Launch &l, double d, cudaStream_t s
 }
 
 static void write_ctl(di_graph *g, double d, double tol, int schedule, int max_sweeps, int plain_loops,
-                      cudaStream_t s, int track = 0) {
+                      cudaStream_t s, int track = 0, int split = 0) {
     SolveCtl &c = *g->ws.ctl_host;
     memset(&c, 0, sizeof(c));
     c.plain_loops = plain_loops;
     c.track = track;
+    c.split = split;
     c.d = d;
     c.tol = tol;
     c.L = (double)g->L;
@@ -1360,10 +1368,12 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
     const Launch l = launch_shape<T>(g);
     SolveCtl *ctl = ws.ctl.as<SolveCtl>();
     to_device(ws.B.p, B, sizeof(double) * (size_t)g->n, s);
-    // r may be tracked between exact reductions only while the fluid is certainly nonnegative:
-    // FP32 sweeps from (0, B) until the first refinement (whose exact residual may be signed);
-    // a refined solve's final residual is exact in any case
-    write_ctl(g, d, tol, schedule, max_sweeps, plain_loops, s, (sizeof(T) == 4 && refine && !H0) ? 1 : 0);
+    // r may be tracked between exact reductions while the fluid is nonnegative or nearly so:
+    // FP32 sweeps from (0, B), up to and after their halfway refinement (see k_reduce: that
+    // refinement comes before the fluid's rounding has grown comparable to tol). A refined
+    // solve's final residual is exact in any case.
+    write_ctl(g, d, tol, schedule, max_sweeps, plain_loops, s, (sizeof(T) == 4 && refine && !H0) ? 1 : 0,
+              (sizeof(T) == 4 && refine) ? 1 : 0);
     if (profile) host_loop = 1;
     KernelClock kc(profile != 0, s);
     cudaEvent_t e0, e1;
@@ -1430,11 +1440,20 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
             read_ctl(g, s);
             rounds++;
             if (ws.ctl_host->status || ws.ctl_host->r <= tol || ws.ctl_host->sweeps >= max_sweeps || rounds >= 4) break;
-            // continuation sweeps aim at half the tolerance, so the next exact residual lands below it
-            const double half = 0.5 * tol;
-            DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->tol, &half, sizeof(double), cudaMemcpyHostToDevice, s));
-            static const int32_t no_track = 0;
-            DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->track, &no_track, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            // Continuation sweeps start from the exact residual. After the halfway refinement of
+            // a split solve the fluid's rounding since then is far below tol, so they aim just
+            // under it; otherwise at half the tolerance, so the next exact residual lands below.
+            const bool after_split = rounds == 1 && ws.ctl_host->tol > tol;
+            const double aim = (after_split ? kAimAfterSplit : 0.5) * tol;
+            DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->tol, &aim, sizeof(double), cudaMemcpyHostToDevice, s));
+            // An exact residual may have negative entries. After the halfway refinement they are
+            // of the size of the rounding it replaced, a fraction of a percent of sum |F|, so the
+            // tracked total (which follows sum F) stays on between exact reductions; otherwise
+            // every reduction sums |F|.
+            if (!after_split) {
+                static const int32_t no_track = 0;
+                DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->track, &no_track, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            }
             run_sweeps();
         }
         DI_CHECK_CUDA(cudaEventRecord(e1, s));

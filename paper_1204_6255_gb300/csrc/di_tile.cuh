@@ -43,6 +43,8 @@ struct BatchCtl {
     int32_t batch_next;
     int32_t body_runs;
     uint32_t ticket;
+    int32_t split;                   // 1: the next stop test raises each active column's tol to
+                                     //    sqrt(tol * r), its first refinement point
 };
 
 // ------------------------------------------------------------------------------------------
@@ -144,6 +146,13 @@ __device__ __forceinline__ void column_l1(const V *v, int32_t n, double *partial
 
 // Column retirement and the stop test (thread 0 of the finishing block).
 static __device__ __forceinline__ void batch_stop_test(BatchCtl *ctl, cudaGraphConditionalHandle h, int set_cond) {
+    if (ctl->split) {
+        ctl->split = 0;
+        for (int c = 0; c < ctl->ncols; c++) {
+            const double mid = sqrt(ctl->tol[c] * ctl->r[c]);
+            if (ctl->active[c] && mid > ctl->tol[c]) ctl->tol[c] = mid;
+        }
+    }
     bool any = false;
     double rsum = 0.0;
     for (int c = 0; c < ctl->ncols; c++) {
