@@ -565,6 +565,7 @@ __global__ void __launch_bounds__(256) k_e_visit(const int32_t *nodes, int32_t c
 // links per round, finds their owner once (binary search over the warp's 33 offsets in shared
 // memory) and keeps kPushVT independent index loads in flight before its atomic adds.
 constexpr int kPushVT = 4;   // measured on GB300: 4 beats 2, 8 and 16 (fewer registers, more blocks)
+constexpr int kHeavyPushUnroll = 4;   // index loads in flight per lane in a heavy node's chunk
 constexpr int kPushRow = 64; // rows at least this long are pushed warp-wide (measured: 64 beats 16 and 32)
 
 template <class T>
@@ -593,9 +594,13 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
         const T sh = heavy_s[p];
         const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * kHeavyChunk;
         const int64_t ce = min(cb + (int64_t)kHeavyChunk, rp_out[u + 1]);
-        for (int64_t k = cb + lane; k < ce; k += 32) {
-            const int32_t j = __ldcs(col_out + k);
-            if (j != u || loops) red_keep(&F[j], sh, pol);
+        for (int64_t k0 = cb + lane; k0 < ce; k0 += 32 * kHeavyPushUnroll) {
+            int32_t j[kHeavyPushUnroll];
+#pragma unroll
+            for (int v = 0; v < kHeavyPushUnroll; v++) j[v] = k0 + 32 * v < ce ? __ldcs(col_out + k0 + 32 * v) : -1;
+#pragma unroll
+            for (int v = 0; v < kHeavyPushUnroll; v++)
+                if (j[v] >= 0 && (j[v] != u || loops)) red_keep(&F[j[v]], sh, pol);
         }
     }
 
@@ -690,9 +695,13 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
         const float sh = heavy_s[p];
         const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * kHeavyChunk;
         const int64_t ce = min(cb + (int64_t)kHeavyChunk, rp_out[u + 1]);
-        for (int64_t k = cb + lane; k < ce; k += 32) {
-            const int32_t jr = ld_stream(col_push + k, stream);
-            if ((jr & 0x7fffffff) != u || loops) far_add(jr, sh);
+        for (int64_t k0 = cb + lane; k0 < ce; k0 += 32 * kHeavyPushUnroll) {
+            int32_t jr[kHeavyPushUnroll];
+#pragma unroll
+            for (int v = 0; v < kHeavyPushUnroll; v++) jr[v] = k0 + 32 * v < ce ? ld_stream(col_push + k0 + 32 * v, stream) : 0;
+#pragma unroll
+            for (int v = 0; v < kHeavyPushUnroll; v++)
+                if (k0 + 32 * v < ce && ((jr[v] & 0x7fffffff) != u || loops)) far_add(jr[v], sh);
         }
     }
 
@@ -886,6 +895,8 @@ __global__ void k_df_to_double(const float2 *X, int32_t n, double *out) {
 }
 
 // partial[c] = sum of y over the in-links of heavy-row chunk c
+constexpr int kHeavyPullUnroll = 8;
+
 __global__ void k_pull_heavy(const int64_t *rp_in, const int32_t *col_in, const int32_t *heavy_rows,
                              const int32_t *chunk_off, const int32_t *chunk_row, int32_t n_chunks,
                              const float2 *y0, const float2 *y1, const SolveCtl *ctl, int alternate,
@@ -899,7 +910,17 @@ __global__ void k_pull_heavy(const int64_t *rp_in, const int32_t *col_in, const 
         const int64_t b = rp_in[row] + (int64_t)(c - chunk_off[h]) * kPullChunk;
         const int64_t e = min(b + (int64_t)kPullChunk, rp_in[row + 1]);
         float2 s = make_float2(0.f, 0.f);
-        for (int64_t k = b + lane; k < e; k += 32) s = df_add(s, y[__ldcs(col_in + k)]);
+        // kHeavyPullUnroll index loads, then as many gathers, in flight before the additions
+        for (int64_t k0 = b + lane; k0 < e; k0 += 32 * kHeavyPullUnroll) {
+            int32_t j[kHeavyPullUnroll];
+#pragma unroll
+            for (int v = 0; v < kHeavyPullUnroll; v++) j[v] = k0 + 32 * v < e ? __ldcs(col_in + k0 + 32 * v) : -1;
+            float2 val[kHeavyPullUnroll];
+#pragma unroll
+            for (int v = 0; v < kHeavyPullUnroll; v++) val[v] = j[v] >= 0 ? y[j[v]] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int v = 0; v < kHeavyPullUnroll; v++) s = df_add(s, val[v]);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             float2 t;

@@ -389,9 +389,13 @@ __global__ void __launch_bounds__(256) kb_push(const int32_t *__restrict__ front
             const float4 s = reinterpret_cast<const float4 *>(front_s + (int64_t)p * T)[q];
             const bool any = (s.x != 0.f) || (s.y != 0.f) || (s.z != 0.f) || (s.w != 0.f);
             if (!any) continue;
-            for (int e = es; e < deg; e += EPI) {
-                const int32_t j = col_out[beg + e];
-                if (j != u) red_add_v4(F + (int64_t)j * T + 4 * q, s);
+            for (int e0 = es; e0 < deg; e0 += EPI * 4) {
+                int32_t j[4];   // four index loads in flight before the reductions
+#pragma unroll
+                for (int v = 0; v < 4; v++) j[v] = e0 + EPI * v < deg ? col_out[beg + e0 + EPI * v] : u;
+#pragma unroll
+                for (int v = 0; v < 4; v++)
+                    if (j[v] != u) red_add_v4(F + (int64_t)j[v] * T + 4 * q, s);
             }
         }
     }
@@ -406,9 +410,13 @@ __global__ void __launch_bounds__(256) kb_push(const int32_t *__restrict__ front
         const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * kHeavyChunk;
         const int64_t ce = min(cb + (int64_t)kHeavyChunk, rp_out[u + 1]);
         if (!any) continue;
-        for (int64_t e = cb + es; e < ce; e += EPI) {
-            const int32_t j = col_out[e];
-            if (j != u) red_add_v4(F + (int64_t)j * T + 4 * q, s);
+        for (int64_t e0 = cb + es; e0 < ce; e0 += EPI * 4) {
+            int32_t j[4];   // four index loads in flight before the reductions
+#pragma unroll
+            for (int v = 0; v < 4; v++) j[v] = e0 + EPI * v < ce ? col_out[e0 + EPI * v] : u;
+#pragma unroll
+            for (int v = 0; v < 4; v++)
+                if (j[v] != u) red_add_v4(F + (int64_t)j[v] * T + 4 * q, s);
         }
     }
 }
@@ -465,6 +473,7 @@ __global__ void kb_resid_heavy(const int64_t *rp_in, const int32_t *col_in, cons
                                const int32_t *chunk_off, const int32_t *chunk_row, int32_t n_chunks,
                                const float2 *y, uint32_t mask, float2 *partial) {
     constexpr int SL = 32 / T;
+    constexpr int kUnroll = 8;
     const int lane = (int)lane_id(), c = lane % T, slot = lane / T;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < n_chunks; ch += nwarps) {
@@ -474,7 +483,17 @@ __global__ void kb_resid_heavy(const int64_t *rp_in, const int32_t *col_in, cons
         const int64_t e = min(b + (int64_t)kPullChunk, rp_in[row + 1]);
         float2 acc = make_float2(0.f, 0.f);
         if (mask >> c & 1u)
-            for (int64_t k = b + slot; k < e; k += SL) acc = tdf_add(acc, y[(int64_t)__ldcs(col_in + k) * T + c]);
+            // kUnroll index loads, then as many gathers, in flight before the additions
+            for (int64_t k0 = b + slot; k0 < e; k0 += SL * kUnroll) {
+                int32_t j[kUnroll];
+#pragma unroll
+                for (int v = 0; v < kUnroll; v++) j[v] = k0 + SL * v < e ? __ldcs(col_in + k0 + SL * v) : -1;
+                float2 val[kUnroll];
+#pragma unroll
+                for (int v = 0; v < kUnroll; v++) val[v] = j[v] >= 0 ? y[(int64_t)j[v] * T + c] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int v = 0; v < kUnroll; v++) acc = tdf_add(acc, val[v]);
+            }
 #pragma unroll
         for (int o = 16; o >= T; o >>= 1) {
             float2 t;
