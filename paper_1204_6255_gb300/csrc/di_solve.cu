@@ -262,6 +262,34 @@ __device__ __forceinline__ bool selects(double f, int32_t o, bool cyc, double th
     return cyc ? (f != 0.0) : (fabs(f) > thr * (double)o);
 }
 
+// cp.async (16-byte pieces into shared memory, zero-filled past src_bytes) and its groups
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, unsigned src_bytes, uint64_t pol) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(d), "l"(src), "r"(src_bytes),
+                 "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_newest() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Copies F and the degree words of the nodes [wb, wb + 256) (those below n) into a warp's
+// shared-memory slots: 64 16-byte pieces per array, two per lane. wb is a multiple of 256, so
+// every piece is 16-byte aligned.
+__device__ __forceinline__ void sel_prefetch(float *dst_f, int32_t *dst_i, const float *F, const int32_t *info,
+                                             uint32_t wb, int32_t n, unsigned lane, uint64_t keep, uint64_t stream) {
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const uint32_t piece = lane + 32 * q, first = wb + 4 * piece;
+        if (first < (uint32_t)n) {
+            const unsigned bytes = 4u * min(4u, (uint32_t)n - first);
+            cp_async16(dst_f + 4 * piece, F + first, bytes, keep);
+            cp_async16(dst_i + 4 * piece, info + first, bytes, stream);
+        }
+    }
+}
+__device__ __forceinline__ void sel_prefetch(double *, int32_t *, const double *, const int32_t *, uint32_t, int32_t,
+                                             unsigned, uint64_t, uint64_t) {}
+
 // Nodes are visited in chunks of kSelChunk consecutive ids per block iteration; warp w of the
 // block owns the kSelWarpNodes consecutive ids from base + w * kSelWarpNodes. The frontier
 // entries of a chunk are compacted with one atomic per chunk, so the frontier is id-sorted
@@ -286,8 +314,11 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
     // Per warp, the selected nodes of its range packed in id order: fluid, degree word and
     // offset within the range. After their visits the same slots hold the warp's frontier
     // entries (share, offset), again in id order.
-    __shared__ T s_f[8][kSelWarpNodes];
-    __shared__ int32_t s_info[8][kSelWarpNodes];
+    // With FP32 fluid the slots are double-buffered: the next chunk's F and degree words are
+    // copied in (cp.async) while the current chunk is visited.
+    constexpr bool kPre = sizeof(T) == 4;
+    __shared__ __align__(16) T s_f[kPre ? 2 : 1][8][kSelWarpNodes];
+    __shared__ __align__(16) int32_t s_info[kPre ? 2 : 1][8][kSelWarpNodes];
     __shared__ uint8_t s_off[8][kSelWarpNodes];
     __shared__ int s_wcount[8], s_wbase[8];
     __shared__ int s_chunk_base;
@@ -299,36 +330,59 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
     const bool cyc = ctl->schedule == DI_CYC || ctl->force_cyc;
     const bool plain_loops = ctl->plain_loops != 0;
     const float thr_f = (float)thr, d_f = (float)d;
-    const uint64_t keep = policy_evict_last();
+    const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
     const unsigned lane = lane_id(), lt = lanemask_lt();
     const int warp = threadIdx.x >> 5;
-    T *wf = s_f[warp];
-    int32_t *winfo = s_info[warp];
     uint8_t *woff = s_off[warp];
+    int cur = 0;
+    if (kPre) {
+        if (blockIdx.x * kSelChunk < (uint32_t)n)
+            sel_prefetch(s_f[0][warp], s_info[0][warp], F, out_info, blockIdx.x * kSelChunk + warp * kSelWarpNodes,
+                         n, lane, keep, stream);
+        cp_async_commit();
+    }
     T e_run = (T)0;      // dangling mass of this thread
     float ab_run = 0.f;  // fluid absorbed by this thread's visits (FP32: FP64 is slow here)
     unsigned long long pushed = 0;
     unsigned visited = 0;
-    for (int64_t base = (int64_t)blockIdx.x * kSelChunk; base < n; base += (int64_t)gridDim.x * kSelChunk) {
-        const int64_t wb = base + (int64_t)warp * kSelWarpNodes;
+    // 32-bit node arithmetic: ids stay below 2^31 and a stride below 2^31, so nothing wraps
+    for (uint32_t base = blockIdx.x * kSelChunk; base < (uint32_t)n; base += gridDim.x * kSelChunk) {
+        const uint32_t wb = base + warp * kSelWarpNodes;
+        T *wf = s_f[cur][warp];
+        int32_t *winfo = s_info[cur][warp];
         // F and the degree word of the warp's nodes: every load is issued before any is used
         T f[kSelItems];
         int32_t info[kSelItems];
+        if (kPre) {
+            const uint32_t nb = base + gridDim.x * kSelChunk;
+            if (nb < (uint32_t)n)
+                sel_prefetch(s_f[cur ^ 1][warp], s_info[cur ^ 1][warp], F, out_info, nb + warp * kSelWarpNodes, n,
+                             lane, keep, stream);
+            cp_async_commit();
+            cp_async_wait_all_but_newest();   // this chunk's copies are in
+            __syncwarp();
+        }
 #pragma unroll
         for (int j = 0; j < kSelItems; j++) {
-            const int64_t i = wb + j * 32 + lane;
+            const uint32_t i = wb + j * 32 + lane;
             f[j] = (T)0;
             info[j] = 0;
-            if (i < n) {
-                f[j] = ld_keep(F + i, keep);
-                info[j] = __ldcs(out_info + i);
+            if (i < (uint32_t)n) {
+                if (kPre) {
+                    f[j] = wf[j * 32 + lane];
+                    info[j] = winfo[j * 32 + lane];
+                } else {
+                    f[j] = ld_keep(F + i, keep);
+                    info[j] = __ldcs(out_info + i);
+                }
             }
         }
+        if (kPre) __syncwarp();   // all read before the packing below overwrites the slots
         // pack the selected nodes, so the visits below run on full warps
         int cnt = 0;
 #pragma unroll
         for (int j = 0; j < kSelItems; j++) {
-            const bool s = wb + j * 32 + lane < n && selects(f[j], info[j] & 0x7fffffff, cyc, thr, thr_f);
+            const bool s = wb + j * 32 + lane < (uint32_t)n && selects(f[j], info[j] & 0x7fffffff, cyc, thr, thr_f);
             const unsigned b = __ballot_sync(kFull, s);
             if (s) {
                 const int p = cnt + __popc(b & lt);
@@ -364,7 +418,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
 #pragma unroll
             for (int v = 0; v < kSelBatch<T>; v++) {
                 const int k = r0 + v * 32 + lane;
-                const int64_t i = wb + poff[v];
+                const uint32_t i = wb + poff[v];
                 bool light = false, heavy = false;
                 T share = (T)0;
                 const int32_t o = pinfo[v] & 0x7fffffff;
@@ -437,7 +491,8 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
             __stcs(front_id + cb + k, (int32_t)(wb + woff[k]));
             __stcs(front_s + cb + k, wf[k]);
         }
-        __syncwarp();   // the next chunk's packing reuses the slots
+        __syncwarp();   // the slots are reused: by the next chunk's copies or packing
+        if (kPre) cur ^= 1;
     }
     // warp sums in the fluid's type, block sums in FP64 by one thread
     const T e_w = warp_sum(e_run);
