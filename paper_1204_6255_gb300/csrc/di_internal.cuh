@@ -167,6 +167,8 @@ struct Workspace {
     cudaGraphExec_t sweep_exec = nullptr;   // reduce -> WHILE{select, push, reduce}
     cudaGraphExec_t pi_exec = nullptr;      // pull -> WHILE{pull}
     cudaStream_t capture_stream = nullptr;
+    cudaStream_t out_stream = nullptr;      // copies X out beside the last refinement
+    cudaEvent_t out_ready = nullptr, out_done = nullptr;
     SolveCtl *ctl_host = nullptr;           // pinned mirror for readback
     void reset_graphs();
     ~Workspace();

@@ -1172,6 +1172,9 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
 Workspace::~Workspace() {
     reset_graphs();
     if (capture_stream) cudaStreamDestroy(capture_stream);
+    if (out_stream) cudaStreamDestroy(out_stream);
+    if (out_ready) cudaEventDestroy(out_ready);
+    if (out_done) cudaEventDestroy(out_done);
     if (ctl_host) cudaFreeHost(ctl_host);
 }
 
@@ -1274,6 +1277,11 @@ static void ensure_workspace(di_graph *g) {
     ws.cdf_d = -1.0;
     ws.Xdf.ensure(sizeof(float2) * n);
     if (!ws.capture_stream) DI_CHECK_CUDA(cudaStreamCreateWithFlags(&ws.capture_stream, cudaStreamNonBlocking));
+    if (!ws.out_stream) {
+        DI_CHECK_CUDA(cudaStreamCreateWithFlags(&ws.out_stream, cudaStreamNonBlocking));
+        DI_CHECK_CUDA(cudaEventCreateWithFlags(&ws.out_ready, cudaEventDisableTiming));
+        DI_CHECK_CUDA(cudaEventCreateWithFlags(&ws.out_done, cudaEventDisableTiming));
+    }
     if (!ws.ctl_host) DI_CHECK_CUDA(cudaMallocHost(&ws.ctl_host, sizeof(SolveCtl)));
     ws.fluid = fl;
 }
@@ -1434,6 +1442,20 @@ static void check_common(di_graph *g, const double *B, double d, double tol, con
     DI_REQUIRE(tol > 0.0 && std::isfinite(tol), DI_ERR_INVALID_ARG, "tol must be positive and finite (got %g)", tol);
 }
 
+// X may be copied on a second stream when it is device memory or pinned host memory (a copy to
+// pageable memory would block the host thread before the refinement is launched).
+static bool async_copy_target(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged;
+}
+
+// A refined FP32 solve is split (write_ctl), so its first refinement is the halfway one.
+static bool ctl_split_expected(bool fp32, int refine) { return fp32 && refine; }
+
 template <class T>
 static void solve_impl(di_graph *g, const double *B, double d, double tol, int schedule, int max_sweeps, int refine,
                        int host_loop, int profile, int e_prediffuse, int plain_loops, double *X_out,
@@ -1511,11 +1533,28 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
         };
         run_sweeps();
         // every refinement round ends on an exact residual, so the reported one is exact
+        const size_t x_bytes = sizeof(double) * (size_t)g->n;
+        const bool x_async = async_copy_target(X_out);
+        bool x_copied = false;
         while (refine) {
+            // A refinement leaves H as it is. When this round is likely the last (not the halfway
+            // one of a split solve), X goes out on a second stream while the refinement runs; if
+            // more sweeps follow after all, they wait for that copy and X is copied again.
+            x_copied = x_async && (rounds > 0 || !ctl_split_expected(sizeof(T) == 4, refine));
+            if (x_copied) {
+                DI_CHECK_CUDA(cudaEventRecord(ws.out_ready, s));
+                DI_CHECK_CUDA(cudaStreamWaitEvent(ws.out_stream, ws.out_ready, 0));
+                from_device(X_out, ws.H.p, x_bytes, ws.out_stream);
+                DI_CHECK_CUDA(cudaEventRecord(ws.out_done, ws.out_stream));
+            }
             kc.run(KC_REFINE, g->n_heavy_in_chunks > 0 ? 3 : 2, [&] { launch_refine<T>(g, l, d, s); });
             read_ctl(g, s);
             rounds++;
             if (ws.ctl_host->status || ws.ctl_host->r <= tol || ws.ctl_host->sweeps >= max_sweeps || rounds >= 4) break;
+            if (x_copied) {
+                DI_CHECK_CUDA(cudaStreamWaitEvent(s, ws.out_done, 0));
+                x_copied = false;
+            }
             // Continuation sweeps start from the exact residual. After the halfway refinement of
             // a split solve the fluid's rounding since then is far below tol, so they aim just
             // under it; otherwise at half the tolerance, so the next exact residual lands below.
@@ -1533,7 +1572,10 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
             run_sweeps();
         }
         DI_CHECK_CUDA(cudaEventRecord(e1, s));
-        from_device(X_out, ws.H.p, sizeof(double) * (size_t)g->n, s);
+        if (x_copied)
+            DI_CHECK_CUDA(cudaStreamWaitEvent(s, ws.out_done, 0));
+        else
+            from_device(X_out, ws.H.p, x_bytes, s);
         if (F_out) {
             // the final fluid (after refinement: the exact residual, rounded to the fluid's type)
             double *stage = reinterpret_cast<double *>(ws.y0.p);
@@ -1543,6 +1585,7 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
         }
         read_ctl(g, s);
     } catch (...) {
+        if (ws.out_stream) cudaStreamSynchronize(ws.out_stream);   // no copy outlives the call
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         throw;
