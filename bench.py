@@ -464,7 +464,7 @@ def run_gpu(args):
     Bh = torch.full((n,), (1.0 - D) / n, dtype=torch.float64).pin_memory()
     Xh = torch.empty(n, dtype=torch.float64).pin_memory()
     e2e_ms, e2e_pushed = [], 0
-    for _ in range(max(1, min(args.steps, 5))):
+    for _ in range(max(1, min(args.steps, 20))):
         flush.fill_(1)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)

@@ -138,6 +138,9 @@ struct SolveCtl {
     unsigned long long front_total;  // frontier entries over all sweeps
     int32_t split;            // 1: the first reduction raises tol to sqrt(tol * r), the point of
                               //    the first refinement of a refined FP32 solve
+    int32_t halfway;          // 1: these sweeps end in that halfway refinement, whose exact
+                              //    residual replaces the fluid, so the stop test may use the
+                              //    tracked sum all the way down
 };
 
 // Fixed tuning of the single-RHS kernels.

@@ -4,23 +4,27 @@
 //   k_select    reads F and out[], picks the nodes of the sweep (DI-CYC: F_i != 0; DI-SOP:
 //               |F_i| > (r / L) * out_i with r = ||F||_1 taken at the sweep start), and performs
 //               the node part of every visit: F_i -> 0, transit (F_i * out_i / (out_i - d) for a
-//               loop node), H_i += transit, dangling mass e. Visited nodes with out-links become
-//               frontier entries (node id, per-link share d * transit / out_i), id-sorted within
-//               segments of kSelChunk nodes; nodes with more than kPushHeavy links go to a
-//               separate heavy list.
+//               loop node), H_i += transit, dangling mass e. Each warp packs the selected nodes
+//               of its 256-node range first, so the visits run on full warps; with FP32 fluid
+//               the next range's F and degrees arrive by cp.async meanwhile. Visited nodes with
+//               out-links become frontier entries (node id, per-link share d * transit / out_i),
+//               id-sorted within segments of kSelChunk nodes; nodes with more than kPushHeavy
+//               links go to a separate heavy list.
 //   k_push_win  (FP32 fluid) scatters the shares onto the out-neighbours j != i (the l_out loop
 //               of Section 2.5): a block takes a segment, adds the links that land near it into
 //               a shared-memory window and the links into hubs into a shared-memory hub cache,
-//               and sends the rest to F with L2 reductions; heavy nodes are spread over every
-//               warp of the grid. k_push does the same for FP64 fluid without the caches.
+//               and sends the rest to F with L2 reductions. Rows of kPushRow links or more go
+//               warp-wide; heavy nodes are spread over every warp of the grid. k_push does the
+//               same for FP64 fluid without the caches.
 //   k_reduce    r = sum |F_i| in FP64 (FP32 runs, warp shuffle, block, then the last block to
 //               finish sums the block partials in a fixed order), and the stop test r <= tol.
 //               It writes the WHILE-node condition, so the whole sweep loop runs from one CUDA
 //               graph launch.
 // All selected nodes diffuse concurrently; the result is a valid D-iteration in another
 // diffusion order, which reaches the same fixed point. Around the sweeps: k_e_visit (the E-level
-// pre-diffusion, one launch per level of E), the exact FP64 residual refinement, and resumed
-// solves from a given (H, F).
+// pre-diffusion, one launch per level of E), the exact FP64 residual refinement (an FP32 solve
+// refines halfway, on a log scale, between ||B||_1 and tol, and at the end), and resumed solves
+// from a given (H, F).
 //
 // Power iteration (Section 2.5 "PI", Jacobi on X = P.X + B) and the exact FP64 residual
 // F* = B + P.H - H both use k_pull: a warp takes 32 consecutive rows of the in-CSR; each lane
@@ -162,7 +166,10 @@ __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl,
             // between ||B||_1 and tol, where an exact residual replaces the fluid
             ctl->split = 0;
             const double mid = sqrt(ctl->tol * tot);
-            if (mid > ctl->tol) ctl->tol = mid;
+            if (mid > ctl->tol) {
+                ctl->tol = mid;
+                ctl->halfway = 1;
+            }
         }
         bool cont = ctl->status == 0 && tot > ctl->tol && ctl->sweeps < ctl->max_sweeps;
         ctl->done = cont ? 0 : 1;
@@ -521,8 +528,11 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
             const int sw = atomicAdd(&ctl->sweeps, 1) + 1;
             // this sweep's reduction takes r from the tracked sum while r is well above tol,
             // except every kTrackResync-th sweep (the FP32 atomics' rounding is not tracked);
-            // near the tolerance every reduction sums F, so the stop test is on the exact sum
-            ctl->reduce_est = (ctl->track && r > kTrackBand * ctl->tol && sw % kTrackResync != 0) ? 1 : 0;
+            // near the tolerance every reduction sums F, so the stop test is on the exact sum.
+            // Sweeps that end in the halfway refinement stop on the tracked sum all the way
+            // down: that refinement's exact residual replaces the fluid in any case.
+            ctl->reduce_est =
+                (ctl->track && (ctl->halfway || r > kTrackBand * ctl->tol) && sw % kTrackResync != 0) ? 1 : 0;
         }
     }
 }
@@ -1561,6 +1571,8 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
             const bool after_split = rounds == 1 && ws.ctl_host->tol > tol;
             const double aim = (after_split ? kAimAfterSplit : 0.5) * tol;
             DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->tol, &aim, sizeof(double), cudaMemcpyHostToDevice, s));
+            static const int32_t final_phase = 0;   // the next refinement may be the last
+            DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->halfway, &final_phase, sizeof(int32_t), cudaMemcpyHostToDevice, s));
             // An exact residual may have negative entries. After the halfway refinement they are
             // of the size of the rounding it replaced, a fraction of a percent of sum |F|, so the
             // tracked total (which follows sum F) stays on between exact reductions; otherwise
