@@ -9,7 +9,9 @@
 //      loop also ends as soon as every occupied slot has retired);
 //   3. retire: a slot whose ||F_c||_1 fell to its tolerance is finished; for tolerances below
 //      1e-6 the exact FP64 residual of the tile (B + P.H - H) is recomputed first and a slot
-//      whose exact residual is still above its tolerance keeps sweeping from it;
+//      whose exact residual is still above its tolerance keeps sweeping from it (such a
+//      request first stops halfway, on a log scale, between ||B||_1 and its tolerance, so that
+//      one exact residual clears the FP32 rounding early);
 //   4. copy each finished column's history out and zero the column, so the slot is clean for the
 //      next request; the copy to pinned host memory is followed on the stream by a host function
 //      that marks the request done, so the worker never waits for the copy.
@@ -58,6 +60,9 @@ __global__ void ks_col_retire(float *F, double *H, double *Bn, int32_t n, int c,
     }
 }
 
+// Requests with a tolerance below this get an exact FP64 residual before they retire.
+constexpr double kServeExactTol = 1e-6;
+
 struct Request {
     int64_t id = 0;
     int graph = 0;
@@ -66,6 +71,7 @@ struct Request {
     double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
     int slot = -1;
     int admit_sweep = 0;
+    bool halfway = false;           // sweeping towards the halfway refinement point
     double *X = nullptr;            // pinned host copy of the history (from the worker's pool)
     di_status status = DI_OK;
     int sweeps = 0;
@@ -218,6 +224,12 @@ void Worker::step_loop() {
                 const int c = r->slot;
                 hc.active[c] = 1;
                 hc.tol[c] = r->tol;
+                // a tight request (refined at retirement) first stops halfway, on a log scale,
+                // between ||B||_1 = 1 - d and its tol, where an exact residual replaces its
+                // fluid before the FP32 rounding grows comparable to tol
+                const double mid = sqrt(r->tol * (1.0 - srv->d));
+                r->halfway = r->tol < kServeExactTol && mid > r->tol;
+                if (r->halfway) hc.tol[c] = mid;
                 hc.r[c] = 0.0;
                 hc.e[c] = 0.0;
                 hc.retire_sweep[c] = -1;
@@ -243,7 +255,7 @@ void Worker::step_loop() {
             const bool capped = hc.sweeps - slot[c]->admit_sweep >= srv->max_request_sweeps;
             if (!hc.active[c] || capped) {
                 retired.push_back(c);
-                if (slot[c]->tol < 1e-6) exact_mask |= 1u << c;
+                if (slot[c]->tol < kServeExactTol) exact_mask |= 1u << c;
             }
         }
         if (retired.empty()) continue;
@@ -258,7 +270,8 @@ void Worker::step_loop() {
             const bool capped = hc.sweeps - r->admit_sweep >= srv->max_request_sweeps;
             if (hc.r[c] > r->tol && !capped) {
                 hc.active[c] = 1;            // keeps sweeping from the exact residual
-                hc.tol[c] = 0.5 * r->tol;
+                hc.tol[c] = (r->halfway ? kAimAfterSplit : 0.5) * r->tol;
+                r->halfway = false;
                 continue;
             }
             // 4. the column's history goes to a pinned buffer of the request, the column is zeroed
