@@ -152,6 +152,22 @@ def push_traffic():
         return None, None
 
 
+def host_cpu():
+    """The host the oracle ran on: architecture, logical cores, and the CPU model when the
+    kernel reports one."""
+    import platform
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":", 1)[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"machine": platform.machine(), "nproc": os.cpu_count(), "model": model}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -204,7 +220,8 @@ def run_reference(args):
                    "step": "one oracle DI-SOP cycle from F=B (bounded sample of the solve)", "fluid": "f64",
                    "history": "f64"},
         "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                         "sample": "one sequential DI-SOP cycle per step on the full 10M-node graph"},
+                         "sample": "one sequential DI-SOP cycle per step on the full 10M-node graph",
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -536,7 +553,8 @@ def run_gpu(args):
         cp, csec, ccyc, _ = oracle_sample(n, src, dst, D, cyc)
         cpu = {"value": cp / csec / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                "sample": f"first {ccyc} sequential DI-SOP cycles of the oracle on the same 10M-node graph "
-                         f"({cp} pushed links in {csec:.1f} s; oracle build excluded)"}
+                         f"({cp} pushed links in {csec:.1f} s; oracle build excluded)",
+               "host": host_cpu()}
 
     if rank != 0:
         if dist:
