@@ -77,7 +77,10 @@ typedef struct {
     int32_t max_sweeps;  /* cap on sweeps; <= 0: 100000; clamped to 1000000 */
     int32_t refine;      /* 0: default (on for F32, off for F64); 1: on; -1: off. Refinement
                             recomputes the exact FP64 residual F* = B + P.H - H and continues
-                            sweeping from it until ||F*||_1 <= tol (at most 4 rounds). */
+                            sweeping from it until ||F*||_1 <= tol (at most 4 rounds). An FP32
+                            solve refines first where ||F||_1 reaches sqrt(tol * ||F_0||_1),
+                            before the FP32 rounding has grown comparable to tol, then at the
+                            end. */
     int32_t host_loop;   /* 1: drive sweeps from the host (one sync per sweep) instead of a CUDA
                             graph WHILE node; default 0 */
     int32_t rhs_tile;    /* batched solves: RHS per tile, 4, 8, 16 or 32 (0: autotuned per graph) */
