@@ -156,15 +156,19 @@ def host_cpu():
     """The host the oracle ran on: architecture, logical cores, and the CPU model when the
     kernel reports one."""
     import platform
-    model = None
+    model, arm = None, {}
     try:
         for line in open("/proc/cpuinfo"):
-            key = line.split(":", 1)[0].strip().lower()
-            if key in ("model name", "cpu model", "hardware"):
-                model = line.split(":", 1)[1].strip()
-                break
+            key, _, val = line.partition(":")
+            key = key.strip().lower()
+            if key in ("model name", "cpu model") and model is None:
+                model = val.strip()
+            elif key in ("cpu implementer", "cpu part") and key not in arm:
+                arm[key] = val.strip()   # Arm cores report these instead of a model name
     except OSError:
         pass
+    if model is None and arm:
+        model = "implementer {} part {}".format(arm.get("cpu implementer", "?"), arm.get("cpu part", "?"))
     return {"machine": platform.machine(), "nproc": os.cpu_count(), "model": model}
 
 
