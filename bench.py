@@ -152,13 +152,13 @@ def push_traffic():
         return None, None
 
 
-def host_cpu():
+def host_cpu(cpuinfo="/proc/cpuinfo"):
     """The host the oracle ran on: architecture, logical cores, and the CPU model when the
     kernel reports one."""
     import platform
     model, arm = None, {}
     try:
-        for line in open("/proc/cpuinfo"):
+        for line in open(cpuinfo):
             key, _, val = line.partition(":")
             key = key.strip().lower()
             if key in ("model name", "cpu model") and model is None:
