@@ -66,6 +66,8 @@ def _load():
                                       ctypes.c_void_p, ctypes.c_void_p]
         lib.gen_u64.restype = None
         lib.gen_u64.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p]
+        lib.gen_draw.restype = None
+        lib.gen_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p]
         _lib = lib
     return _lib
 
@@ -170,6 +172,15 @@ def u64(seed: int, purpose: int, count: int) -> np.ndarray:
     lib = _load()
     out = np.empty(count, dtype=np.uint64)
     lib.gen_u64(seed & 0xFFFFFFFFFFFFFFFF, purpose, count, out.ctypes.data)
+    return out
+
+
+def draw(key: int, first: int, count: int) -> np.ndarray:
+    """Raw outputs first .. first + count - 1 of the SplitMix64 stream whose state starts at
+    `key` (the generator's counter-based draw)."""
+    lib = _load()
+    out = np.empty(count, dtype=np.uint64)
+    lib.gen_draw(key & 0xFFFFFFFFFFFFFFFF, first & 0xFFFFFFFFFFFFFFFF, count, out.ctypes.data)
     return out
 
 

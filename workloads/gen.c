@@ -300,6 +300,12 @@ int64_t gen_seed_sets(int64_t n, int32_t k, int32_t max_size, uint64_t seed,
 }
 
 /* Uniform u64 stream for tests that need extra seeded integers (e.g. edge permutations). */
+/* raw stream outputs draw(key, first + i), for checking the generator against SplitMix64's
+   published sequence */
+void gen_draw(uint64_t key, uint64_t first, int64_t count, uint64_t *out) {
+    for (int64_t i = 0; i < count; i++) out[i] = draw(key, first + (uint64_t)i);
+}
+
 void gen_u64(uint64_t seed, uint64_t purpose, int64_t count, uint64_t *out) {
     uint64_t k = purpose_key(seed, 100 + purpose);
     for (int64_t i = 0; i < count; i++) out[i] = draw(k, (uint64_t)i);
