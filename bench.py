@@ -2,7 +2,7 @@
 """Benchmark of the GB300 D-iteration.
 
 One step = one DI-SOP solve (Section 2.3) of X = P.X + B to ||F||_1 <= 1e-8 on the resident
-10M-node / ~141M-link synthetic web graph (FP32 fluid, FP64 history and residual, exact FP64
+10M-node / ~150M-link synthetic web graph (FP32 fluid, FP64 history and residual, exact FP64
 refinement), B = (1-d)/N, d = 0.85. The metric is GTEPS = pushed links / solve time (the graph
 build is timed apart, like the paper's "Init"). Inputs (CSR ~1.8 GB) are larger than L2 and L2 is
 flushed between steps anyway.
@@ -44,6 +44,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     p.add_argument("--no-legs", action="store_true", help="skip the extra legs (DI-CYC, PI, d=0.95)")
+    p.add_argument("--legs", default="all",
+                   help="comma list of extra legs to run: solvers, small_graphs, transposed, e_dominated, "
+                        "ppr_batch, serving")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--one-solve", action="store_true",
                    help="build the graph, run one DI-SOP solve and exit (the command the ncu captures profile)")
@@ -256,8 +259,9 @@ def ppr_batch_leg(di, workloads, torch):
     _, res, info = di.di_ppr_batch(g, off_d, seeds_d, d, tol, X_out=X)
     torch.cuda.synchronize()
     batch_s = time.perf_counter() - t
-    # per-request plain solves (single right-hand side, FP32 fluid + refinement), a sample
-    sample = 48
+    # per-request plain solves (single right-hand side, FP32 fluid + refinement) of the same
+    # 256 requests
+    sample = k
     B = torch.zeros(n, dtype=torch.float64, device="cuda")
     Xs = torch.empty(n, dtype=torch.float64, device="cuda")
     for r in range(2):                                   # warm-up of the same path
@@ -280,6 +284,44 @@ def ppr_batch_leg(di, workloads, torch):
             "batched_qps": k / batch_s, "batched_ms": 1e3 * batch_s,
             "per_request_qps": sample / solo_s, "per_request_p50_ms": pct(lat, 50), "per_request_p99_ms": pct(lat, 99),
             "speedup": (k / batch_s) / (sample / solo_s), "max_residual": float(np.max(res))}
+
+
+def small_graph_leg(di, workloads, torch, name, reps=7):
+    """The paper's four solvers on a smaller workload, median of `reps` solves after warm-ups,
+    inputs resident: pa_n10k (10k nodes, everything in FP64, tol 1e-10) and web_n1m (1M nodes,
+    FP32 fluid with the exact FP64 refinement, tol 1e-8)."""
+    import statistics
+    cfg = workloads.WORKLOADS[name]
+    n, src, dst = workloads.generate(cfg["spec"])
+    g = di.di_graph_create(n, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda())
+    d, tol = cfg["d"], cfg["tol"]
+    fp64 = cfg["fluid"] == "f64"
+    fluid = di.DI_FLUID_F64 if fp64 else di.DI_FLUID_F32
+    B = torch.full((n,), (1.0 - d) / n, dtype=torch.float64, device="cuda")
+    X = torch.empty(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    runs = {
+        "di_sop": lambda: di.di_solve_ex(g, B, d, tol, schedule=di.DI_SOP, fluid=fluid, max_sweeps=MAX_SWEEPS, X_out=X)[1],
+        "di_cyc": lambda: di.di_solve_ex(g, B, d, tol, schedule=di.DI_CYC, fluid=fluid, max_sweeps=MAX_SWEEPS, X_out=X)[1],
+        "pi": lambda: di.di_power_iter_ex(g, B, d, tol, fluid=fluid, max_iters=MAX_SWEEPS, X_out=X)[1],
+        "pi_push": lambda: di.di_power_iter_push(g, B, d, tol, max_iters=MAX_SWEEPS, fluid=fluid, X_out=X)[1],
+    }
+    out = {"graph": {k: g.stats[k] for k in ("n_nodes", "L", "D", "E", "O", "max_in", "max_out")}, "d": d, "tol": tol,
+           "fluid": cfg["fluid"], "median_of": reps}
+    for label, fn in runs.items():
+        fn()
+        fn()
+        ms, inf = [], None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            inf = fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        out[label] = {"ms_to_residual": statistics.median(ms), "iterations_or_sweeps": inf["sweeps"],
+                      "pushed_per_L": inf["pushed_edges"] / g.stats["L"], "residual_l1": inf["residual_l1"]}
+    return out
 
 
 def transposed_leg(di, workloads, torch, flush, name="web_n10m_t"):
@@ -319,12 +361,18 @@ def transposed_leg(di, workloads, torch, flush, name="web_n10m_t"):
     return out
 
 
-def serving_leg(di, workloads, torch, rate_qps=600.0, n_req=300, slots=16, sweeps_per_step=8, plain=True):
-    """Poisson stream of personalised PageRank requests over four resident graphs (N = 100k,
-    500k, 2M, 5M), tolerances 1e-4/1e-6/1e-8, seed sets of 1..1000 nodes: the continuously
-    batched server against the same stream served by plain single-RHS solves in arrival order.
-    Latency runs from arrival to the history in host memory on both sides."""
-    import threading
+def serving_leg(di, workloads, torch, n_req=1000, fracs=(0.25, 0.5, 0.75, 1.0, 1.25), slots=16,
+                sweeps_per_step=8, tile_min_queue=0):
+    """Poisson streams of personalised PageRank requests over four resident graphs (N = 100k,
+    500k, 2M, 5M), tolerances 1e-4/1e-6/1e-8, seed sets of 1..1000 nodes, at arrival rates of
+    25% to 125% of the plain path's capacity: the continuously batched server against
+    per-request plain solves in arrival order (one at a time on the same GPU). Latency runs from
+    arrival to the history in host memory on both sides.
+
+    The plain path is a single FIFO server whose service times do not depend on the arrivals, so
+    each request's plain service time (seed upload, solve, copy-out) is measured once, and its
+    latency at every rate follows from the FIFO recursion finish = max(arrival, previous finish)
+    + service. The served side runs in real time at each rate."""
     import numpy as np
     cfg = workloads.WORKLOADS["serve_4g"]
     d = cfg["d"]
@@ -333,8 +381,6 @@ def serving_leg(di, workloads, torch, rate_qps=600.0, n_req=300, slots=16, sweep
         n, src, dst = workloads.generate(spec)
         graphs.append(di.di_graph_create(n, src, dst))
     u = workloads.uniform(4242, 1, 3 * n_req)
-    gaps = -np.log(1.0 - u[:n_req]) / rate_qps                  # Poisson arrivals
-    arrive = np.cumsum(gaps)
     gsel = (u[n_req:2 * n_req] * len(graphs)).astype(int)
     tsel = (u[2 * n_req:] * 3).astype(int)
     reqs = []
@@ -343,48 +389,12 @@ def serving_leg(di, workloads, torch, rate_qps=600.0, n_req=300, slots=16, sweep
         off, seeds = workloads.seed_sets(g.n, 1, cfg["max_seeds"], seed=7000 + i)
         reqs.append((gsel[i], seeds, cfg["tols"][tsel[i]]))
 
-    # served
-    srv = di.di_server_create(graphs, d=d, slots=slots, sweeps_per_step=sweeps_per_step)
-    for gi in range(len(graphs)):                                   # warm every worker
-        di.di_server_wait(srv, di.di_server_submit(srv, gi, np.array([0], np.int32), 1e-4), timeout_ms=60000)
-    ids = [None] * n_req
-    t0 = time.perf_counter()
-    for i, (gi, seeds, tol) in enumerate(reqs):
-        delay = arrive[i] - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        ids[i] = di.di_server_submit(srv, int(gi), seeds, tol)
-    lat, worst = [], 0.0
-    for i in range(n_req):
-        _, info = di.di_server_wait(srv, ids[i], timeout_ms=600000)
-        lat.append(info["total_ms"])
-        worst = max(worst, info["residual_l1"] / reqs[i][2])
-    served_s = time.perf_counter() - t0
-    srv.close()
-    out = {"requests": n_req, "arrival_qps": rate_qps, "graphs": [g.n for g in graphs], "slots": slots,
-           "sweeps_per_step": sweeps_per_step, "served_qps": n_req / served_s, "served_p50_ms": pct(lat, 50),
-           "served_p99_ms": pct(lat, 99), "worst_residual_over_tol": worst}
-    if not plain:
-        return out
-
-    # per-request plain solves in arrival order (one request at a time on the same GPU); like a
-    # served request, a request is done when its history is in (pinned) host memory
+    # plain service times, one request at a time (done when its history is in pinned host memory)
     Bs = [torch.zeros(g.n, dtype=torch.float64, device="cuda") for g in graphs]
     Xs = [torch.empty(g.n, dtype=torch.float64, device="cuda") for g in graphs]
     Xh = [torch.empty(g.n, dtype=torch.float64).pin_memory() for g in graphs]
-    for gi, g in enumerate(graphs):                                 # warm-up of the same path
-        B = Bs[gi]
-        B.zero_()
-        sd = torch.arange(0, 8, dtype=torch.int64, device="cuda")
-        B.index_add_(0, sd, torch.full((8,), (1 - d) / 8, dtype=torch.float64, device="cuda"))
-        di.di_solve(g, B, d, 1e-4, di.DI_SOP, MAX_SWEEPS, X_out=Xs[gi])
-    torch.cuda.synchronize()
-    lat_p = []
-    t0 = time.perf_counter()
-    for i, (gi, seeds, tol) in enumerate(reqs):
-        now = time.perf_counter() - t0
-        if now < arrive[i]:
-            time.sleep(arrive[i] - now)
+
+    def plain(gi, seeds, tol):
         B = Bs[gi]
         B.zero_()
         sd = torch.from_numpy(seeds.astype(np.int64)).cuda()
@@ -392,10 +402,61 @@ def serving_leg(di, workloads, torch, rate_qps=600.0, n_req=300, slots=16, sweep
         di.di_solve(graphs[gi], B, d, tol, di.DI_SOP, MAX_SWEEPS, X_out=Xs[gi])
         Xh[gi].copy_(Xs[gi], non_blocking=True)
         torch.cuda.current_stream().synchronize()
-        lat_p.append(1e3 * ((time.perf_counter() - t0) - arrive[i]))
-    plain_s = time.perf_counter() - t0
-    out.update({"plain_qps": n_req / plain_s, "plain_p50_ms": pct(lat_p, 50), "plain_p99_ms": pct(lat_p, 99)})
-    return out
+
+    for gi, g in enumerate(graphs):                                 # warm-up of the same path
+        plain(gi, np.arange(8, dtype=np.int32), 1e-4)
+    service = np.empty(n_req)
+    for i, (gi, seeds, tol) in enumerate(reqs):
+        t = time.perf_counter()
+        plain(gi, seeds, tol)
+        service[i] = time.perf_counter() - t
+    capacity = n_req / service.sum()
+
+    srv = di.di_server_create(graphs, d=d, slots=slots, sweeps_per_step=sweeps_per_step,
+                              tile_min_queue=tile_min_queue)
+    for gi in range(len(graphs)):                                   # warm every worker
+        di.di_server_wait(srv, di.di_server_submit(srv, gi, np.array([0], np.int32), 1e-4), timeout_ms=60000)
+    points = []
+    for k, frac in enumerate(fracs):
+        rate = frac * capacity
+        gaps = -np.log(1.0 - workloads.uniform(4300 + k, 1, n_req)) / rate      # Poisson arrivals
+        arrive = np.cumsum(gaps)
+        # plain: FIFO recursion over the measured service times
+        finish, lat_p = 0.0, np.empty(n_req)
+        for i in range(n_req):
+            finish = max(arrive[i], finish) + service[i]
+            lat_p[i] = 1e3 * (finish - arrive[i])
+        plain_qps = n_req / finish
+        # served, in real time
+        ids = [None] * n_req
+        t0 = time.perf_counter()
+        for i, (gi, seeds, tol) in enumerate(reqs):
+            delay = arrive[i] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids[i] = di.di_server_submit(srv, int(gi), seeds, tol)
+        lat, worst, lone, by_graph = [], 0.0, 0, {}
+        for i in range(n_req):
+            _, info = di.di_server_wait(srv, ids[i], timeout_ms=600000)
+            lat.append(info["total_ms"])
+            lone += info["slot"] < 0
+            by_graph.setdefault(int(reqs[i][0]), []).append(info["total_ms"])
+            worst = max(worst, info["residual_l1"] / reqs[i][2])
+        served_s = time.perf_counter() - t0
+        plain_by_graph = {}
+        for i in range(n_req):
+            plain_by_graph.setdefault(int(reqs[i][0]), []).append(lat_p[i])
+        points.append({"load": frac, "arrival_qps": rate, "served_qps": n_req / served_s,
+                       "served_p50_ms": pct(lat, 50), "served_p99_ms": pct(lat, 99), "plain_qps": plain_qps,
+                       "plain_p50_ms": pct(list(lat_p), 50), "plain_p99_ms": pct(list(lat_p), 99),
+                       "served_single_path": lone / n_req,
+                       "served_p99_ms_by_graph": [pct(by_graph.get(k, []), 99) for k in range(len(graphs))],
+                       "plain_p99_ms_by_graph": [pct(plain_by_graph.get(k, []), 99) for k in range(len(graphs))],
+                       "worst_residual_over_tol": worst})
+    srv.close()
+    return {"requests_per_point": n_req, "graphs": [g.n for g in graphs], "slots": slots,
+            "sweeps_per_step": sweeps_per_step, "tile_min_queue": tile_min_queue or 4, "plain_capacity_qps": capacity,
+            "plain_service_ms_mean": 1e3 * float(service.mean()), "points": points}
 
 
 # ------------------------------------------------------------------------------------------
@@ -510,42 +571,61 @@ def run_gpu(args):
     traffic, traffic_src = push_traffic()
 
     legs = {}
-    if not args.no_legs:
-        for name, kw in (("di_cyc", dict(schedule=di.DI_CYC)), ("di_sop_d095", dict(d=0.95, Bx=torch.full(
-                (n,), (1.0 - 0.95) / n, dtype=torch.float64, device=dev))), ("di_sop_e_prediffused",
-                                                                             dict(e_prediffuse=1))):
+    want = set(["solvers", "small_graphs", "transposed", "e_dominated", "ppr_batch", "serving"] if args.legs == "all"
+               else args.legs.split(","))
+    if args.no_legs:
+        want = set()
+    def median_of(fn, reps=5):
+        """Median device time of `reps` runs of fn (after one warm-up), L2 flushed before each."""
+        fn()
+        times, inf = [], None
+        for _ in range(reps):
             flush.fill_(1)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            inf = step(**kw)
+            inf = fn()
             b.record(stream)
             b.synchronize()
-            ms = a.elapsed_time(b)
+            times.append(a.elapsed_time(b))
+        return statistics.median(times), inf
+
+    if "solvers" in want:
+        B95 = torch.full((n,), (1.0 - 0.95) / n, dtype=torch.float64, device=dev)
+        for name, kw in (("di_cyc", dict(schedule=di.DI_CYC)), ("di_sop_d095", dict(d=0.95, Bx=B95)),
+                         ("di_sop_e_prediffused", dict(e_prediffuse=1))):
+            ms, inf = median_of(lambda: step(**kw))
             legs[name] = {"ms_to_residual": ms, "GTEPS": inf["pushed_edges"] / (ms * 1e-3) / 1e9,
                           "sweeps": inf["sweeps"], "pushed_per_L": inf["pushed_edges"] / st["L"],
-                          "residual_l1": inf["residual_l1"]}
-        flush.fill_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        _, pinf = di.di_power_iter(g, B, D, TOL, max_iters=MAX_SWEEPS, X_out=X)
-        b.record(stream)
-        b.synchronize()
-        ms = a.elapsed_time(b)
+                          "residual_l1": inf["residual_l1"], "median_of": 5}
+        ms, pinf = median_of(lambda: di.di_power_iter(g, B, D, TOL, max_iters=MAX_SWEEPS, X_out=X)[1])
         legs["pi"] = {"ms_to_residual": ms, "GTEPS": pinf["pushed_edges"] / (ms * 1e-3) / 1e9,
-                      "iterations": pinf["sweeps"], "residual_l1": pinf["residual_l1"]}
-        flush.fill_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        _, qinf = di.di_power_iter_push(g, B, D, TOL, max_iters=MAX_SWEEPS, X_out=X)
-        b.record(stream)
-        b.synchronize()
-        ms = a.elapsed_time(b)
+                      "iterations": pinf["sweeps"], "refine_rounds": pinf["refine_rounds"],
+                      "residual_l1": pinf["residual_l1"], "median_of": 5,
+                      "form": "FP32 increments, FP64 X, exact FP64-certified residual"}
+        ms, qinf = median_of(lambda: di.di_power_iter_push(g, B, D, TOL, max_iters=MAX_SWEEPS, X_out=X)[1])
         legs["pi_push"] = {"ms_to_residual": ms, "GTEPS": qinf["pushed_edges"] / (ms * 1e-3) / 1e9,
-                           "iterations": qinf["sweeps"], "residual_l1": qinf["residual_l1"]}
+                           "iterations": qinf["sweeps"], "residual_l1": qinf["residual_l1"], "median_of": 5}
+        # the pull's roofline: per pass 4 B index + 4 B FP32 increment gathered per link; per row
+        # 8 B row start, 8 B FP64 X read and 8 B written, 4 B increment written, 4 B d/out
+        pprof = di.di_power_iter_ex(g, B, D, TOL, max_iters=MAX_SWEEPS, profile=1, X_out=X)[1]
+        if pprof["push_launches"]:
+            pull_ms = pprof["push_ms"] / pprof["push_launches"]
+            pull_bytes = 8.0 * st["L"] + 32.0 * n
+            peak, peak_kind = peaks()
+            legs["pi"]["roofline"] = {"kernel": "k_pull<PULL_INC>", "bound": "hbm", "bytes_per_launch": pull_bytes,
+                                      "ms_per_launch": pull_ms, "achieved": pull_bytes / (pull_ms * 1e-3) / 1e9,
+                                      "peak": peak, "unit": "GB/s",
+                                      "frac": pull_bytes / (pull_ms * 1e-3) / 1e9 / peak, "peak_kind": peak_kind}
+    if "small_graphs" in want:
+        legs["pa_n10k"] = small_graph_leg(di, workloads, torch, "pa_n10k")
+        legs["web_n1m"] = small_graph_leg(di, workloads, torch, "web_n1m")
+    if "transposed" in want:
         legs["transposed"] = transposed_leg(di, workloads, torch, flush)
+    if "e_dominated" in want:
         legs["e_dominated"] = transposed_leg(di, workloads, torch, flush, name="web_n10m_e")
-    if not args.no_legs:
+    if "ppr_batch" in want:
         legs["ppr_batch"] = ppr_batch_leg(di, workloads, torch)
+    if "serving" in want:
         legs["serving"] = serving_leg(di, workloads, torch)
     legs["di_sop"] = {"ms_to_residual": statistics.median(step_ms), "sweeps": infos[-1]["sweeps"],
                       "pushed_per_L": infos[-1]["pushed_edges"] / st["L"], "refine_rounds": infos[-1]["refine_rounds"],

@@ -11,7 +11,9 @@
  * Conventions shared by every entry point
  *   - Pointers: every array argument may be host memory (pageable or pinned) or device memory
  *     of the graph's GPU; the library asks the CUDA runtime which one it is. The caller owns
- *     every array it passes and keeps it alive for the duration of the call.
+ *     every array it passes and keeps it alive for the duration of the call. A graph handle owns
+ *     its graph arrays; solve scratch is either allocated by the library on first use or laid
+ *     out in a workspace the caller attaches (di_workspace_size, di_graph_set_workspace).
  *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *     All device work of a call is ordered on that stream. Every call returns only after its
  *     results are written (it synchronises the stream before returning).
@@ -91,6 +93,15 @@ typedef struct {
                             level order (Section 2.4: E converges in finitely many steps). Each
                             node of E then holds its exact value, up to rounding, and receives no
                             fluid afterwards, so no sweep selects it again. Default 0. */
+    int32_t r_refresh;   /* single-RHS DI-SOP: a sweep selects in this many consecutive parts of
+                            the node range (0 or 1: one part), and r = ||F||_1 is taken again
+                            before each part, so a part's threshold sees the fluid that the parts
+                            before it pushed (Section 2.3 takes r_n' once per cycle; this is the
+                            variant that refreshes it within the cycle). At most 16. */
+    int32_t exact_r;     /* single-RHS FP32 solves: 1 takes r from a sum of |F| after every sweep.
+                            Default 0: while r is far above tol and the fluid is nonnegative, r is
+                            tracked as the sum before the sweep less the fluid its visits absorbed,
+                            with an exact sum every 8th sweep and at every sweep near tol. */
 } di_solve_opts;
 
 /* Per-solve report. */
@@ -184,11 +195,29 @@ di_status di_solve_ex(di_graph *g, const double *B, double d, double tol, const 
  * di_power_iter — power iteration PI (Section 2.3, Section 2.5 "PI": row vectors, i.e. a pull
  * over the in-links), applied to X = P.X + B as a Jacobi iteration: X_0 = 0,
  * X_(k+1) = B + P.X_k, stopping when ||X_(k+1) - X_k||_1 <= tol or after max_iters (<= 0:
- * 100000) iterations. FP64 throughout. X_out double[n]; residual_out and info nullable.
- * Errors as di_solve.
+ * 100000) iterations. This is di_power_iter_ex with default options: the increments
+ * X_(k+1) - X_k = P (X_k - X_(k-1)) in FP32, X in FP64, and the exact
+ * next increment B + P.X - X (double-float link sums, FP64 B and X) taken halfway and at the
+ * end; the reported residual is that exact ||X_(k+1) - X_k||_1 of the returned X.
+ * X_out double[n]; residual_out and info nullable. Errors as di_solve.
  */
 di_status di_power_iter(di_graph *g, const double *B, double d, double tol, int32_t max_iters,
                         double *X_out, double *residual_out, di_solve_info *info, void *stream);
+
+/*
+ * di_power_iter_ex — di_power_iter with options (opts may be NULL):
+ *   fluid      DI_FLUID_F32 (default): FP32 increments, X in FP64, exact FP64
+ *              certification as described for di_power_iter.
+ *              DI_FLUID_F64: FP64 throughout (y_j = d X_j / out_j, the link sums and X in FP64);
+ *              the iterates and the iteration count are those of an FP64 Jacobi iteration.
+ *   max_sweeps iteration cap (<= 0: 100000).   refine   -1: no exact certification (FP32
+ *              increments only; the residual is the last FP32 increment's norm).
+ *   profile    1: iterations driven from the host with CUDA events around every kernel
+ *              (push_ms: the pull kernel, select_ms: the heavy rows' chunk sums).
+ * Other fields are ignored. Errors as di_solve.
+ */
+di_status di_power_iter_ex(di_graph *g, const double *B, double d, double tol, const di_solve_opts *opts,
+                           double *X_out, double *residual_out, di_solve_info *info, void *stream);
 
 /*
  * di_solve_resume — D-iteration from a given state (H0, F0) instead of (0, B) (Section 2.5: the
@@ -263,6 +292,78 @@ di_status di_ppr_batch(di_graph *g, int32_t k, const int64_t *seed_offsets, cons
                        double *res_out, di_solve_info *info, void *stream);
 
 /* ------------------------------------------------------------------------------------------
+ * Caller-owned scratch ("workspace"). By default a graph's first solve allocates the scratch
+ * it keeps for later solves (cudaMalloc). A caller whose own allocator must own all device
+ * memory (PyTorch's caching allocator, a serving runtime's pool) asks for the size, allocates
+ * the buffer itself and attaches it; from then on the solves of that kind lay their scratch out
+ * in it and call no allocator. The paper has no counterpart: this is the ownership rule of the
+ * C boundary.
+ * ------------------------------------------------------------------------------------------ */
+typedef enum {
+    DI_WS_SOLVE = 0,   /* di_solve, di_solve_ex, di_solve_resume, di_power_iter,
+                          di_power_iter_push (param: the fluid, DI_FLUID_F32 or DI_FLUID_F64;
+                          power iteration uses the DI_FLUID_F32 size) */
+    DI_WS_BATCH = 1    /* di_solve_batch, di_ppr_batch (param: the widest tile, 4, 8, 16 or 32
+                          columns; 0 means 32). With a workspace for fewer than 32 columns the
+                          autotuner only tries the widths it holds. */
+} di_workspace_kind;
+
+/*
+ * di_workspace_size — bytes of device scratch the solves of `kind` need on graph g, for the
+ * given param (see di_workspace_kind). The size grows with the graph (about 70 bytes per node
+ * for DI_WS_SOLVE with FP32 fluid; about 44 * param bytes per node for DI_WS_BATCH).
+ * Errors: DI_ERR_INVALID_ARG (NULL, unknown kind or param).
+ */
+di_status di_workspace_size(const di_graph *g, int32_t kind, int32_t param, int64_t *bytes);
+
+/*
+ * di_graph_set_workspace — attaches `bytes` of the caller's device memory at `workspace` (256-byte
+ * aligned, on the graph's GPU) as the scratch of the solves of `kind`, or detaches it (workspace
+ * NULL: later solves allocate their own again). Scratch the library had allocated for that kind
+ * is freed at once. The caller keeps the memory alive and leaves it alone until it detaches it or
+ * destroys the graph; the library keeps solver state there between calls, so two graphs must not
+ * share one workspace. A solve that needs more than the attached size fails with
+ * DI_ERR_INVALID_ARG (see di_workspace_size) and allocates nothing. The call waits for the device
+ * to finish earlier work (cudaDeviceSynchronize), since that work may still use the old scratch.
+ * Errors: DI_ERR_INVALID_ARG (NULL graph, kind, alignment, not device memory of the graph's
+ * GPU), DI_ERR_BUSY (a solve on the graph is running), DI_ERR_CUDA.
+ */
+di_status di_graph_set_workspace(di_graph *g, int32_t kind, void *workspace, int64_t bytes);
+
+/* ------------------------------------------------------------------------------------------
+ * Autotuning of the push (the paper has no counterpart: it chooses how the GPU splits work).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int32_t push_row;          /* single right-hand side: rows of at least this many links are
+                                  pushed one at a time by a whole warp */
+    int32_t heavy_cut;         /* nodes with more links than this are pushed in chunks spread over
+                                  all warps of the grid ... */
+    int32_t heavy_chunk;       /* ... of this many links each (so out / heavy_chunk warps share the
+                                  row) */
+    int32_t rhs_tile;          /* batched: columns per tile (0 before the first batched call) */
+    int32_t batch_heavy_cut;   /* batched push: the same split for tiles */
+    int32_t batch_heavy_chunk;
+    double single_probe_ms;    /* device time of the chosen single-RHS probe solve (ms) */
+    double batch_rate;         /* column-link updates per second of the chosen batched setting */
+} di_tuning;
+
+/*
+ * di_autotune — times short probe solves on graph g (damping d, uniform right-hand sides) and
+ * keeps the fastest push split for later solves on g. what: bit 0 tunes the single right-hand
+ * side push (row cut-off, heavy cut-off, chunk length; probe: a DI-SOP solve to 1e-3 ||B||_1,
+ * median of 3), bit 1 the batched tile width and its push split (probes of 6 and 24 sweeps);
+ * 0 only reports the current values. Untuned graphs use 64 / 4096 / 1024; a graph's first
+ * batched call with rhs_tile 0 tunes the batched setting itself. out (nullable) receives the
+ * values in use. Errors: DI_ERR_INVALID_ARG, DI_ERR_BUSY, DI_ERR_OOM, DI_ERR_CUDA.
+ */
+di_status di_autotune(di_graph *g, double d, int32_t what, di_tuning *out, void *stream);
+
+/* Bytes of device memory this library holds from its own allocations (cudaMalloc), over every
+ * graph of the process: the graphs' arrays and any scratch not attached by the caller. A
+ * diagnostic: with workspaces attached, solves leave it unchanged. */
+int64_t di_device_bytes_held(void);
+
+/* ------------------------------------------------------------------------------------------
  * Serving: personalised-PageRank requests over resident graphs, continuously batched.
  * ------------------------------------------------------------------------------------------ */
 typedef struct di_server di_server;
@@ -274,7 +375,9 @@ typedef struct {
     int32_t sweeps_per_step;     /* sweeps between two admission / retirement points; 0 means 8 */
     int32_t max_request_sweeps;  /* a request still above its tolerance after this many sweeps
                                     ends with DI_ERR_NOT_CONVERGED; 0 means 100000 */
-    int32_t reserved;
+    int32_t tile_min_queue;      /* a graph whose tile is idle solves its queued requests one at a
+                                    time on the single right-hand-side path until this many wait;
+                                    then they share the tile's sweeps. 0 means 4; 1 always tiles */
     int64_t mem_budget;          /* device bytes for request state over all graphs (24 bytes per
                                     node and slot); slots halve until it fits; 0 means no limit */
 } di_server_opts;
@@ -359,20 +462,26 @@ di_status di_graph_validate(const di_graph *g);
  * di_residual_noalloc — the exact residual F* = B + P.H - H of a history H and its norm
  * ||F*||_1 (by the identity X = H + (I - P)^-1 F*, ||X - H||_1 <= ||F*||_1 / (1 - d)), computed
  * without allocating any memory. The paper has no counterpart: this entry point exists for
- * callers that cannot call cudaMalloc, such as code that records its work into a CUDA graph by
- * stream capture, or hosts whose own pool owns all device memory. Its scratch is a static device
- * array of about 8 MB that every GPU which loads this library holds until the process exits.
+ * callers that cannot call cudaMalloc, such as hosts whose own pool owns all device memory and
+ * forbids the runtime's allocator, or code that must not add the device-wide synchronisation
+ * that cudaMalloc may cause. Its scratch is a static device array of about 8 MB that every GPU
+ * which loads this library holds until the process exits.
  *   n          1 .. 1048576 nodes (the size the static scratch holds); larger n is rejected with
  *              DI_ERR_INVALID_ARG.
  *   rp_in, col_in  int64[n+1], int32[L]: rows of P (in-links), as di_graph_export returns them.
+ *              Every id in col_in must lie in [0, n): the call does not check them (an id outside
+ *              that range reads scratch left by an earlier call or past it). di_csr_validate
+ *              checks a CSR that did not come from di_graph_export.
  *   out_deg    int32[n]: out-degrees.   B, H: double[n].   0 <= d < 1.
  *   Fstar_out  double[n] or NULL: receives F*.   norm_out: one double, receives ||F*||_1.
  * Every array must be device memory of the current device; the caller owns all of them. The call
  * only enqueues work on `stream` (no synchronisation, no allocation); results are ready when
  * the stream reaches that point. The first call on a device looks up the scratch array's device
- * address, so make it before any stream capture. Every call shares the one scratch array: calls
- * whose work can overlap on the GPU (different streams without ordering) race and must not be
- * issued. Errors: DI_ERR_INVALID_ARG (size, d, NULL or host pointer), DI_ERR_CUDA.
+ * address and keeps it for the life of the process, so make that first call before any stream
+ * capture; a device reset (cudaDeviceReset) in between is not supported. Every call shares the one
+ * scratch array: calls whose work can overlap on the GPU (different streams without ordering)
+ * race and must not be issued. Errors: DI_ERR_INVALID_ARG (size, d, NULL pointer, host memory or
+ * memory of another device), DI_ERR_CUDA.
  */
 di_status di_residual_noalloc(int32_t n, const int64_t *rp_in, const int32_t *col_in,
                               const int32_t *out_deg, const double *B, double d, const double *H,

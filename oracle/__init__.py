@@ -9,6 +9,9 @@ Parity status of each function (what pins it lives in tests/test_oracle_*.py):
   build, zero_in, zero_in_naive  pinned: brute force on tiny graphs, hand cases, naive == peeling
   di (DI-CYC, DI-SOP)            pinned: dense direct solve, closed forms, exact rational golden
                                  fixtures, mass invariant, identity X = H + (I-P)^-1 F
+  di_refresh (DI-SOP, r taken    pinned: equals di bit for bit when r is taken once per cycle,
+    every r_every ids)           dense direct solve, identity X = H + (I-P)^-1 F, a hand case
+                                 where the refreshed r admits a node the cycle's r would not
   pi                             pinned: dense direct solve, closed forms
   pi_paper                       pinned: equals X / ||X||_1 for uniform B (derived invariant)
   residual                       pinned: zero at the dense solution, equals the remaining fluid
@@ -84,6 +87,8 @@ def _load():
     lib.or_di.restype = ctypes.c_int
     lib.or_di.argtypes = [i64, i64, vp, vp, vp, vp, dbl, dbl, ctypes.c_int, i64, vp, vp,
                           ctypes.POINTER(DiInfo)]
+    lib.or_di_refresh.restype = ctypes.c_int
+    lib.or_di_refresh.argtypes = [i64, i64, vp, vp, vp, vp, dbl, dbl, i64, i64, vp, vp, ctypes.POINTER(DiInfo)]
     lib.or_di_e.restype = ctypes.c_int
     lib.or_di_e.argtypes = [i64, i64, vp, vp, vp, vp, vp, ctypes.c_int32, vp, dbl, dbl, ctypes.c_int, i64, vp, vp,
                             ctypes.POINTER(DiInfo)]
@@ -171,6 +176,19 @@ def di(g: Graph, B, d: float, tol: float, schedule: int = SOP, max_cycles: int =
     info = DiInfo()
     rc = lib.or_di(g.n, g.L, g.rp_out.ctypes.data, g.col_out.ctypes.data, g.loop.ctypes.data, pb,
                    d, tol, schedule, max_cycles, H.ctypes.data, F.ctypes.data, ctypes.byref(info))
+    return H, F, info.as_dict(), rc == 0
+
+
+def di_refresh(g: Graph, B, d: float, tol: float, r_every: int, max_cycles: int = 100_000):
+    """DI-SOP with r = ||F||_1 taken again every r_every node ids within a cycle (r_every <= 0
+    or >= N: the plain DI-SOP of di). Returns (H, F, info dict, converged)."""
+    lib = _load()
+    B, pb = _c(B, np.float64)
+    H = np.zeros(g.n, np.float64)
+    F = np.zeros(g.n, np.float64)
+    info = DiInfo()
+    rc = lib.or_di_refresh(g.n, g.L, g.rp_out.ctypes.data, g.col_out.ctypes.data, g.loop.ctypes.data, pb,
+                           d, tol, int(r_every), max_cycles, H.ctypes.data, F.ctypes.data, ctypes.byref(info))
     return H, F, info.as_dict(), rc == 0
 
 

@@ -20,6 +20,7 @@
  *   or_zero_in       E, the recursively defined zero-in-degree set (Section 2.4), by peeling.
  *   or_zero_in_naive E by its definition, iterated to the least fixpoint (small N only).
  *   or_di            DI-CYC and DI-SOP (Section 2.3, Section 2.5), one node visit at a time.
+ *   or_di_refresh    DI-SOP with r taken again every r_every node ids within a cycle.
  *   or_di_e          the same after one visit of every node of E in level order (E converges
  *                    in finitely many steps, Section 2.4).
  *   or_di_from       the same from a given state (H, F) instead of (0, B): resuming a
@@ -228,7 +229,7 @@ static double sum_fluid(int64_t n, const double *F) {
  * H overshoots X), which the visit moves like any other by linearity.
  */
 static int run_cycles(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out, const uint8_t *loop,
-                      double d, double tol, int schedule, int64_t max_cycles, double *H, double *F,
+                      double d, double tol, int schedule, int64_t max_cycles, int64_t r_every, double *H, double *F,
                       or_di_info *info) {
     double r = sum_fluid(n, F);
     while (r > tol && (max_cycles < 0 || info->cycles < max_cycles)) {
@@ -236,6 +237,8 @@ static int run_cycles(int64_t n, int64_t L, const int64_t *rp_out, const int32_t
         if (schedule == 1) {
             double r_cycle = r;
             for (int64_t i = 0; i < n; i++) {
+                /* the refreshed variant takes r again before nodes r_every, 2 r_every, ... */
+                if (r_every > 0 && i > 0 && i % r_every == 0) r_cycle = sum_fluid(n, F);
                 double out_i = (double)(rp_out[i + 1] - rp_out[i]);
                 if (fabs(F[i]) > (r_cycle / (double)L) * out_i) visit(i, d, rp_out, col_out, loop, H, F, info);
             }
@@ -261,7 +264,21 @@ int or_di(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out, c
           double *H, double *F, or_di_info *info) {
     memset(info, 0, sizeof(*info));
     for (int64_t i = 0; i < n; i++) { H[i] = 0.0; F[i] = B[i]; }
-    return run_cycles(n, L, rp_out, col_out, loop, d, tol, schedule, max_cycles, H, F, info);
+    return run_cycles(n, L, rp_out, col_out, loop, d, tol, schedule, max_cycles, 0, H, F, info);
+}
+
+/*
+ * DI-SOP with r refreshed within the cycle (the variant of Section 2.3's threshold that takes
+ * r_n' more often than once per cycle): r = ||F||_1 is taken at the start of the cycle and again
+ * before node ids r_every, 2 r_every, ... Everything else is or_di's DI-SOP, including the
+ * fallback of a cycle that visits nothing. r_every <= 0 or >= n is or_di itself.
+ */
+int or_di_refresh(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out, const uint8_t *loop,
+                  const double *B, double d, double tol, int64_t r_every, int64_t max_cycles,
+                  double *H, double *F, or_di_info *info) {
+    memset(info, 0, sizeof(*info));
+    for (int64_t i = 0; i < n; i++) { H[i] = 0.0; F[i] = B[i]; }
+    return run_cycles(n, L, rp_out, col_out, loop, d, tol, 1, max_cycles, r_every, H, F, info);
 }
 
 /*
@@ -274,7 +291,7 @@ int or_di_from(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_o
                double *H, double *F, or_di_info *info) {
     memset(info, 0, sizeof(*info));
     for (int64_t i = 0; i < n; i++) { H[i] = H0[i]; F[i] = F0[i]; }
-    return run_cycles(n, L, rp_out, col_out, loop, d, tol, schedule, max_cycles, H, F, info);
+    return run_cycles(n, L, rp_out, col_out, loop, d, tol, schedule, max_cycles, 0, H, F, info);
 }
 
 /*
@@ -296,7 +313,7 @@ int or_di_e(int64_t n, int64_t L, const int64_t *rp_out, const int32_t *col_out,
                 visit(i, d, rp_out, col_out, loop, H, F, info);
                 info->e_visits++;
             }
-    return run_cycles(n, L, rp_out, col_out, loop, d, tol, schedule, max_cycles, H, F, info);
+    return run_cycles(n, L, rp_out, col_out, loop, d, tol, schedule, max_cycles, 0, H, F, info);
 }
 
 /* ------------------------------------------------------------------------------------------ */

@@ -19,15 +19,19 @@ __all__ = [
     "build", "load", "DiError", "Graph",
     "DI_CYC", "DI_SOP", "DI_FLUID_F32", "DI_FLUID_F64",
     "di_graph_create", "di_graph_destroy", "di_graph_stats_get", "di_graph_export",
-    "di_solve", "di_solve_ex", "di_solve_resume", "di_power_iter", "di_power_iter_push", "di_solve_batch", "di_ppr_batch", "di_residual_noalloc",
+    "di_solve", "di_solve_ex", "di_solve_resume", "di_power_iter", "di_power_iter_ex", "di_power_iter_push", "di_solve_batch", "di_ppr_batch", "di_residual_noalloc",
     "di_server_create", "di_server_submit", "di_server_wait", "di_server_destroy", "Server",
     "di_csr_validate", "di_graph_validate", "di_last_error", "di_version",
+    "DI_WS_SOLVE", "DI_WS_BATCH", "di_workspace_size", "di_graph_set_workspace", "di_device_bytes_held",
+    "di_autotune",
 ]
 
 DI_CYC, DI_SOP = 0, 1
+DI_WS_SOLVE, DI_WS_BATCH = 0, 1
+NOALLOC_MAX_NODES = 1 << 20   # largest n di_residual_noalloc's static scratch holds
 DI_FLUID_F32, DI_FLUID_F64 = 0, 1
 STATUS = {0: "DI_OK", 1: "DI_ERR_INVALID_ARG", 2: "DI_ERR_OUT_OF_RANGE_ID", 3: "DI_ERR_OOM", 4: "DI_ERR_CUDA",
-          5: "DI_ERR_NOT_CONVERGED", 6: "DI_ERR_BUSY", 7: "DI_ERR_TIMEOUT"}
+          5: "DI_ERR_NOT_CONVERGED", 6: "DI_ERR_BUSY", 7: "DI_ERR_TIMEOUT", 8: "DI_ERR_CORRUPT"}
 ARRAYS = {  # di_array id -> (numpy dtype, length kind)
     "rowptr_out": (0, np.int64, "n+1"), "col_out": (1, np.int32, "L"), "rowptr_in": (2, np.int64, "n+1"),
     "col_in": (3, np.int32, "L"), "out_deg": (4, np.int32, "n"), "in_deg": (5, np.int32, "n"),
@@ -55,18 +59,30 @@ class GraphStats(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("fluid", ctypes.c_int32), ("max_sweeps", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("host_loop", ctypes.c_int32), ("rhs_tile", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("e_prediffuse", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("e_prediffuse", ctypes.c_int32), ("r_refresh", ctypes.c_int32),
+                ("exact_r", ctypes.c_int32)]
 
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("d", ctypes.c_double), ("slots", ctypes.c_int32), ("sweeps_per_step", ctypes.c_int32),
-                ("max_request_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mem_budget", ctypes.c_int64)]
+                ("max_request_sweeps", ctypes.c_int32), ("tile_min_queue", ctypes.c_int32),
+                ("mem_budget", ctypes.c_int64)]
 
 
 class RequestInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("slot", ctypes.c_int32), ("residual_l1", ctypes.c_double), ("queue_ms", ctypes.c_double),
                 ("service_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("push_row", ctypes.c_int32), ("heavy_cut", ctypes.c_int32), ("heavy_chunk", ctypes.c_int32),
+                ("rhs_tile", ctypes.c_int32), ("batch_heavy_cut", ctypes.c_int32),
+                ("batch_heavy_chunk", ctypes.c_int32), ("single_probe_ms", ctypes.c_double),
+                ("batch_rate", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -119,6 +135,8 @@ def load(path: str | None = None):
     lib.di_solve_ex.argtypes = [vp, vp, dbl, dbl, ctypes.POINTER(SolveOpts), vp, vp, ctypes.POINTER(SolveInfo), vp]
     lib.di_power_iter.restype = st
     lib.di_power_iter.argtypes = [vp, vp, dbl, dbl, i32, vp, vp, ctypes.POINTER(SolveInfo), vp]
+    lib.di_power_iter_ex.restype = st
+    lib.di_power_iter_ex.argtypes = [vp, vp, dbl, dbl, ctypes.POINTER(SolveOpts), vp, vp, ctypes.POINTER(SolveInfo), vp]
     lib.di_solve_resume.restype = st
     lib.di_solve_resume.argtypes = [vp, vp, vp, vp, dbl, dbl, ctypes.POINTER(SolveOpts), vp, vp, vp,
                                     ctypes.POINTER(SolveInfo), vp]
@@ -143,6 +161,14 @@ def load(path: str | None = None):
     lib.di_server_destroy.argtypes = [vp]
     lib.di_residual_noalloc.restype = st
     lib.di_residual_noalloc.argtypes = [i32, vp, vp, vp, vp, dbl, vp, vp, vp, vp]
+    lib.di_workspace_size.restype = st
+    lib.di_workspace_size.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_int64)]
+    lib.di_graph_set_workspace.restype = st
+    lib.di_graph_set_workspace.argtypes = [vp, i32, vp, i64]
+    lib.di_autotune.restype = st
+    lib.di_autotune.argtypes = [vp, dbl, i32, ctypes.POINTER(Tuning), vp]
+    lib.di_device_bytes_held.restype = i64
+    lib.di_device_bytes_held.argtypes = []
     lib.di_last_error.restype = ctypes.c_char_p
     lib.di_last_error.argtypes = []
     lib.di_version.restype = ctypes.c_char_p
@@ -181,6 +207,18 @@ def _stream(*arrays):
     return None
 
 
+def _numel(x) -> int:
+    return int(x.numel()) if _is_torch(x) else int(np.asarray(x).size)
+
+
+def _need(n: int, **arrays):
+    """Raises DiError (invalid argument) when an array given is shorter than its required
+    length; the library takes lengths from the graph, not from the arrays."""
+    for name, x in arrays.items():
+        if x is not None and _numel(x) < n:
+            raise DiError(1, f"{name} has {_numel(x)} entries; this call needs {n}")
+
+
 def _check(status: int, info=None):
     if status != 0:
         raise DiError(status, load().di_last_error().decode(), info.as_dict() if info is not None else None)
@@ -203,6 +241,7 @@ class Graph:
         self.handle = handle
         self.n = n
         self._stats = None
+        self.workspaces = {}   # kind -> the caller's buffer while attached (kept alive here)
 
     @property
     def stats(self) -> dict:
@@ -214,6 +253,7 @@ class Graph:
         if self.handle:
             load().di_graph_destroy(self.handle)
             self.handle = None
+            self.workspaces = {}
 
     def __del__(self):
         try:
@@ -235,6 +275,42 @@ def di_graph_create(n_nodes: int, src, dst) -> Graph:
 
 def di_graph_destroy(g: Graph):
     g.close()
+
+
+def di_workspace_size(g: Graph, kind: int, param: int = 0) -> int:
+    """Bytes of device scratch the solves of `kind` (DI_WS_SOLVE with param = fluid, DI_WS_BATCH
+    with param = widest tile) need on this graph."""
+    b = ctypes.c_int64()
+    _check(load().di_workspace_size(g.handle, int(kind), int(param), ctypes.byref(b)))
+    return b.value
+
+
+def di_graph_set_workspace(g: Graph, kind: int, workspace=None):
+    """Attach a caller-owned device buffer (a CUDA tensor, e.g. torch.empty(bytes, dtype=uint8,
+    device='cuda')) as the scratch of the solves of `kind`, or detach it (None). The graph keeps a
+    reference to the tensor while it is attached."""
+    if workspace is None:
+        _check(load().di_graph_set_workspace(g.handle, int(kind), None, 0))
+        g.workspaces.pop(int(kind), None)
+        return
+    if not (_is_torch(workspace) and workspace.is_cuda and workspace.is_contiguous()):
+        raise DiError(1, "the workspace must be a contiguous CUDA tensor")
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(load().di_graph_set_workspace(g.handle, int(kind), workspace.data_ptr(), int(nbytes)))
+    g.workspaces[int(kind)] = workspace
+
+
+def di_autotune(g: Graph, d: float = 0.85, what: int = 3) -> dict:
+    """Tune the push split on this graph (bit 0: single right-hand side, bit 1: batched; 0 only
+    reports). Returns the values in use."""
+    t = Tuning()
+    _check(load().di_autotune(g.handle, float(d), int(what), ctypes.byref(t), None))
+    return t.as_dict()
+
+
+def di_device_bytes_held() -> int:
+    """Device bytes the library holds from its own allocations (all graphs of the process)."""
+    return int(load().di_device_bytes_held())
 
 
 def di_graph_stats_get(g: Graph) -> dict:
@@ -259,6 +335,7 @@ def di_graph_export(g: Graph, which: str, out=None):
 def di_solve(g: Graph, B, d: float, tol: float, schedule: int = DI_SOP, max_sweeps: int = 0, X_out=None):
     """D-iteration with default options (FP32 fluid + FP64 refinement). Returns (X, info)."""
     X = X_out if X_out is not None else _like(B, g.n, np.float64)
+    _need(g.n, B=B, X_out=X)
     info = SolveInfo()
     res = ctypes.c_double()
     _check(load().di_solve(g.handle, _ptr(B, np.float64), float(d), float(tol), int(schedule), int(max_sweeps),
@@ -268,11 +345,12 @@ def di_solve(g: Graph, B, d: float, tol: float, schedule: int = DI_SOP, max_swee
 
 def di_solve_ex(g: Graph, B, d: float, tol: float, schedule: int = DI_SOP, fluid: int = DI_FLUID_F32,
                 max_sweeps: int = 0, refine: int = 0, host_loop: int = 0, profile: int = 0, e_prediffuse: int = 0,
-                X_out=None):
+                r_refresh: int = 0, exact_r: int = 0, X_out=None):
     """D-iteration with explicit options. Returns (X, info)."""
     X = X_out if X_out is not None else _like(B, g.n, np.float64)
+    _need(g.n, B=B, X_out=X)
     o = SolveOpts(int(schedule), int(fluid), int(max_sweeps), int(refine), int(host_loop), 0, int(profile),
-                  int(e_prediffuse))
+                  int(e_prediffuse), int(r_refresh), int(exact_r))
     info = SolveInfo()
     res = ctypes.c_double()
     _check(load().di_solve_ex(g.handle, _ptr(B, np.float64), float(d), float(tol), ctypes.byref(o),
@@ -286,6 +364,7 @@ def di_solve_resume(g: Graph, B, H0, d: float, tol: float, F0=None, F_out=None, 
     """D-iteration from the state (H0, F0) (F0 None: the exact residual of H0, a warm start).
     Returns (X, info); the final fluid goes to F_out when given."""
     X = X_out if X_out is not None else _like(B, g.n, np.float64)
+    _need(g.n, B=B, H0=H0, F0=F0, F_out=F_out, X_out=X)
     o = SolveOpts(int(schedule), int(fluid), int(max_sweeps), int(refine), int(host_loop), 0, int(profile),
                   int(e_prediffuse))
     info = SolveInfo()
@@ -299,10 +378,25 @@ def di_solve_resume(g: Graph, B, H0, d: float, tol: float, F0=None, F_out=None, 
 def di_power_iter(g: Graph, B, d: float, tol: float, max_iters: int = 0, X_out=None):
     """Jacobi power iteration on X = P.X + B. Returns (X, info)."""
     X = X_out if X_out is not None else _like(B, g.n, np.float64)
+    _need(g.n, B=B, X_out=X)
     info = SolveInfo()
     res = ctypes.c_double()
     _check(load().di_power_iter(g.handle, _ptr(B, np.float64), float(d), float(tol), int(max_iters),
                                 _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)), info)
+    return X, info.as_dict()
+
+
+def di_power_iter_ex(g: Graph, B, d: float, tol: float, fluid: int = DI_FLUID_F32, max_iters: int = 0,
+                     refine: int = 0, profile: int = 0, X_out=None):
+    """Power iteration with options: fluid DI_FLUID_F32 (FP32 increments, exact certification) or
+    DI_FLUID_F64 (FP64 throughout). Returns (X, info)."""
+    X = X_out if X_out is not None else _like(B, g.n, np.float64)
+    _need(g.n, B=B, X_out=X)
+    o = SolveOpts(0, int(fluid), int(max_iters), int(refine), 0, 0, int(profile), 0, 0, 0)
+    info = SolveInfo()
+    res = ctypes.c_double()
+    _check(load().di_power_iter_ex(g.handle, _ptr(B, np.float64), float(d), float(tol), ctypes.byref(o),
+                                   _ptr(X, np.float64), ctypes.byref(res), ctypes.byref(info), _stream(B, X)), info)
     return X, info.as_dict()
 
 
@@ -311,6 +405,7 @@ def di_power_iter_push(g: Graph, B, d: float, tol: float, max_iters: int = 0, fl
     """Power iteration per column (PI', a push over the out-links): the Jacobi iteration on
     X = P.X + B with the same stopping rule as di_power_iter. Returns (X, info)."""
     X = X_out if X_out is not None else _like(B, g.n, np.float64)
+    _need(g.n, B=B, X_out=X)
     info = SolveInfo()
     res = ctypes.c_double()
     _check(load().di_power_iter_push(g.handle, _ptr(B, np.float64), float(d), float(tol), int(max_iters), int(fluid),
@@ -332,6 +427,8 @@ def di_solve_batch(g: Graph, B, d: float, tol, schedule: int = DI_SOP, max_sweep
     tol = _tol_array(tol, k, B)
     X = X_out if X_out is not None else (_like(B, k * g.n, np.float64).reshape(k, g.n))
     res = res_out if res_out is not None else np.empty(k, dtype=np.float64)
+    _need(k * g.n, B=B, X_out=X)
+    _need(k, tol=tol, res_out=res)
     o = SolveOpts(int(schedule), DI_FLUID_F32, int(max_sweeps), int(refine), 0, int(rhs_tile), 0, 0)
     info = SolveInfo()
     _check(load().di_solve_batch(g.handle, k, _ptr(B, np.float64), float(d), _ptr(tol, np.float64), ctypes.byref(o),
@@ -348,6 +445,8 @@ def di_ppr_batch(g: Graph, seed_offsets, seeds, d: float, tol, schedule: int = D
     tol = _tol_array(tol, k, seeds)
     X = X_out if X_out is not None else (_like(seeds, k * g.n, np.float64).reshape(k, g.n))
     res = res_out if res_out is not None else np.empty(k, dtype=np.float64)
+    _need(k * g.n, X_out=X)
+    _need(k, tol=tol, res_out=res)
     o = SolveOpts(int(schedule), DI_FLUID_F32, int(max_sweeps), int(refine), int(host_loop), int(rhs_tile), 0, 0)
     info = SolveInfo()
     _check(load().di_ppr_batch(g.handle, k, _ptr(seed_offsets, np.int64), _ptr(seeds, np.int32), float(d),
@@ -358,11 +457,32 @@ def di_ppr_batch(g: Graph, seed_offsets, seeds, d: float, tol, schedule: int = D
 
 def di_residual_noalloc(n: int, rp_in, col_in, out_deg, B, d: float, H, norm_out, Fstar_out=None):
     """Exact residual F* = B + P.H - H and ||F*||_1 (into the one-element CUDA tensor norm_out)
-    with no allocation: every argument is a CUDA tensor the caller owns. Only enqueues work on
-    torch's current stream."""
-    _check(load().di_residual_noalloc(int(n), _ptr(rp_in, np.int64), _ptr(col_in, np.int32), _ptr(out_deg, np.int32),
-                                      _ptr(B, np.float64), float(d), _ptr(H, np.float64),
-                                      _ptr(Fstar_out, np.float64), _ptr(norm_out, np.float64), _stream(H, B)))
+    with no allocation: every argument is a CUDA tensor the caller owns, all on one device.
+    Only enqueues work on that device's current torch stream. The lengths are checked here,
+    since the C call trusts n: rp_in n+1 entries, out_deg, B, H and Fstar_out at least n,
+    norm_out at least one."""
+    import torch
+    n = int(n)
+    args = {"rp_in": rp_in, "col_in": col_in, "out_deg": out_deg, "B": B, "H": H, "norm_out": norm_out}
+    if Fstar_out is not None:
+        args["Fstar_out"] = Fstar_out
+    for name, t in args.items():
+        if not (_is_torch(t) and t.is_cuda):
+            raise DiError(1, f"{name} must be a CUDA tensor")
+    dev = H.device
+    for name, t in args.items():
+        if t.device != dev:
+            raise DiError(1, f"{name} is on {t.device}, H on {dev}: every tensor must be on one device")
+    if 1 <= n <= NOALLOC_MAX_NODES:   # other n: the library rejects it with its own message
+        need = {"rp_in": n + 1, "out_deg": n, "B": n, "H": n, "norm_out": 1, "Fstar_out": n}
+        for name, want in need.items():
+            if name in args and (args[name].numel() < want or (name == "rp_in" and args[name].numel() != want)):
+                raise DiError(1, f"{name} has {args[name].numel()} entries; n = {n} needs "
+                                 f"{'exactly' if name == 'rp_in' else 'at least'} {want}")
+    with torch.cuda.device(dev):
+        _check(load().di_residual_noalloc(n, _ptr(rp_in, np.int64), _ptr(col_in, np.int32), _ptr(out_deg, np.int32),
+                                          _ptr(B, np.float64), float(d), _ptr(H, np.float64),
+                                          _ptr(Fstar_out, np.float64), _ptr(norm_out, np.float64), _stream(H)))
     return norm_out
 
 
@@ -386,10 +506,11 @@ class Server:
 
 
 def di_server_create(graphs, d: float = 0.85, slots: int = 0, sweeps_per_step: int = 0, max_request_sweeps: int = 0,
-                     mem_budget: int = 0) -> Server:
+                     mem_budget: int = 0, tile_min_queue: int = 0) -> Server:
     lib = load()
     arr = (ctypes.c_void_p * len(graphs))(*[g.handle for g in graphs])
-    o = ServerOpts(float(d), int(slots), int(sweeps_per_step), int(max_request_sweeps), 0, int(mem_budget))
+    o = ServerOpts(float(d), int(slots), int(sweeps_per_step), int(max_request_sweeps), int(tile_min_queue),
+                   int(mem_budget))
     h = ctypes.c_void_p()
     _check(lib.di_server_create(arr, len(graphs), ctypes.byref(o), ctypes.byref(h)))
     return Server(h.value, graphs)

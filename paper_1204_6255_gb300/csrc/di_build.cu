@@ -25,6 +25,7 @@ namespace di {
 // errors and small host utilities
 // ------------------------------------------------------------------------------------------
 static thread_local std::string g_last_error;
+std::atomic<long long> g_device_bytes{0};
 
 void set_error(const char *fmt, ...) {
     char buf[1024];
@@ -439,7 +440,7 @@ __global__ void k_heavy_in_lists(const uint32_t *flag, const uint32_t *flag_pos,
 __global__ void k_count_heavy_out(const int32_t *out_deg, int32_t n, unsigned long long *cnt) {
     unsigned long long c = 0;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        c += out_deg[v] > kPushHeavy;
+        c += out_deg[v] > kPushHeavyMin;
     c = warp_sum(c);
     if (lane_id() == 0 && c) atomicAdd(cnt, c);
 }
@@ -468,6 +469,84 @@ __global__ void k_hub_insert(const int32_t *in_deg, int32_t n, int32_t min_deg, 
 __global__ void k_hub_finalize(const unsigned long long *slots, int32_t *ids) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < kHubSlots) ids[i] = slots[i] ? (int32_t)(uint32_t)(slots[i] & 0xffffffffu) : -1;
+}
+
+// Largest number of in-links that a node which is not a hub receives from sources less than
+// `reach` ids away (the rows of col_in are sorted, so two binary searches per node). The push
+// window adds at most one link per source of a segment into a slot, and only from sources that
+// near, so this bounds the adds into any window slot per segment.
+__global__ void k_window_reach(const int64_t *rp_in, const int32_t *col_in, int32_t n, const int32_t *hub_ids,
+                               int32_t reach, unsigned int *max_cnt) {
+    unsigned int best = 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        if (__ldg(hub_ids + hub_slot((int32_t)j)) == (int32_t)j) continue;
+        const int64_t b = rp_in[j], e = rp_in[j + 1];
+        const int64_t lo_id = j - reach + 1, hi_id = j + reach - 1;
+        int64_t a = b, z = e;   // first link with id >= lo_id
+        while (a < z) {
+            const int64_t m = (a + z) >> 1;
+            if (col_in[m] < lo_id) a = m + 1; else z = m;
+        }
+        int64_t c = a, y = e;   // first link with id > hi_id
+        while (c < y) {
+            const int64_t m = (c + y) >> 1;
+            if (col_in[m] <= hi_id) c = m + 1; else y = m;
+        }
+        const unsigned int cnt = (unsigned int)(c - a);
+        best = cnt > best ? cnt : best;
+    }
+    atomicMax(max_cnt, best);
+}
+
+// Largest number of in-links that a hub receives from the sources of one kSelChunk-id segment
+// (the push's hub slots sum at most that many shares per segment before they are folded into
+// FP32). One warp per hub slot; its lanes walk the segments the hub's sorted in-row touches,
+// counting each by two binary searches.
+__global__ void k_hub_reach(const int64_t *rp_in, const int32_t *col_in, const int32_t *hub_ids, int chunk,
+                            unsigned int *max_cnt) {
+    const int lane = (int)lane_id();
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned int best = 0;
+    for (int64_t h = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; h < kHubSlots; h += nw) {
+        const int32_t v = hub_ids[h];
+        if (v < 0) continue;
+        const int64_t b = rp_in[v], e = rp_in[v + 1];
+        if (e <= b) continue;
+        const int32_t s0 = col_in[b] / chunk, s1 = col_in[e - 1] / chunk;
+        for (int32_t sg = s0 + lane; sg <= s1; sg += 32) {
+            int64_t lo = b, hi = e;
+            while (lo < hi) {   // first link from a source >= sg * chunk
+                const int64_t m = (lo + hi) >> 1;
+                if (col_in[m] < (int64_t)sg * chunk) lo = m + 1; else hi = m;
+            }
+            int64_t lo2 = lo, hi2 = e;
+            while (lo2 < hi2) {   // first link from a source >= (sg + 1) * chunk
+                const int64_t m = (lo2 + hi2) >> 1;
+                if (col_in[m] < (int64_t)(sg + 1) * chunk) lo2 = m + 1; else hi2 = m;
+            }
+            const unsigned int c = (unsigned int)(lo2 - lo);
+            best = c > best ? c : best;
+        }
+    }
+    best = max(best, __shfl_xor_sync(kFull, best, 16));
+    best = max(best, __shfl_xor_sync(kFull, best, 8));
+    best = max(best, __shfl_xor_sync(kFull, best, 4));
+    best = max(best, __shfl_xor_sync(kFull, best, 2));
+    best = max(best, __shfl_xor_sync(kFull, best, 1));
+    if (lane == 0 && best) atomicMax(max_cnt, best);
+}
+
+// (level << bits | id) keys of the nodes of E, and back to ids after sorting
+__global__ void k_e_keys(const int32_t *order, int64_t cnt, const int32_t *level, int bits, uint64_t *keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = order[i];
+        keys[i] = ((uint64_t)(uint32_t)level[v] << bits) | (uint64_t)(uint32_t)v;
+    }
+}
+__global__ void k_e_unkey(const uint64_t *keys, int64_t cnt, int bits, int32_t *order) {
+    const uint64_t mask = (1ull << bits) - 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        order[i] = (int32_t)(keys[i] & mask);
 }
 
 // the push kernels' copy of the link targets: bit 31 marks a target that owns its hub slot
@@ -623,8 +702,32 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
         if (L > 0)
             k_mark_hub_links<<<grid_for(L, 256, dev), 256, 0, s>>>(g->col_out.as<int32_t>(), L, g->hub_ids.as<int32_t>(),
                                                                  g->col_push.as<int32_t>());
+        // fixed-point width of the push window: a slot sums at most `reach_cnt` shares per
+        // segment, each below 2^win_qbits in magnitude, and the sum must stay an int32
+        unsigned int *reach_cnt = reinterpret_cast<unsigned int *>(slots.as<char>());
+        DI_CHECK_CUDA(cudaMemsetAsync(reach_cnt, 0, sizeof(unsigned int), s));
+        k_window_reach<<<grid_for(n, 256, dev), 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), n,
+                                                           g->hub_ids.as<int32_t>(), kWinReach, reach_cnt);
+        unsigned int rc = 0;
+        DI_CHECK_CUDA(cudaMemcpyAsync(&rc, reach_cnt, sizeof(rc), cudaMemcpyDeviceToHost, s));
         DI_CHECK_CUDA(cudaGetLastError());
         DI_CHECK_CUDA(cudaStreamSynchronize(s));
+        g->win_reach_max = (int32_t)rc;
+        int qb = 30;
+        while (qb > 1 && (uint64_t)(rc ? rc : 1) * ((1ull << qb) - 1) > 0x7fffffffull) qb--;
+        g->win_qbits = qb;
+        // the same for the hub slots: the most in-links of a hub from one segment's sources
+        DI_CHECK_CUDA(cudaMemsetAsync(reach_cnt, 0, sizeof(unsigned int), s));
+        k_hub_reach<<<(kHubSlots * 32 + 255) / 256, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(),
+                                                               g->hub_ids.as<int32_t>(), kSelChunkNodes, reach_cnt);
+        unsigned int hc = 0;
+        DI_CHECK_CUDA(cudaMemcpyAsync(&hc, reach_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        DI_CHECK_CUDA(cudaGetLastError());
+        DI_CHECK_CUDA(cudaStreamSynchronize(s));
+        g->hub_reach_max = (int32_t)hc;
+        int hb = 30;
+        while (hb > 1 && (uint64_t)(hc ? hc : 1) * ((1ull << hb) - 1) > 0x7fffffffull) hb--;
+        g->hub_qbits = hb < qb ? hb : qb;
     }
 
     // E by peeling; each level's frontier is appended to e_order, so e_order lists E grouped by
@@ -667,6 +770,21 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
         throw;
     }
     cudaFreeHost(hcount);
+    // each level's nodes in ascending id order (a stable sort of (level, id) keys): the
+    // pre-diffusion selects a level's nodes by id chunks, so the windowed push sees id-sorted
+    // segments
+    if (e_total > 1) {
+        DevBuf keys, alt, hist2, scan2;
+        keys.ensure(sizeof(uint64_t) * (size_t)e_total);
+        k_e_keys<<<grid_for(e_total, 256, dev), 256, 0, s>>>(eo, e_total, g->e_level.as<int32_t>(), bits,
+                                                             keys.as<uint64_t>());
+        int lbits = 1;
+        while ((1 << lbits) < level + 1) lbits++;
+        radix_sort(keys, alt, e_total, 0, bits + lbits, hist2, scan2, s);
+        k_e_unkey<<<grid_for(e_total, 256, dev), 256, 0, s>>>(keys.as<uint64_t>(), e_total, bits, eo);
+        DI_CHECK_CUDA(cudaGetLastError());
+        DI_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
 
     // heavy in-CSR rows for the pull kernels
     {
@@ -731,6 +849,9 @@ di_status di_graph_create(int32_t n_nodes, const int32_t *src, const int32_t *ds
         g->n = n_nodes;
         try {
             build_graph(g, src, dst, n_edges, (cudaStream_t)stream);
+            // the solves' pinned control-block mirror, so a solve with an attached workspace
+            // allocates nothing
+            DI_CHECK_CUDA(cudaMallocHost(&g->ws.ctl_host, sizeof(SolveCtl)));
         } catch (...) {
             delete g;
             throw;

@@ -57,30 +57,64 @@ di_status guarded(F &&body) {
 }
 
 // ------------------------------------------------------------------------------------------
-// device memory owned by the library
+// device memory: owned by the library (cudaMalloc) or borrowed from a caller's workspace
 // ------------------------------------------------------------------------------------------
+// Bytes of device memory the library currently holds from cudaMalloc, over every graph (the
+// graphs' CSR arrays included; a caller's workspace is not counted).
+extern std::atomic<long long> g_device_bytes;
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    bool borrowed = false;         // p points into a caller's workspace: never freed here
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
     ~DevBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p && !borrowed) {
+            cudaFree(p);
+            g_device_bytes -= (long long)bytes;
+        }
         p = nullptr;
         bytes = 0;
+        borrowed = false;
     }
     // (Re)allocates to at least `n` bytes; contents are not preserved.
     void ensure(size_t n) {
-        if (n <= bytes && p) return;
+        if (n <= bytes && p && !borrowed) return;
         release();
         size_t b = n ? n : 16;
         DI_CHECK_CUDA(cudaMalloc(&p, b));
+        g_device_bytes += (long long)b;
         bytes = b;
+    }
+    // Points at `n` bytes of a caller's workspace (whatever it held is released first).
+    void bind(void *q, size_t n) {
+        release();
+        p = q;
+        bytes = n;
+        borrowed = true;
     }
     template <class T>
     T *as() const { return static_cast<T *>(p); }
+};
+
+// Hands out consecutive 256-byte-aligned pieces of a caller's workspace (or, with base NULL,
+// only adds up the bytes the pieces need).
+struct Carve {
+    char *base = nullptr;
+    size_t cap = 0, used = 0;
+    static size_t round(size_t n) { return (n + 255) & ~(size_t)255; }
+    void take(DevBuf &b, size_t n) {
+        const size_t a = round(n ? n : 16);
+        if (base) {
+            DI_REQUIRE(used + a <= cap, DI_ERR_INVALID_ARG,
+                       "the attached workspace holds %zu bytes; this call needs more (see di_workspace_size)", cap);
+            b.bind(base + used, a);
+        }
+        used += a;
+    }
 };
 
 // True when `ptr` is device (or managed) memory.
@@ -124,7 +158,7 @@ struct SolveCtl {
     // latest selection: one atomic reserves both for a select chunk
     unsigned long long front_chunks;
     int32_t heavy_count;      // heavy frontier entries written by the latest selection
-    int32_t heavy_chunks;     // kHeavyChunk-link chunks of those entries
+    int32_t heavy_chunks;     // PushTune::chunk-link chunks of those entries
     int32_t done;             // 1 when the stop test has fired
     int32_t status;           // 0 ok; 1 bad right-hand side
     uint32_t ticket;          // last-block-done counter of the reductions
@@ -138,6 +172,9 @@ struct SolveCtl {
     unsigned long long front_total;  // frontier entries over all sweeps
     int32_t split;            // 1: the first reduction raises tol to sqrt(tol * r), the point of
                               //    the first refinement of a refined FP32 solve
+    int32_t subs;             // selections so far (a sweep is r_refresh selections, one per
+                              //    part of the node range)
+    int32_t sweep_selected;   // nodes the parts of the current sweep selected so far
     int32_t halfway;          // 1: these sweeps end in that halfway refinement, whose exact
                               //    residual replaces the fluid, so the stop test may use the
                               //    tracked sum all the way down
@@ -150,25 +187,46 @@ __host__ __device__ inline int32_t front_entries(unsigned long long fc) {
 }
 __host__ __device__ inline int32_t front_segments(unsigned long long fc) { return (int32_t)(fc >> kFrontBits); }
 
-constexpr int kPushHeavy = 4096;
+// Push work split, picked per graph by the autotuner (di_autotune), defaults below: rows of at
+// least `row` links are pushed one at a time by a whole warp; nodes with more than `heavy` links
+// are pushed in `chunk`-link pieces spread over all warps (so out / chunk warps share such a row).
+struct PushTune {
+    int32_t row = 64;
+    int32_t heavy = 4096;
+    int32_t chunk = 1024;
+    bool operator==(const PushTune &o) const { return row == o.row && heavy == o.heavy && chunk == o.chunk; }
+};
+constexpr int kPushHeavyMin = 1024;   // smallest `heavy` the tuner tries (buffers are sized for it)
+constexpr int kHeavyChunkMin = 256;   // smallest `chunk` the tuner tries
 // A refined FP32 solve refines first where ||F||_1 reaches sqrt(tol * ||F_0||_1) (halfway on a log
 // scale); its continuation sweeps then aim at kAimAfterSplit * tol.
 constexpr double kAimAfterSplit = 0.9;
-constexpr int kHeavyChunk = 1024;   // links per work unit of a heavy node's push    // out-degree above which a node's edges are split over warps
+// ... and only when tol is below kSplitBelow * ||F_0||_1: the FP32 rounding of a whole solve was
+// measured near 7e-8 of ||F_0||_1, so above that bound it stays a few percent of tol and the
+// halfway refinement would only cost an extra exact residual.
+constexpr double kSplitBelow = 1e-6;
 constexpr int kPullHeavy = 8192;    // in-degree above which a row's edges are split over warps
 constexpr int kPullChunk = 4096;    // edges per heavy-row chunk of the pull
 constexpr int kReduceBlocks = 1024; // partial sums of the last-block-done reductions
 constexpr int kHubSlots = 2048;     // shared-memory hub cache of the push kernels
+constexpr int kWinReach = 4096;     // push window: every source-target pair it takes is closer
+constexpr int kSelChunkNodes = 2048;   // source nodes of a push segment (the selection's chunk)
 
 // Per-graph state for single-RHS solves and power iteration.
 struct Workspace {
     int fluid = -1;                 // di_fluid the buffers were sized for
+    void *ext = nullptr;            // caller's workspace (di_graph_set_workspace), or NULL
+    size_t ext_bytes = 0;
     DevBuf F, H, B, front_id, front_s, heavy_id, heavy_s, partials, ctl, y0, y1, chunks;
     DevBuf heavy_cstart, heavy_chunk;   // heavy entry -> first chunk; chunk -> heavy entry
-    DevBuf Bdf, cdf, Xdf;           // power iteration in double-float: B, d/out, X
+    DevBuf Bdf, cdf, Xdf;           // power iteration: d/out (FP32 or FP64) in Bdf, X in Xdf;
+                                    // cdf: d/out as double-float for the exact residual
     double cdf_d = -1.0;            // damping factor cdf currently holds (-1: none)
-    cudaGraphExec_t sweep_exec = nullptr;   // reduce -> WHILE{select, push, reduce}
-    cudaGraphExec_t pi_exec = nullptr;      // pull -> WHILE{pull}
+    cudaGraphExec_t sweep_exec = nullptr;   // reduce -> WHILE{(select, push, reduce) x sweep_parts}
+    int sweep_parts = 1;
+    PushTune sweep_tune;                    // push split the sweep graph was captured with
+    cudaGraphExec_t pi_exec = nullptr;      // WHILE{[heavy chunk sums,] pull}
+    int pi_fp64 = 0;                        // mode pi_exec was built for
     cudaStream_t capture_stream = nullptr;
     cudaStream_t out_stream = nullptr;      // copies X out beside the last refinement
     cudaEvent_t out_ready = nullptr, out_done = nullptr;
@@ -218,8 +276,14 @@ struct di_graph {
     di::DevBuf heavy_in_chunk_off; // int32[n_heavy_in + 1]
     di::DevBuf heavy_in_chunk_row; // int32[n_heavy_in_chunks]: heavy index of each chunk
     di::DevBuf heavy_in_partial;   // float2[n_heavy_in_chunks] (double-float partial sums)
-    int64_t n_heavy_out = 0;       // nodes with out-degree > kPushHeavy
+    int64_t n_heavy_out = 0;       // nodes with out-degree > kPushHeavyMin
+    di::PushTune tune_single;      // single right-hand-side push split (autotuned or default)
+    di::PushTune tune_batch;       // batched push split
     di::DevBuf hub_ids;            // int32[kHubSlots]: hub node per hash slot, -1 when empty
+    int32_t win_reach_max = 0;     // most in-links of a non-hub node from sources < kWinReach ids away
+    int32_t win_qbits = 20;        // push window: |fixed-point share| < 2^win_qbits (no int32 overflow)
+    int32_t hub_reach_max = 0;     // most in-links of a hub from the sources of one segment
+    int32_t hub_qbits = 20;        // push hub slots: the same bound (<= win_qbits)
     di::DevBuf col_push;           // int32[L]: col_out with bit 31 set on links into a hub
     std::mutex mu;                 // serialises use of the workspaces
     di::Workspace ws;
@@ -233,6 +297,16 @@ di_status solve_single(di_graph *g, const double *B, double d, double tol, const
                        double *X_out, double *residual_out, di_solve_info *info, cudaStream_t s);
 di_status power_iter(di_graph *g, const double *B, double d, double tol, int32_t max_iters,
                      double *X_out, double *residual_out, di_solve_info *info, cudaStream_t s);
+// A single solve in a workspace the caller owns (not the graph's): no graph lock is taken, so
+// the caller keeps that workspace to itself (the server's workers do).
+di_status solve_single_in(di_graph *g, Workspace &ws, const double *B, double d, double tol,
+                          const di_solve_opts *opts, double *X_out, double *residual_out, di_solve_info *info,
+                          cudaStream_t s);
+// Autotuning of the single right-hand-side push split (di_solve.cu); the caller holds g->mu.
+PushTune autotune_single(di_graph *g, double d, cudaStream_t s, double *best_ms);
+// Caller-provided solve workspace (di_solve.cu): bytes a fluid needs, and attaching one.
+size_t solve_workspace_bytes(di_graph *g, int fluid);
+void solve_workspace_attach(di_graph *g, void *ext, size_t bytes);
 }  // namespace di
 
 // ------------------------------------------------------------------------------------------

@@ -1,11 +1,11 @@
 // Exact residual of a history without any allocation.
 //
-// Some callers cannot call cudaMalloc: code that records its work into a CUDA graph by stream
-// capture (an allocation is not a capturable stream operation, and cudaMalloc may synchronise
-// the device), and hosts that own all device memory through their own pool and forbid the
-// runtime's allocator. di_residual_noalloc serves them: the caller passes every input and output,
-// and the only scratch the kernels need lives in the file-scope array below, which every GPU
-// that loads this library holds until the process exits.
+// Some callers cannot call cudaMalloc: hosts that own all device memory through their own pool
+// and forbid the runtime's allocator, and code that must not add a device-wide synchronisation
+// between two stream-ordered steps (cudaMalloc may synchronise the device). di_residual_noalloc
+// serves them: the caller passes every input and output, and the only scratch the kernels need
+// lives in the file-scope array below, which every GPU that loads this library holds until the
+// process exits.
 //
 // It is a variant of the refinement kernel of the single-RHS solve: F* = B + P.H - H with the
 // link sums in double-float, and ||F*||_1 by a last-block-done FP64 reduction. It walks every row
@@ -105,13 +105,15 @@ void *scratch_for(int dev) {
     return g_scratch_ptr[dev];
 }
 
-bool on_device(const void *p) {
+// True when p is device (or managed) memory of device `dev`, the one the kernels run on.
+bool on_device(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -124,11 +126,12 @@ extern "C" di_status di_residual_noalloc(int32_t n, const int64_t *rp_in, const 
                    "n = %d is outside [1, %d], the size the no-allocation scratch holds", n, kNoAllocMaxNodes);
         DI_REQUIRE(d >= 0.0 && d < 1.0, DI_ERR_INVALID_ARG, "d must be in [0, 1) (got %g)", d);
         DI_REQUIRE(rp_in && col_in && out_deg && B && H && norm_out, DI_ERR_INVALID_ARG, "NULL argument");
-        const void *ptrs[7] = {rp_in, col_in, out_deg, B, H, norm_out, Fstar_out ? Fstar_out : (const void *)H};
-        for (const void *p : ptrs)
-            DI_REQUIRE(on_device(p), DI_ERR_INVALID_ARG, "every array must be device memory");
         int dev = 0;
         DI_CHECK_CUDA(cudaGetDevice(&dev));
+        const void *ptrs[7] = {rp_in, col_in, out_deg, B, H, norm_out, Fstar_out ? Fstar_out : (const void *)H};
+        for (const void *p : ptrs)
+            DI_REQUIRE(on_device(p, dev), DI_ERR_INVALID_ARG, "every array must be device memory of the current device (%d)",
+                       dev);
         unsigned char *scratch = static_cast<unsigned char *>(scratch_for(dev));
         float2 *y = reinterpret_cast<float2 *>(scratch);
         double *partials = reinterpret_cast<double *>(scratch + kPartialOffset);

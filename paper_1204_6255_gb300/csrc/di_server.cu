@@ -39,25 +39,9 @@ double now_ms() {
 }
 
 
-template <int T>
-__global__ void ks_seed_col(const int32_t *seeds, int cnt, int c, double share, float *F, double *Bn) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
-        const int64_t s = seeds[e];
-        atomicAdd(&Bn[s * T + c], share);
-        atomicAdd(&F[s * T + c], (float)share);
-    }
-}
-
-// a finished column: its history goes to out, and its fluid, history and B are zeroed
-template <int T>
-__global__ void ks_col_retire(float *F, double *H, double *Bn, int32_t n, int c, double *out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t idx = i * T + c;
-        out[i] = H[idx];
-        H[idx] = 0.0;
-        F[idx] = 0.f;
-        Bn[idx] = 0.0;
-    }
+__global__ void ks_seed_dense(const int32_t *seeds, int cnt, double share, double *B) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x)
+        atomicAdd(&B[seeds[e]], share);
 }
 
 // Requests with a tolerance below this get an exact FP64 residual before they retire.
@@ -89,6 +73,7 @@ struct di_server {
     double d = 0.85;
     int sweeps_per_step = 8;
     int max_request_sweeps = 100000;
+    int tile_min_queue = 4;              // requests waiting on an idle graph before the tile runs
     std::vector<std::unique_ptr<di::Worker>> workers;
     std::mutex mu;                       // requests map, completion signalling
     std::condition_variable done_cv;
@@ -109,7 +94,8 @@ struct Worker {
     int T = 32;
     BatchWorkspace w;
     cudaStream_t s = nullptr;
-    DevBuf seeds_dev, col_out;
+    DevBuf seeds_dev, col_out, lone_B;
+    Workspace lone_ws;                   // single-solve workspace of the worker's lone requests
     std::mutex pool_mu;
     std::vector<double *> pool;          // free pinned host buffers of n doubles
     std::mutex mu;
@@ -148,6 +134,7 @@ struct Worker {
     template <int TT>
     void step_loop();
     void run();
+    bool solve_lone(const std::shared_ptr<Request> &r);
 
     // runs on the CUDA runtime's thread once a result's copy to host memory has completed; it
     // only takes the server's lock (no CUDA call)
@@ -187,6 +174,7 @@ void Worker::step_loop() {
     while (!srv->stop.load()) {
         // 1. admission
         std::vector<std::shared_ptr<Request>> admitted;
+        std::shared_ptr<Request> lone;
         {
             std::unique_lock<std::mutex> lk(mu);
             bool any_busy = false;
@@ -195,7 +183,16 @@ void Worker::step_loop() {
                 cv.wait_for(lk, std::chrono::milliseconds(20));
                 continue;
             }
-            for (int c = 0; c < TT && !queue.empty(); c++) {
+            // while few requests wait on an idle tile, they run one by one on the single
+            // right-hand-side path: a tile sweep moves all TT columns' state, a single solve only
+            // its own, so the tile pays only once enough requests share its sweeps
+            if (!any_busy && (int)queue.size() < srv->tile_min_queue) {
+                lone = queue.front();
+                queue.pop_front();
+                lone->t_admit = now_ms();
+            }
+            // (a pass that takes a lone request admits nothing into the tile)
+            for (int c = 0; c < TT && !queue.empty() && !lone; c++) {
                 if (slot[c]) continue;
                 auto r = queue.front();
                 queue.pop_front();
@@ -204,6 +201,10 @@ void Worker::step_loop() {
                 slot[c] = r;
                 admitted.push_back(r);
             }
+        }
+        if (lone) {
+            solve_lone(lone);
+            continue;
         }
         if (!admitted.empty()) {
             // free slots are clean (a retiring column is zeroed), so admission only scatters the
@@ -217,9 +218,9 @@ void Worker::step_loop() {
             size_t at = 0;
             for (auto &r : admitted) {
                 const int cnt = (int)r->seeds.size();
-                ks_seed_col<TT><<<(cnt + 255) / 256, 256, 0, s>>>(seeds_dev.as<int32_t>() + at, cnt, r->slot,
-                                                                   (1.0 - srv->d) / cnt, w.F.as<float>(),
-                                                                   w.Bn.as<double>());
+                kb_seed_col<TT><<<(cnt + 255) / 256, 256, 0, s>>>(seeds_dev.as<int32_t>() + at, cnt, r->slot,
+                                                                   (1.0 - srv->d) / cnt, n, w.F.as<float>(),
+                                                                   w.Bn.as<double>(), ctl);
                 at += (size_t)cnt;
                 const int c = r->slot;
                 hc.active[c] = 1;
@@ -228,7 +229,7 @@ void Worker::step_loop() {
                 // between ||B||_1 = 1 - d and its tol, where an exact residual replaces its
                 // fluid before the FP32 rounding grows comparable to tol
                 const double mid = sqrt(r->tol * (1.0 - srv->d));
-                r->halfway = r->tol < kServeExactTol && mid > r->tol;
+                r->halfway = r->tol < kSplitBelow * (1.0 - srv->d);
                 if (r->halfway) hc.tol[c] = mid;
                 hc.r[c] = 0.0;
                 hc.e[c] = 0.0;
@@ -277,7 +278,7 @@ void Worker::step_loop() {
             // 4. the column's history goes to a pinned buffer of the request, the column is zeroed
             // for its next request, and a host function marks the request done after the copy
             r->X = take_buffer();
-            ks_col_retire<TT><<<l.ew, 256, 0, s>>>(w.F.as<float>(), w.H.as<double>(), w.Bn.as<double>(), n, c,
+            kb_col_retire<TT><<<l.ew, 256, 0, s>>>(w.F.as<float>(), w.H.as<double>(), w.Bn.as<double>(), n, c,
                                                    col_out.as<double>());
             DI_CHECK_CUDA(cudaMemcpyAsync(r->X, col_out.p, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
             r->sweeps = hc.sweeps - r->admit_sweep;
@@ -291,6 +292,42 @@ void Worker::step_loop() {
             }
         }
     }
+}
+
+// One request alone: B = (1 - d) / |S| on its seeds, a single right-hand-side DI-SOP solve into
+// a pinned buffer, in the worker's own workspace.
+bool Worker::solve_lone(const std::shared_ptr<Request> &r) {
+    const int32_t n = g->n;
+    const int cnt = (int)r->seeds.size();
+    lone_B.ensure(sizeof(double) * (size_t)n);
+    seeds_dev.ensure(sizeof(int32_t) * (size_t)cnt);
+    DI_CHECK_CUDA(cudaMemsetAsync(lone_B.p, 0, sizeof(double) * (size_t)n, s));
+    DI_CHECK_CUDA(cudaMemcpyAsync(seeds_dev.p, r->seeds.data(), sizeof(int32_t) * (size_t)cnt, cudaMemcpyHostToDevice, s));
+    ks_seed_dense<<<(cnt + 255) / 256, 256, 0, s>>>(seeds_dev.as<int32_t>(), cnt, (1.0 - srv->d) / cnt,
+                                                    lone_B.as<double>());
+    DI_CHECK_CUDA(cudaGetLastError());
+    double *X = take_buffer();
+    di_solve_opts o;
+    memset(&o, 0, sizeof(o));
+    o.schedule = DI_SOP;
+    o.max_sweeps = srv->max_request_sweeps;
+    di_solve_info info;
+    double res = 0.0;
+    // the worker's own single-solve workspace, so callers' solves on the same graph never wait
+    const di_status st = solve_single_in(g, lone_ws, lone_B.as<double>(), srv->d, r->tol, &o, X, &res, &info, s);
+    DI_REQUIRE(st == DI_OK || st == DI_ERR_NOT_CONVERGED, st, "single solve of request %lld failed", (long long)r->id);
+    r->X = X;
+    r->sweeps = info.sweeps;
+    r->residual = res;
+    r->status = st;
+    r->slot = -1;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);   // the history is in host memory already
+        r->t_done = now_ms();
+        r->done = true;
+    }
+    srv->done_cv.notify_all();
+    return true;
 }
 
 void Worker::run() {
@@ -379,6 +416,7 @@ di_status di_server_create(di_graph *const *graphs, int32_t n_graphs, const di_s
         srv->d = d;
         srv->sweeps_per_step = o.sweeps_per_step > 0 ? o.sweeps_per_step : 8;
         srv->max_request_sweeps = o.max_request_sweeps > 0 ? o.max_request_sweeps : 100000;
+        srv->tile_min_queue = o.tile_min_queue > 0 ? o.tile_min_queue : 4;
         for (int i = 0; i < n_graphs; i++) {
             DI_REQUIRE(graphs[i] != nullptr, DI_ERR_INVALID_ARG, "graph %d is NULL", i);
             std::unique_ptr<Worker> w(new Worker());

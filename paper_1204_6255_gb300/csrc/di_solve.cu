@@ -8,14 +8,14 @@
 //               of its 256-node range first, so the visits run on full warps; with FP32 fluid
 //               the next range's F and degrees arrive by cp.async meanwhile. Visited nodes with
 //               out-links become frontier entries (node id, per-link share d * transit / out_i),
-//               id-sorted within segments of kSelChunk nodes; nodes with more than kPushHeavy
-//               links go to a separate heavy list.
+//               id-sorted within segments of kSelChunk nodes; nodes with more links than the
+//               graph's heavy cut-off go to a separate heavy list.
 //   k_push_win  (FP32 fluid) scatters the shares onto the out-neighbours j != i (the l_out loop
 //               of Section 2.5): a block takes a segment, adds the links that land near it into
 //               a shared-memory window and the links into hubs into a shared-memory hub cache,
-//               and sends the rest to F with L2 reductions. Rows of kPushRow links or more go
-//               warp-wide; heavy nodes are spread over every warp of the grid. k_push does the
-//               same for FP64 fluid without the caches.
+//               and sends the rest to F with L2 reductions. Long rows go warp-wide; heavy
+//               nodes are spread over every warp of the grid in chunks (PushTune: the lengths
+//               are autotuned per graph). k_push does the same for FP64 fluid without the caches.
 //   k_reduce    r = sum |F_i| in FP64 (FP32 runs, warp shuffle, block, then the last block to
 //               finish sums the block partials in a fixed order), and the stop test r <= tol.
 //               It writes the WHILE-node condition, so the whole sweep loop runs from one CUDA
@@ -31,6 +31,7 @@
 // walks a run of kPullVT contiguous in-links, and a segmented scan joins the rows that span
 // lanes. Rows with more than kPullHeavy in-links are summed chunk-wise by k_pull_heavy first.
 // Power iteration per column (PI') runs the sweep kernels above with self-links as plain links.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -134,9 +135,14 @@ __device__ __forceinline__ double abs_sum(const double *F, int32_t n) {
 // r = ||F||_1, stop test, and bookkeeping for the next selection.
 template <class T>
 __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl, cudaGraphConditionalHandle h,
-                         int set_cond) {
+                         int set_cond, int sweep_end) {
     __shared__ double scratch[32];
     double tot;
+    if (ctl->done) {
+        // an earlier part of this sweep already stopped the loop: keep the WHILE condition at 0
+        if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+        return;
+    }
     if (ctl->reduce_est) {
         // with nonnegative fluid, sum |F| after the sweep is the sum before it less what the
         // visits absorbed (the select decided this per sweep; see there for when)
@@ -152,8 +158,14 @@ __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl,
         ctl->r = tot;
         ctl->absorbed = 0.0;
         ctl->reduce_est = 0;
-        int sel = ctl->last_selected;
-        ctl->force_cyc = (sel == 0 && tot > 0.0) ? 1 : 0;   // a DI-SOP sweep found no node
+        // a DI-SOP sweep whose parts together found no node is followed by a DI-CYC sweep
+        if (sweep_end) {
+            const int sel = ctl->last_selected < 0 ? -1 : ctl->sweep_selected + ctl->last_selected;
+            ctl->force_cyc = (sel == 0 && tot > 0.0) ? 1 : 0;
+            ctl->sweep_selected = 0;
+        } else {
+            ctl->sweep_selected += ctl->last_selected > 0 ? ctl->last_selected : 0;
+        }
         ctl->last_selected = 0;
         ctl->front_total += (unsigned long long)(front_entries(ctl->front_chunks) + ctl->heavy_count);
         ctl->front_chunks = 0;
@@ -166,7 +178,7 @@ __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl,
             // between ||B||_1 and tol, where an exact residual replaces the fluid
             ctl->split = 0;
             const double mid = sqrt(ctl->tol * tot);
-            if (mid > ctl->tol) {
+            if (ctl->tol < kSplitBelow * tot) {
                 ctl->tol = mid;
                 ctl->halfway = 1;
             }
@@ -262,8 +274,21 @@ __device__ __forceinline__ void visit_math(double f, int32_t o, bool lp, double 
     t = lp ? f * (double)o / ((double)o - d) : f;
     share = o ? t * d / (double)o : 0.0;
 }
-__device__ __forceinline__ bool selects(float f, int32_t o, bool cyc, double, float thr_f) {
-    return cyc ? (f != 0.f) : (fabsf(f) > thr_f * (float)o);
+// DI-SOP's test |F_i| > (r / L) * out_i, decided as in FP64 (r / L is an FP64 value). The FP32
+// product thr_f * out differs from the FP64 one by less than 2^-22 of it, so FP32 decides every
+// node whose fluid is more than 2^-20 (relative) away from its threshold, and FP64 the near ties
+// (and every node when r / L is too small for FP32's normal range).
+constexpr float kThrBand = 1.0f / (1 << 20);
+__device__ __forceinline__ bool sop_selects(float a, int32_t o, double thr, float thr_f) {
+    const float p = thr_f * (float)o;
+    if (thr_f >= 1e-30f) {
+        if (a > p * (1.f + kThrBand)) return true;
+        if (a < p * (1.f - kThrBand)) return false;
+    }
+    return (double)a > thr * (double)o;
+}
+__device__ __forceinline__ bool selects(float f, int32_t o, bool cyc, double thr, float thr_f) {
+    return cyc ? (f != 0.f) : sop_selects(fabsf(f), o, thr, thr_f);
 }
 __device__ __forceinline__ bool selects(double f, int32_t o, bool cyc, double thr, float) {
     return cyc ? (f != 0.0) : (fabs(f) > thr * (double)o);
@@ -297,6 +322,24 @@ __device__ __forceinline__ void sel_prefetch(float *dst_f, int32_t *dst_i, const
 __device__ __forceinline__ void sel_prefetch(double *, int32_t *, const double *, const int32_t *, uint32_t, int32_t,
                                              unsigned, uint64_t, uint64_t) {}
 
+// Fixed-point scale of a segment's shared-memory push window (k_push_win). FP32 atomics on
+// shared memory are compare-and-swap loops on this part, integer ones are native, so the window
+// adds integers: q = round(share * 2^k) for each frontier entry. A window slot sums at most
+// win_reach_max shares per segment (at most one link per source, and only from sources within
+// kWinReach ids: a bound the graph build measures), so shares with |q| < 2^win_qbits cannot
+// overflow its int32. k puts the segment's mean |share| just below 2^(win_qbits - kWinHeadBits):
+// shares up to 2^kWinHeadBits times the mean stay in the window, larger ones skip it, and a unit
+// is 2^-(win_qbits - kWinHeadBits) of the mean share.
+constexpr int kWinHeadBits = 4;
+__device__ __forceinline__ int window_exponent(float mean_abs, int mean_bits) {
+    if (!(mean_abs > 0.f) || isinf(mean_abs)) return 0;
+    int e;
+    frexpf(mean_abs, &e);   // mean_abs < 2^e
+    const int k = mean_bits - e;
+    return k < -126 ? -126 : (k > 126 ? 126 : k);
+}
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }   // -126 <= k <= 127
+
 // Nodes are visited in chunks of kSelChunk consecutive ids per block iteration; warp w of the
 // block owns the kSelWarpNodes consecutive ids from base + w * kSelWarpNodes. The frontier
 // entries of a chunk are compacted with one atomic per chunk, so the frontier is id-sorted
@@ -307,6 +350,7 @@ constexpr int kTrackResync = 8;      // an exact reduction at least every kTrack
 constexpr double kTrackBand = 16.0;  // ... and at every sweep once r <= kTrackBand * tol
 constexpr int kSelWarpNodes = 32 * kSelItems;
 constexpr int kSelChunk = 8 * kSelWarpNodes;   // 256 threads
+static_assert(kSelChunk == kSelChunkNodes, "the build's hub bound counts sources per selection chunk");
 constexpr int kSelMinBlocks = 4;
 template <class T>
 constexpr int kSelBatch = sizeof(T) == 4 ? 4 : 2;   // packed rounds of 32 visits whose history loads fly together
@@ -315,7 +359,9 @@ template <class T>
 __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, const int32_t *out_info,
                                                             int32_t n, SolveCtl *ctl, int32_t *front_id, T *front_s,
                                                             int32_t *heavy_id, T *heavy_s, int32_t *heavy_cstart,
-                                                            int32_t *heavy_chunk, int4 *chunks) {
+                                                            int32_t *heavy_chunk, int4 *chunks, int win_mean_bits,
+                                                            int32_t node_lo, int32_t node_hi, int sweep_end,
+                                                            int heavy_cut, int heavy_len) {
     __shared__ double scratch[32];
     __shared__ unsigned long long scratch_u[32];
     // Per warp, the selected nodes of its range packed in id order: fluid, degree word and
@@ -328,6 +374,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
     __shared__ __align__(16) int32_t s_info[kPre ? 2 : 1][8][kSelWarpNodes];
     __shared__ uint8_t s_off[8][kSelWarpNodes];
     __shared__ int s_wcount[8], s_wbase[8];
+    __shared__ float s_wabs[8];
     __shared__ int s_chunk_base;
     __shared__ double s_thr;
     if (ctl->done) return;
@@ -342,10 +389,13 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
     const int warp = threadIdx.x >> 5;
     uint8_t *woff = s_off[warp];
     int cur = 0;
+    // this launch selects among the nodes [node_lo, node_hi) (node_lo a multiple of kSelChunk):
+    // the whole range, or one part of it when r is refreshed within a sweep
+    n = node_hi;
     if (kPre) {
-        if (blockIdx.x * kSelChunk < (uint32_t)n)
-            sel_prefetch(s_f[0][warp], s_info[0][warp], F, out_info, blockIdx.x * kSelChunk + warp * kSelWarpNodes,
-                         n, lane, keep, stream);
+        if (node_lo + blockIdx.x * kSelChunk < (uint32_t)n)
+            sel_prefetch(s_f[0][warp], s_info[0][warp], F, out_info,
+                         node_lo + blockIdx.x * kSelChunk + warp * kSelWarpNodes, n, lane, keep, stream);
         cp_async_commit();
     }
     T e_run = (T)0;      // dangling mass of this thread
@@ -353,7 +403,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
     unsigned long long pushed = 0;
     unsigned visited = 0;
     // 32-bit node arithmetic: ids stay below 2^31 and a stride below 2^31, so nothing wraps
-    for (uint32_t base = blockIdx.x * kSelChunk; base < (uint32_t)n; base += gridDim.x * kSelChunk) {
+    for (uint32_t base = node_lo + blockIdx.x * kSelChunk; base < (uint32_t)n; base += gridDim.x * kSelChunk) {
         const uint32_t wb = base + warp * kSelWarpNodes;
         T *wf = s_f[cur][warp];
         int32_t *winfo = s_info[cur][warp];
@@ -401,6 +451,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
         }
         __syncwarp();
         int nlight = 0;
+        float sh_abs = 0.f;   // sum of |share| over this lane's light entries of the chunk
         for (int r0 = 0; r0 < cnt; r0 += 32 * kSelBatch<T>) {
             T pf[kSelBatch<T>];
             int32_t pinfo[kSelBatch<T>];
@@ -441,7 +492,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                     ab_run += (float)pf[v] - (float)share * (float)(o - (lp ? 1 : 0));
                     if (o == 0) {
                         e_run += t;
-                    } else if (o > kPushHeavy) {
+                    } else if (o > heavy_cut) {
                         heavy = true;
                     } else if (o - (lp ? 1 : 0) > 0) {
                         light = true;
@@ -452,6 +503,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                     const int p = nlight + __popc(bl & lt);
                     wf[p] = share;
                     woff[p] = (uint8_t)poff[v];
+                    sh_abs += fabsf((float)share);
                 }
                 nlight += __popc(bl);
                 // heavy nodes are rare: one atomic per warp that has any
@@ -462,12 +514,12 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                     if ((int)lane == leader) p0 = atomicAdd(&ctl->heavy_count, __popc(bh));
                     p0 = __shfl_sync(kFull, p0, leader);
                     if (heavy) {
-                        // the node's links are pushed in kHeavyChunk-link chunks over all warps;
+                        // the node's links are pushed in heavy_len-link chunks over all warps;
                         // the chunk list maps each chunk back to its entry
                         const int p = p0 + __popc(bh & lt);
                         heavy_id[p] = (int32_t)i;
                         heavy_s[p] = share;
-                        const int nch = (o + kHeavyChunk - 1) / kHeavyChunk;
+                        const int nch = (o + heavy_len - 1) / heavy_len;
                         const int cs = atomicAdd(&ctl->heavy_chunks, nch);
                         heavy_cstart[p] = cs;
                         for (int c = 0; c < nch; c++) heavy_chunk[cs + c] = p;
@@ -476,7 +528,11 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
             }
         }
         // one atomic reserves the chunk's frontier entries and its segment slot
-        if (lane == 0) s_wcount[warp] = nlight;
+        const float wabs = kPre ? warp_sum(sh_abs) : 0.f;
+        if (lane == 0) {
+            s_wcount[warp] = nlight;
+            s_wabs[warp] = wabs;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             int run = 0;
@@ -487,9 +543,13 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
             }
             s_chunk_base = 0;
             if (run) {
+                float abs_tot = 0.f;
+#pragma unroll
+                for (int w = 0; w < 8; w++) abs_tot += s_wabs[w];
                 const unsigned long long fc = atomicAdd(&ctl->front_chunks, (1ull << kFrontBits) | (unsigned)run);
                 s_chunk_base = front_entries(fc);
-                chunks[front_segments(fc)] = make_int4((int)base, s_chunk_base, run, 0);
+                chunks[front_segments(fc)] =
+                    make_int4((int)base, s_chunk_base, run, window_exponent(abs_tot / (float)run, win_mean_bits));
             }
         }
         __syncthreads();
@@ -525,7 +585,8 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
             atomicAdd(&ctl->last_selected, (int)nvis);
         }
         if (blockIdx.x == 0) {
-            const int sw = atomicAdd(&ctl->sweeps, 1) + 1;
+            const int sw = atomicAdd(&ctl->subs, 1) + 1;
+            if (sweep_end) atomicAdd(&ctl->sweeps, 1);
             // this sweep's reduction takes r from the tracked sum while r is well above tol,
             // except every kTrackResync-th sweep (the FP32 atomics' rounding is not tracked);
             // near the tolerance every reduction sums F, so the stop test is on the exact sum.
@@ -624,14 +685,151 @@ __global__ void __launch_bounds__(256) k_e_visit(const int32_t *nodes, int32_t c
     }
 }
 
-// Push, one warp per batch of 32 frontier entries (no block barriers). Rows of kPushRow links or
+// E-level pre-diffusion of a large level through the windowed push: the level's nodes are
+// id-sorted (the graph build sorts E by level, then id), so a block takes kSelChunk-id chunks,
+// finds the level's nodes in each by binary search, visits them (no node of E has a self-loop:
+// transit = F_i, share d F_i / out_i) and writes their frontier entries as one id-sorted segment
+// per chunk, with the same records the sweep's selection writes; k_push_win then pushes them.
+// Nodes above the heavy cut-off go to the heavy list as in the selection.
+__global__ void __launch_bounds__(256) k_e_select(const int32_t *nodes, int32_t count, float *F, double *H,
+                                                  const int32_t *out_info, int32_t n, SolveCtl *ctl,
+                                                  int32_t *front_id, float *front_s, int32_t *heavy_id,
+                                                  float *heavy_s, int32_t *heavy_cstart, int32_t *heavy_chunk,
+                                                  int4 *chunks, int win_mean_bits, int heavy_cut, int heavy_len) {
+    constexpr int kPerWarp = kSelChunk / 8;   // a chunk holds at most kSelChunk nodes of a level
+    __shared__ int32_t s_id[8][kPerWarp];
+    __shared__ float s_sh[8][kPerWarp];
+    __shared__ int s_range[2];
+    __shared__ int s_wcount[8], s_wbase[8];
+    __shared__ float s_wabs[8];
+    __shared__ int s_base;
+    __shared__ double scratch[32];
+    __shared__ unsigned long long scratch_u[32];
+    const float d_f = (float)ctl->d;
+    const unsigned lane = lane_id(), lt = lanemask_lt();
+    const int warp = threadIdx.x >> 5;
+    float e_run = 0.f;
+    unsigned long long pushed = 0, visited = 0;
+    const int nchunk = (n + kSelChunk - 1) / kSelChunk;
+    for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+        if (threadIdx.x < 2) {
+            // first list entry with id >= (c + threadIdx.x) * kSelChunk
+            const int64_t key = (int64_t)(c + (int)threadIdx.x) * kSelChunk;
+            int lo = 0, hi = count;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (nodes[mid] < key) lo = mid + 1; else hi = mid;
+            }
+            s_range[threadIdx.x] = lo;
+        }
+        __syncthreads();
+        const int e0 = s_range[0], e1 = s_range[1];
+        if (e1 <= e0) {
+            __syncthreads();   // s_range is rewritten for the next chunk
+            continue;
+        }
+        // warp w visits the contiguous run [w0, w1) of the chunk's entries, in order
+        const int per = (e1 - e0 + 7) / 8;
+        const int w0 = min(e1, e0 + warp * per), w1 = min(e1, w0 + per);
+        int nl = 0;
+        float wabs = 0.f;
+        for (int k0 = w0; k0 < w1; k0 += 32) {
+            const int k = k0 + (int)lane;
+            bool light = false;
+            int32_t u = 0;
+            float share = 0.f;
+            if (k < w1) {
+                u = nodes[k];
+                const float f = F[u];
+                const int32_t o = out_info[u] & 0x7fffffff;
+                F[u] = 0.f;
+                H[u] += widen(f);
+                visited++;
+                pushed += (unsigned long long)o;
+                share = o ? __fdividef(f, (float)o) * d_f : 0.f;
+                if (o == 0) {
+                    e_run += f;
+                } else if (o > heavy_cut) {
+                    const int p = atomicAdd(&ctl->heavy_count, 1);
+                    heavy_id[p] = u;
+                    heavy_s[p] = share;
+                    const int nch = (o + heavy_len - 1) / heavy_len;
+                    const int cs = atomicAdd(&ctl->heavy_chunks, nch);
+                    heavy_cstart[p] = cs;
+                    for (int q = 0; q < nch; q++) heavy_chunk[cs + q] = p;
+                } else {
+                    light = true;
+                }
+            }
+            const unsigned bl = __ballot_sync(kFull, light);
+            if (light) {
+                const int p = nl + __popc(bl & lt);
+                s_id[warp][p] = u;
+                s_sh[warp][p] = share;
+                wabs += fabsf(share);
+            }
+            nl += __popc(bl);
+        }
+        wabs = warp_sum(wabs);
+        if (lane == 0) {
+            s_wcount[warp] = nl;
+            s_wabs[warp] = wabs;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            float abs_tot = 0.f;
+            for (int w = 0; w < 8; w++) {
+                s_wbase[w] = run;
+                run += s_wcount[w];
+                abs_tot += s_wabs[w];
+            }
+            s_base = 0;
+            if (run) {
+                // one atomic reserves the chunk's frontier entries and its segment slot
+                const unsigned long long fc = atomicAdd(&ctl->front_chunks, (1ull << kFrontBits) | (unsigned)run);
+                s_base = front_entries(fc);
+                chunks[front_segments(fc)] = make_int4(c * kSelChunk, s_base, run,
+                                                       window_exponent(abs_tot / (float)run, win_mean_bits));
+            }
+        }
+        __syncthreads();
+        const int cb = s_base + s_wbase[warp];
+        for (int k = (int)lane; k < nl; k += 32) {
+            front_id[cb + k] = s_id[warp][k];
+            front_s[cb + k] = s_sh[warp][k];
+        }
+        __syncthreads();   // staging and s_range are reused by the next chunk
+    }
+    const double e_loc = block_sum((double)e_run, scratch);
+    pushed = block_sum(pushed, scratch_u);
+    visited = block_sum(visited, scratch_u);
+    if (threadIdx.x == 0) {
+        if (e_loc != 0.0) atomicAdd(&ctl->e, e_loc);
+        if (pushed) atomicAdd(&ctl->pushed, pushed);
+        if (visited) atomicAdd(&ctl->visited, visited);
+    }
+}
+
+constexpr int64_t kELevelSelectMin = 16384;   // levels of E at least this large take k_e_select
+
+// Clears the frontier counters after a pre-diffusion level's push (the sweeps' reduction does
+// this after every sweep).
+__global__ void k_front_reset(SolveCtl *ctl) {
+    ctl->front_total += (unsigned long long)(front_entries(ctl->front_chunks) + ctl->heavy_count);
+    ctl->front_chunks = 0;
+    ctl->heavy_count = 0;
+    ctl->heavy_chunks = 0;
+    ctl->chunk_next = 0;
+}
+
+// Push, one warp per batch of 32 frontier entries (no block barriers). Rows of PushTune::row links or
 // more go one at a time over the whole warp, 32 consecutive links per load. For the others the
 // warp scans their degrees, then each lane takes kPushVT contiguous links of their concatenated
 // links per round, finds their owner once (binary search over the warp's 33 offsets in shared
 // memory) and keeps kPushVT independent index loads in flight before its atomic adds.
 constexpr int kPushVT = 4;   // measured on GB300: 4 beats 2, 8 and 16 (fewer registers, more blocks)
 constexpr int kHeavyPushUnroll = 4;   // index loads in flight per lane in a heavy node's chunk
-constexpr int kPushRow = 64; // rows at least this long are pushed warp-wide (measured: 64 beats 16 and 32)
 
 template <class T>
 __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_id, const T *__restrict__ front_s,
@@ -639,7 +837,7 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
                                               const int32_t *__restrict__ heavy_cstart,
                                               const int32_t *__restrict__ heavy_chunk,
                                               const int64_t *__restrict__ rp_out, const int32_t *__restrict__ col_out,
-                                              T *F, SolveCtl *ctl) {
+                                              T *F, SolveCtl *ctl, int heavy_len) {
     __shared__ int s_off[8][33];
     __shared__ int64_t s_beg[8][32];
     __shared__ int32_t s_u[8][32];
@@ -651,14 +849,14 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
 
-    // nodes with more than kPushHeavy links: their chunks over all warps
+    // nodes with more than the heavy cut-off of links: their chunks over all warps
     const int hch = ctl->heavy_chunks;
     for (int64_t c = gwarp; c < hch; c += nwarps) {
         const int p = heavy_chunk[c];
         const int32_t u = heavy_id[p];
         const T sh = heavy_s[p];
-        const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * kHeavyChunk;
-        const int64_t ce = min(cb + (int64_t)kHeavyChunk, rp_out[u + 1]);
+        const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * heavy_len;
+        const int64_t ce = min(cb + (int64_t)heavy_len, rp_out[u + 1]);
         for (int64_t k0 = cb + lane; k0 < ce; k0 += 32 * kHeavyPushUnroll) {
             int32_t j[kHeavyPushUnroll];
 #pragma unroll
@@ -717,11 +915,15 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
 // Push with a shared-memory window (FP32 fluid). The select emits the frontier as id-sorted
 // segments of kSelChunk consecutive source nodes; a block takes one segment at a time and adds
 // every link whose target lies within kHalo ids of the segment (host locality: most web links
-// stay near their source) into a window of kWin floats in shared memory, sending only the other
-// links straight to F. The window then goes to F with one four-float atomic per non-zero group,
-// so a dense segment issues a fraction of the global atomics of a link-by-link push.
+// stay near their source) into a window of kWin slots in shared memory, sending only the other
+// links straight to F. The window holds integers: each entry's share in the segment's fixed
+// point (window_exponent), added with native 32-bit shared atomics; FP32 shared atomics would be
+// compare-and-swap loops. The window then goes to F, converted back to FP32, with one four-float
+// atomic per non-zero group, so a dense segment issues a fraction of the global atomics of a
+// link-by-link push. Shares too large for the segment's fixed point take the direct path, and
+// links into hubs always go to the hub cache (the window's overflow bound leaves hubs out).
 constexpr int kHalo = 1024;
-constexpr int kWin = kSelChunk + 2 * kHalo;     // 4096 floats, 16 KB
+constexpr int kWin = kSelChunk + 2 * kHalo;     // 4096 int32 slots, 16 KB
 constexpr int kWinMinEntries = 24;              // sparser segments push link by link
 
 __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__ front_id, const float *__restrict__ front_s,
@@ -730,11 +932,14 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                                                   const int32_t *__restrict__ heavy_chunk,
                                                   const int64_t *__restrict__ rp_out,
                                                   const int32_t *__restrict__ col_push, const int4 *__restrict__ chunks,
-                                                  const int32_t *__restrict__ hub_ids, float *F, SolveCtl *ctl) {
-    __shared__ __align__(16) float s_win[kWin];
+                                                  const int32_t *__restrict__ hub_ids, float *F, SolveCtl *ctl,
+                                                  int win_qmax, int hub_shift, int hub_qmax, int push_row,
+                                                  int heavy_len) {
+    __shared__ __align__(16) int s_win[kWin];
     __shared__ float s_hacc[kHubSlots];      // this block's pending additions to the hubs
+    __shared__ int s_hint[kHubSlots];        // ... from the current segment, in its hub fixed point
     __shared__ int s_off[8][33];
-    // per entry of a warp's batch: {row start - link offset (int64), source id, share}
+    // per entry of a warp's batch: {row start - link offset, source id, share, fixed-point share}
     __shared__ int4 s_rec[8][32];
     __shared__ int s_chunk, s_batch;
     if (ctl->done) return;
@@ -743,7 +948,10 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int q = tid; q < kHubSlots; q += 256) s_hacc[q] = 0.f;
+    for (int q = tid; q < kHubSlots; q += 256) {
+        s_hacc[q] = 0.f;
+        s_hint[q] = 0;
+    }
     __syncthreads();
     // a link to a far target (jr: target id with bit 31 set when the target is a hub): hubs
     // (high in-degree nodes) collect in shared memory, the rest goes to F directly
@@ -751,15 +959,31 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
         if (jr < 0) atomicAdd(&s_hacc[hub_slot(jr & 0x7fffffff)], v);
         else red_keep(&F[jr], v, keep);
     };
+    // the same within a segment: a hub slot takes at most hub_reach_max shares per segment (one
+    // per source; the graph build measures the bound), so it adds integers in the segment's hub
+    // fixed point (native shared atomics; FP32 ones are compare-and-swap loops) and is folded
+    // into the FP32 cache when the segment ends. A share that rounds to 0 or is too large for
+    // the fixed point takes the FP32 path.
+    float hub_scale = 1.f;
+    auto seg_far_add = [&](int32_t jr, float v) {
+        if (jr < 0) {
+            const int slot = hub_slot(jr & 0x7fffffff);
+            const int q = __float2int_rn(v * hub_scale);
+            if (q != 0 && q > -hub_qmax && q < hub_qmax) atomicAdd(&s_hint[slot], q);
+            else atomicAdd(&s_hacc[slot], v);
+        } else {
+            red_keep(&F[jr], v, keep);
+        }
+    };
 
-    // nodes with more than kPushHeavy links: their chunks over all warps
+    // nodes with more than the heavy cut-off of links: their chunks over all warps
     const int hch = ctl->heavy_chunks;
     for (int64_t c = gwarp; c < hch; c += nwarps) {
         const int p = heavy_chunk[c];
         const int32_t u = heavy_id[p];
         const float sh = heavy_s[p];
-        const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * kHeavyChunk;
-        const int64_t ce = min(cb + (int64_t)kHeavyChunk, rp_out[u + 1]);
+        const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * heavy_len;
+        const int64_t ce = min(cb + (int64_t)heavy_len, rp_out[u + 1]);
         for (int64_t k0 = cb + lane; k0 < ce; k0 += 32 * kHeavyPushUnroll) {
             int32_t jr[kHeavyPushUnroll];
 #pragma unroll
@@ -782,9 +1006,13 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
         const int4 ch = chunks[ci];
         const int cstart = ch.y, clen = ch.z;
         const bool use_win = clen >= kWinMinEntries;
+        const float win_scale = pow2f(ch.w), win_unit = pow2f(-ch.w);   // fixed point <-> FP32
+        const int hub_k = max(-126, min(126, ch.w - hub_shift));
+        hub_scale = pow2f(hub_k);
+        const float hub_unit = pow2f(-hub_k);
         const int lo = max(0, ch.x - kHalo) & ~3;
         if (use_win) {
-            for (int q = tid; q < kWin / 4; q += 256) reinterpret_cast<float4 *>(s_win)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = tid; q < kWin / 4; q += 256) reinterpret_cast<int4 *>(s_win)[q] = make_int4(0, 0, 0, 0);
             __syncthreads();
         }
         for (;;) {
@@ -804,15 +1032,21 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                 ebeg = __ldg(rp_out + eu);
                 deg = (int)(__ldg(rp_out + eu + 1) - ebeg);
             }
-            // rows of kPushRow links or more: one row at a time over the whole warp, 32
+            // the share in the segment's fixed point; 0 (never added to the window) when it
+            // does not fit, so its local links go to F directly
+            int eq = __float2int_rn(es * win_scale);
+            const bool ewin = use_win && eq > -win_qmax && eq < win_qmax;
+            if (!ewin) eq = 0;
+            // rows of push_row links or more: one row at a time over the whole warp, 32
             // consecutive links per load, no owner lookup
-            const bool row = deg >= kPushRow;
+            const bool row = deg >= push_row;
             for (unsigned rows = __ballot_sync(kFull, row); rows; rows &= rows - 1) {
                 const int src = __ffs(rows) - 1;
-                const int64_t rb = __shfl_sync(kFull, ebeg, src);
+                const int rb = (int)__shfl_sync(kFull, ebeg, src);   // links stay below 2^31
                 const int rd = __shfl_sync(kFull, deg, src);
                 const int32_t ru = __shfl_sync(kFull, eu, src);
                 const float rs = __shfl_sync(kFull, es, src);
+                const int rq = __shfl_sync(kFull, eq, src);
                 for (int k0 = lane; k0 < rd; k0 += 32 * kPushVT) {
                     int32_t jr[kPushVT];
 #pragma unroll
@@ -822,8 +1056,8 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                         const int32_t j = jr[v] & 0x7fffffff;
                         if (k0 + 32 * v >= rd || (j == ru && !loops)) continue;
                         const unsigned off = (unsigned)(j - lo);
-                        if (use_win && off < (unsigned)kWin) atomicAdd(&s_win[off], rs);
-                        else far_add(jr[v], rs);
+                        if (rq != 0 && jr[v] >= 0 && off < (unsigned)kWin) atomicAdd(&s_win[off], rq);
+                        else seg_far_add(jr[v], rs);
                     }
                 }
             }
@@ -834,13 +1068,13 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
             if (!small) continue;
             const int inc = warp_inclusive_scan(dsm);
             const int total = __shfl_sync(kFull, inc, 31);
-            const int64_t rbase = ebeg - (inc - dsm);   // link e of the batch sits at col_push[rbase + e]
+            const int rbase = (int)ebeg - (inc - dsm);   // link e of the batch sits at col_push[rbase + e]
             s_off[w][lane + 1] = INT_MAX;
             __syncwarp();
             if (dsm > 0) {
                 const int pos = __popc(small & lanemask_lt());
                 s_off[w][pos] = inc - dsm;
-                s_rec[w][pos] = make_int4((int)(uint32_t)(uint64_t)rbase, (int)((uint64_t)rbase >> 32), eu, __float_as_int(es));
+                s_rec[w][pos] = make_int4(rbase, eu, __float_as_int(es), eq);
             }
             if (lane == 0) s_off[w][__popc(small)] = total;
             __syncwarp();
@@ -853,7 +1087,7 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                 // to the next link crosses at most one entry boundary
                 int next = s_off[w][k + 1];
                 int4 rec = s_rec[w][k];
-                int32_t jr[kPushVT], uu[kPushVT];
+                int32_t jr[kPushVT], uu[kPushVT], qq[kPushVT];
                 float ss[kPushVT];
 #pragma unroll
                 for (int v = 0; v < kPushVT; v++) {
@@ -861,16 +1095,17 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                     jr[v] = 0;
                     uu[v] = 0;
                     ss[v] = 0.f;
+                    qq[v] = 0;
                     if (e < total) {
                         if (e >= next) {
                             ++k;
                             next = s_off[w][k + 1];
                             rec = s_rec[w][k];
                         }
-                        const int64_t row = (int64_t)(((uint64_t)(uint32_t)rec.y << 32) | (uint32_t)rec.x);
-                        jr[v] = ld_stream(col_push + row + e, stream);
-                        uu[v] = rec.z;
-                        ss[v] = __int_as_float(rec.w);
+                        jr[v] = ld_stream(col_push + rec.x + e, stream);
+                        uu[v] = rec.y;
+                        ss[v] = __int_as_float(rec.z);
+                        qq[v] = rec.w;
                     }
                 }
 #pragma unroll
@@ -878,17 +1113,27 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                     const int32_t j = jr[v] & 0x7fffffff;
                     if (e0 + v >= total || (j == uu[v] && !loops)) continue;
                     const unsigned off = (unsigned)(j - lo);
-                    if (use_win && off < (unsigned)kWin) atomicAdd(&s_win[off], ss[v]);
-                    else far_add(jr[v], ss[v]);
+                    if (qq[v] != 0 && jr[v] >= 0 && off < (unsigned)kWin) atomicAdd(&s_win[off], qq[v]);
+                    else seg_far_add(jr[v], ss[v]);
                 }
             }
             __syncwarp();
         }
         __syncthreads();
+        // the segment's hub integers into the FP32 hub cache (each slot by one thread)
+        for (int q = tid; q < kHubSlots; q += 256) {
+            const int v = s_hint[q];
+            if (v != 0) {
+                s_hacc[q] += (float)v * hub_unit;
+                s_hint[q] = 0;
+            }
+        }
         if (use_win) {
             for (int q = tid; q < kWin / 4; q += 256) {
-                const float4 v = reinterpret_cast<const float4 *>(s_win)[q];
-                if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) red_keep_v4(F + lo + 4 * q, v, keep);
+                const int4 v = reinterpret_cast<const int4 *>(s_win)[q];
+                if (v.x != 0 || v.y != 0 || v.z != 0 || v.w != 0)
+                    red_keep_v4(F + lo + 4 * q, make_float4((float)v.x * win_unit, (float)v.y * win_unit,
+                                                            (float)v.z * win_unit, (float)v.w * win_unit), keep);
             }
             __syncthreads();
         }
@@ -942,31 +1187,64 @@ __global__ void k_scale(const double *v, const float2 *c, int32_t n, float2 *y) 
         y[i] = df_mul(df_from(v[i]), c[i]);
 }
 
-// Power-iteration set-up: c[j] = d / out_j (0 if dangling), B and X_0 = 0 as double-float, y_0 = 0.
-__global__ void k_pi_init(const double *B, const int32_t *out_info, int32_t n, double d, float2 *Bdf, float2 *c,
-                          float2 *X, float2 *y0) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t o = out_info[i] & 0x7fffffff;
-        c[i] = df_from(o ? d / (double)o : 0.0);
-        Bdf[i] = df_from(B[i]);
-        X[i] = make_float2(0.f, 0.f);
-        y0[i] = make_float2(0.f, 0.f);
-    }
-}
-
 __global__ void k_df_to_double(const float2 *X, int32_t n, double *out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = df_to(X[i]);
 }
 
-// partial[c] = sum of y over the in-links of heavy-row chunk c
+// Accumulation types of the pull kernels: the gathered value y and the row sums are FP32
+// (power iteration's increments), double-float (the exact residual) or FP64 (power iteration in
+// FP64). Heavy-row chunk sums are always formed in the Wide type (double-float for the FP32 and
+// double-float values, FP64 for FP64) and narrowed when the row is finished.
+struct AccDF {
+    using V = float2;
+    using Wide = AccDF;
+    __device__ static V zero() { return make_float2(0.f, 0.f); }
+    __device__ static V add(V a, V b) { return df_add(a, b); }
+    __device__ static V shfl_up(V v, int off) {
+        return make_float2(__shfl_up_sync(kFull, v.x, off), __shfl_up_sync(kFull, v.y, off));
+    }
+    __device__ static V shfl(V v, int src) { return make_float2(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src)); }
+    __device__ static V shfl_xor(V v, int o) {
+        return make_float2(__shfl_xor_sync(kFull, v.x, o), __shfl_xor_sync(kFull, v.y, o));
+    }
+    __device__ static float2 widen(V v) { return v; }
+    __device__ static V narrow(float2 w) { return w; }
+};
+struct AccF32 {
+    using V = float;
+    using Wide = AccDF;
+    __device__ static V zero() { return 0.f; }
+    __device__ static V add(V a, V b) { return a + b; }
+    __device__ static V shfl_up(V v, int off) { return __shfl_up_sync(kFull, v, off); }
+    __device__ static V shfl(V v, int src) { return __shfl_sync(kFull, v, src); }
+    __device__ static V shfl_xor(V v, int o) { return __shfl_xor_sync(kFull, v, o); }
+    __device__ static float2 widen(V v) { return make_float2(v, 0.f); }
+    __device__ static V narrow(float2 w) { return w.x + w.y; }
+};
+struct AccF64 {
+    using V = double;
+    using Wide = AccF64;
+    __device__ static V zero() { return 0.0; }
+    __device__ static V add(V a, V b) { return a + b; }
+    __device__ static V shfl_up(V v, int off) { return __shfl_up_sync(kFull, v, off); }
+    __device__ static V shfl(V v, int src) { return __shfl_sync(kFull, v, src); }
+    __device__ static V shfl_xor(V v, int o) { return __shfl_xor_sync(kFull, v, o); }
+    __device__ static double widen(V v) { return v; }
+    __device__ static V narrow(double w) { return w; }
+};
+
+// partial[c] = sum of y over the in-links of heavy-row chunk c, in Acc's wide type
 constexpr int kHeavyPullUnroll = 8;
 
+template <class Acc>
 __global__ void k_pull_heavy(const int64_t *rp_in, const int32_t *col_in, const int32_t *heavy_rows,
                              const int32_t *chunk_off, const int32_t *chunk_row, int32_t n_chunks,
-                             const float2 *y0, const float2 *y1, const SolveCtl *ctl, int alternate,
-                             float2 *partial) {
-    const float2 *y = (alternate && (ctl->sweeps & 1)) ? y1 : y0;
+                             const typename Acc::V *y0, const typename Acc::V *y1, const SolveCtl *ctl, int alternate,
+                             typename Acc::Wide::V *partial) {
+    using V = typename Acc::V;
+    using W = typename Acc::Wide;
+    const V *y = (alternate && (ctl->sweeps & 1)) ? y1 : y0;
     const int lane = (int)lane_id();
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += nwarps) {
@@ -974,36 +1252,34 @@ __global__ void k_pull_heavy(const int64_t *rp_in, const int32_t *col_in, const 
         const int32_t row = heavy_rows[h];
         const int64_t b = rp_in[row] + (int64_t)(c - chunk_off[h]) * kPullChunk;
         const int64_t e = min(b + (int64_t)kPullChunk, rp_in[row + 1]);
-        float2 s = make_float2(0.f, 0.f);
+        typename W::V s = W::zero();
         // kHeavyPullUnroll index loads, then as many gathers, in flight before the additions
         for (int64_t k0 = b + lane; k0 < e; k0 += 32 * kHeavyPullUnroll) {
             int32_t j[kHeavyPullUnroll];
 #pragma unroll
             for (int v = 0; v < kHeavyPullUnroll; v++) j[v] = k0 + 32 * v < e ? __ldcs(col_in + k0 + 32 * v) : -1;
-            float2 val[kHeavyPullUnroll];
+            V val[kHeavyPullUnroll];
 #pragma unroll
-            for (int v = 0; v < kHeavyPullUnroll; v++) val[v] = j[v] >= 0 ? y[j[v]] : make_float2(0.f, 0.f);
+            for (int v = 0; v < kHeavyPullUnroll; v++) val[v] = j[v] >= 0 ? y[j[v]] : Acc::zero();
 #pragma unroll
-            for (int v = 0; v < kHeavyPullUnroll; v++) s = df_add(s, val[v]);
+            for (int v = 0; v < kHeavyPullUnroll; v++) s = W::add(s, Acc::widen(val[v]));
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float2 t;
-            t.x = __shfl_xor_sync(kFull, s.x, o);
-            t.y = __shfl_xor_sync(kFull, s.y, o);
-            s = df_add(s, t);
-        }
+        for (int o = 16; o > 0; o >>= 1) s = W::add(s, W::shfl_xor(s, o));
         if (lane == 0) partial[c] = s;
     }
 }
 
-enum { PULL_PI = 0, PULL_RESID = 1 };
+enum { PULL_RESID = 1, PULL_INC = 2, PULL_PI64 = 3 };
 
-// Row sums acc_i = sum_{j in in(i)} y_j (double-float) for 32 consecutive rows per warp, then:
-//   PULL_PI:    X'_i = B_i + acc_i, delta_i = |X'_i - X_i|, X_i = X'_i, y'_i = X'_i * c_i with
-//               c_i = d / out_i (all double-float); sum delta -> ctl->r, iteration count and the
-//               WHILE condition.
-//   PULL_RESID: F*_i = B_i + acc_i - H_i (FP64) -> F_i (as T); sum |F*| -> ctl->r.
+// Row sums acc_i = sum_{j in in(i)} y_j for 32 consecutive rows per warp (Acc's arithmetic), then:
+//   PULL_RESID (double-float): F*_i = B_i + acc_i - H_i (FP64) -> F_i (as T); sum |F*| -> ctl->r.
+//   PULL_INC   (FP32): power iteration in increment form, X_(k+1) - X_k = P (X_k - X_(k-1)):
+//               y_j = d (X_k - X_(k-1))_j / out_j, so acc_i is the next increment; X_i (FP64)
+//               += acc_i, y'_i = acc_i * c_i (c_i = d / out_i in FP32); sum |acc| ->
+//               ctl->r (PI's ||X_(k+1) - X_k||_1), iteration count and the WHILE condition.
+//   PULL_PI64  (FP64): X'_i = B_i + acc_i, delta_i = |X'_i - X_i|, X_i = X'_i, y'_i = X'_i * c_i
+//               (c_i = d / out_i in FP64); sum delta -> ctl->r, iteration count, WHILE condition.
 // Segmented sum over the links of 32 consecutive rows per warp: each lane takes kPullVT
 // contiguous links per round (kPullVT index loads, then kPullVT gathers in flight), forms a
 // segmented prefix over them, and one segmented scan across the 32 lanes joins rows that span
@@ -1011,23 +1287,25 @@ enum { PULL_PI = 0, PULL_RESID = 1 };
 // that runs past a round carries into the next.
 constexpr int kPullVT = 8;
 
-template <int MODE, class T>
+template <int MODE, class Acc, class T>
 __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in, const int32_t *__restrict__ col_in,
-                                              const float2 *y0, float2 *y1, int32_t n, const int32_t *heavy_rows,
-                                              const int32_t *heavy_chunk_off, const float2 *heavy_partial,
-                                              int32_t n_heavy, const double *__restrict__ B,
-                                              const float2 *__restrict__ Bdf, const float2 *__restrict__ cdf,
-                                              float2 *Xdf, const double *H, T *F, double *partials, SolveCtl *ctl,
+                                              const typename Acc::V *y0, typename Acc::V *y1, int32_t n,
+                                              const int32_t *heavy_rows, const int32_t *heavy_chunk_off,
+                                              const typename Acc::Wide::V *heavy_partial, int32_t n_heavy,
+                                              const double *__restrict__ B, const void *__restrict__ cvec, void *Xvec,
+                                              const double *H, T *F, double *partials, SolveCtl *ctl,
                                               cudaGraphConditionalHandle hcond, int set_cond) {
-    __shared__ float2 acc_s[8][32];
+    using V = typename Acc::V;
+    using W = typename Acc::Wide;
+    __shared__ V acc_s[8][32];
     __shared__ int s_off[8][33];
     __shared__ int64_t s_beg[8][32];
     __shared__ double scratch[32];
     const int lane = (int)lane_id(), warp = threadIdx.x >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const bool odd = (MODE == PULL_PI) && (ctl->sweeps & 1);
-    const float2 *y_in = odd ? y1 : y0;
-    float2 *y_out = odd ? const_cast<float2 *>(y0) : y1;
+    const bool odd = (MODE != PULL_RESID) && (ctl->sweeps & 1);
+    const V *y_in = odd ? y1 : y0;
+    V *y_out = odd ? const_cast<V *>(y0) : y1;
     const uint64_t stream = policy_evict_first();
     double sum = 0.0;
     float run = 0.f;
@@ -1053,9 +1331,9 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
         s_off[warp][lane] = inc - deg;
         if (lane == 31) s_off[warp][32] = total;
         s_beg[warp][lane] = beg - (inc - deg);      // link e of row k sits at s_beg[k] + e
-        acc_s[warp][lane] = make_float2(0.f, 0.f);
+        acc_s[warp][lane] = Acc::zero();
         __syncwarp();
-        float2 carry = make_float2(0.f, 0.f);
+        V carry = Acc::zero();
         int carry_row = -1;
         for (int e0 = 0; e0 < total; e0 += 32 * kPullVT) {
             const int first = e0 + lane * kPullVT;
@@ -1064,6 +1342,7 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
             for (int step = 16; step > 0; step >>= 1)
                 if (s_off[warp][k + step] <= first) k += step;
             int next = s_off[warp][k + 1];
+            int64_t base = s_beg[warp][k];          // reloaded only when the row changes
             int key[kPullVT];
             int32_t j[kPullVT];
 #pragma unroll
@@ -1071,34 +1350,33 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
                 const int e = first + v;
                 key[v] = 64 + lane;                 // past the end: a key no row uses
                 if (e < total) {
-                    while (e >= next) next = s_off[warp][++k + 1];
+                    while (e >= next) {
+                        next = s_off[warp][++k + 1];
+                        base = s_beg[warp][k];
+                    }
                     key[v] = k;
-                    j[v] = ld_stream(col_in + s_beg[warp][k] + e, stream);
+                    j[v] = ld_stream(col_in + base + e, stream);
                 }
             }
-            float2 val[kPullVT];
+            V val[kPullVT];
 #pragma unroll
-            for (int v = 0; v < kPullVT; v++) val[v] = key[v] < 64 ? y_in[j[v]] : make_float2(0.f, 0.f);
+            for (int v = 0; v < kPullVT; v++) val[v] = key[v] < 64 ? y_in[j[v]] : Acc::zero();
             // the previous round's carry joins the first link of its row
-            if (lane == 0 && key[0] == carry_row) val[0] = df_add(val[0], carry);
+            if (lane == 0 && key[0] == carry_row) val[0] = Acc::add(val[0], carry);
             // segmented prefix within the lane
 #pragma unroll
             for (int v = 1; v < kPullVT; v++)
-                if (key[v] == key[v - 1]) val[v] = df_add(val[v - 1], val[v]);
+                if (key[v] == key[v - 1]) val[v] = Acc::add(val[v - 1], val[v]);
             // segmented scan of the lanes' last segments (keys never decrease across lanes)
-            float2 sv = val[kPullVT - 1];
+            V sv = val[kPullVT - 1];
             const int sk = key[kPullVT - 1];
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
-                float2 ov;
-                ov.x = __shfl_up_sync(kFull, sv.x, off);
-                ov.y = __shfl_up_sync(kFull, sv.y, off);
+                const V ov = Acc::shfl_up(sv, off);
                 const int ok = __shfl_up_sync(kFull, sk, off);
-                if (lane >= off && ok == sk) sv = df_add(ov, sv);
+                if (lane >= off && ok == sk) sv = Acc::add(ov, sv);
             }
-            float2 cin;
-            cin.x = __shfl_up_sync(kFull, sv.x, 1);
-            cin.y = __shfl_up_sync(kFull, sv.y, 1);
+            const V cin = Acc::shfl_up(sv, 1);
             const int ck = __shfl_up_sync(kFull, sk, 1);
             const bool join = lane > 0 && ck == key[0];
             // finished rows: the row's last link writes its sum
@@ -1106,14 +1384,14 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
             for (int v = 0; v < kPullVT; v++) {
                 const int e = first + v;
                 if (key[v] >= 64) continue;
-                float2 fin = (join && key[v] == key[0]) ? df_add(cin, val[v]) : val[v];
+                const V fin = (join && key[v] == key[0]) ? Acc::add(cin, val[v]) : val[v];
                 if (e + 1 == s_off[warp][key[v] + 1]) acc_s[warp][key[v]] = fin;
                 val[v] = fin;
             }
             // carry for the next round: the round's last link, when its row goes on
             const int last_e = min(e0 + 32 * kPullVT, total) - 1;
             const int owner_lane = (last_e - e0) / kPullVT, owner_v = (last_e - e0) % kPullVT;
-            float2 cv = make_float2(0.f, 0.f);
+            V cv = Acc::zero();
             int crow = -1;
 #pragma unroll
             for (int v = 0; v < kPullVT; v++)
@@ -1121,15 +1399,14 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
                     cv = val[v];
                     crow = key[v];
                 }
-            cv.x = __shfl_sync(kFull, cv.x, owner_lane);
-            cv.y = __shfl_sync(kFull, cv.y, owner_lane);
+            cv = Acc::shfl(cv, owner_lane);
             crow = __shfl_sync(kFull, crow, owner_lane);
             const bool goes_on = crow < 64 && last_e + 1 < s_off[warp][crow + 1];
-            carry = goes_on ? cv : make_float2(0.f, 0.f);
+            carry = goes_on ? cv : Acc::zero();
             carry_row = goes_on ? crow : -1;
         }
         __syncwarp();
-        float2 a = acc_s[warp][lane];
+        V a = acc_s[warp][lane];
         __syncwarp();
         if (heavy) {
             int lo = 0, hi = n_heavy - 1;
@@ -1137,20 +1414,26 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
                 const int mid = (lo + hi) >> 1;
                 if (heavy_rows[mid] < row) lo = mid + 1; else hi = mid;
             }
-            a = make_float2(0.f, 0.f);
-            for (int c = heavy_chunk_off[lo]; c < heavy_chunk_off[lo + 1]; c++) a = df_add(a, heavy_partial[c]);
+            typename W::V wa = W::zero();
+            for (int c = heavy_chunk_off[lo]; c < heavy_chunk_off[lo + 1]; c++) wa = W::add(wa, heavy_partial[c]);
+            a = Acc::narrow(wa);
         }
         if (valid) {
-            if (MODE == PULL_PI) {
-                const float2 xn = df_add(Bdf[row], a);
-                const float2 dx = df_add(xn, df_neg(Xdf[row]));
-                run += fabsf(dx.x + dx.y);
-                Xdf[row] = xn;
-                y_out[row] = df_mul(xn, cdf[row]);
-            } else {
-                const double fs = B[row] + df_to(a) - H[row];
+            if constexpr (MODE == PULL_RESID) {
+                const double fs = B[row] + df_to(AccDF::widen(a)) - H[row];
                 F[row] = (T)fs;
                 sum += fabs(fs);
+            } else if constexpr (MODE == PULL_INC) {
+                double *X = static_cast<double *>(Xvec);
+                X[row] += (double)a;
+                run += fabsf(a);
+                y_out[row] = a * static_cast<const float *>(cvec)[row];
+            } else {
+                double *X = static_cast<double *>(Xvec);
+                const double xn = B[row] + a;
+                sum += fabs(xn - X[row]);
+                X[row] = xn;
+                y_out[row] = xn * static_cast<const double *>(cvec)[row];
             }
             if (++runs == 16) {
                 sum += (double)run;
@@ -1165,7 +1448,7 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
     if (threadIdx.x == 0) {
         ctl->ticket = 0;
         ctl->r = tot;
-        if (MODE == PULL_PI) {
+        if (MODE != PULL_RESID) {
             const int it = ctl->sweeps + 1;
             ctl->sweeps = it;
             if (set_cond) ctl->body_runs++;
@@ -1173,6 +1456,62 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
             ctl->done = cont ? 0 : 1;
             if (set_cond) cudaGraphSetConditional(hcond, cont ? 1u : 0u);
         }
+    }
+}
+
+// Power iteration in increment form, set-up: c_i = d / out_i (FP32, 0 for a dangling node),
+// X_1 = B (the first iteration from X_0 = 0, FP64), y = c * B (the first increment
+// X_1 - X_0 = B, scaled for the next pull); r = ||B||_1, one iteration done, and the halfway
+// point of a refined solve (as the D-iteration's: sqrt(tol * r) when tol is well below r).
+__global__ void k_pi_inc_init(const double *B, const int32_t *out_info, int32_t n, double d, float *c, double *X,
+                              float *y, double *partials, SolveCtl *ctl) {
+    __shared__ double scratch[32];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = out_info[i] & 0x7fffffff;
+        const float ci = o ? (float)(d / (double)o) : 0.f;
+        const double b = B[i];
+        c[i] = ci;
+        X[i] = b;
+        y[i] = (float)b * ci;
+        s += fabs(b);
+    }
+    double tot;
+    if (!finish_sum(s, partials, ctl, scratch, tot)) return;
+    if (threadIdx.x == 0) {
+        ctl->ticket = 0;
+        ctl->r = tot;
+        ctl->sweeps = 1;
+        if (ctl->split && ctl->tol < kSplitBelow * tot) {
+            ctl->tol = sqrt(ctl->tol * tot);
+            ctl->halfway = 1;
+        }
+        ctl->split = 0;
+        ctl->done = (tot > ctl->tol && 1 < ctl->max_sweeps) ? 0 : 1;
+    }
+}
+
+// Continuation of the increment form from an exact residual F* = B + P.X - X (the next
+// increment, computed exactly): X += F*, y = c * F*, one more iteration; y goes to the buffer
+// the next pull reads (it alternates on the iteration count).
+__global__ void k_pi_inc_resume(const float *Fs, int32_t n, const float *c, double *X, float *y0, float *y1,
+                                SolveCtl *ctl) {
+    const int it = ctl->sweeps + 1;
+    float *y = (it & 1) ? y1 : y0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float f = Fs[i];
+        X[i] += (double)f;
+        y[i] = f * c[i];
+    }
+}
+
+// FP64 power iteration set-up: c_i = d / out_i (FP64), X_0 = 0, y_0 = 0.
+__global__ void k_pi64_init(const int32_t *out_info, int32_t n, double d, double *c, double *X, double *y0) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = out_info[i] & 0x7fffffff;
+        c[i] = o ? d / (double)o : 0.0;
+        X[i] = 0.0;
+        y0[i] = 0.0;
     }
 }
 
@@ -1246,7 +1585,7 @@ static Launch launch_shape(const di_graph *g) {
     l.push_blocks = sms * (occ > 0 ? occ : 1);
     DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_win, 256, 0));
     l.win_blocks = sms * (occ > 0 ? occ : 1);
-    DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pull<PULL_PI, T>, 256, 0));
+    DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pull<PULL_RESID, AccDF, T>, 256, 0));
     l.pull_blocks = sms * (occ > 0 ? occ : 1);
     const int64_t n = g->n;
     auto cap = [&](int64_t want, int64_t lim) { return (int)(want < 1 ? 1 : (want < lim ? want : lim)); };
@@ -1260,32 +1599,65 @@ static Launch launch_shape(const di_graph *g) {
     return l;
 }
 
-template <class T>
-static void ensure_workspace(di_graph *g) {
+// The solve workspace's buffers in a fixed order, each with its size for a fluid of
+// `fb` bytes per value (4: FP32, 8: FP64); `take(buffer, bytes)` allocates, binds or counts it.
+template <class Take>
+static void solve_layout(di_graph *g, Workspace &ws, size_t fb, Take &&take) {
+    const size_t n = (size_t)g->n, nh = (size_t)g->n_heavy_out + 1;
+    take(ws.F, fb * (n + 8));   // padded: window flushes write four floats at a time
+    take(ws.chunks, sizeof(int4) * (n / kSelChunk + 2));
+    take(ws.H, sizeof(double) * n);
+    take(ws.B, sizeof(double) * n);
+    take(ws.front_id, sizeof(int32_t) * n);
+    take(ws.front_s, fb * n);
+    take(ws.heavy_id, sizeof(int32_t) * nh);
+    take(ws.heavy_s, fb * nh);
+    take(ws.heavy_cstart, sizeof(int32_t) * nh);
+    // a heavy node has at most out / chunk + 1 chunks, chunk >= kHeavyChunkMin
+    take(ws.heavy_chunk, sizeof(int32_t) * ((size_t)g->L / kHeavyChunkMin + nh));
+    take(ws.partials, sizeof(double) * kReduceBlocks);
+    take(ws.ctl, sizeof(SolveCtl));
+    take(ws.y0, sizeof(float2) * n);   // also stages an FP64 vector (resume, final fluid)
+    take(ws.y1, sizeof(float2) * n);
+    take(ws.Bdf, sizeof(float2) * n);
+    take(ws.cdf, sizeof(float2) * n);
+    take(ws.Xdf, sizeof(float2) * n);
+}
+
+size_t solve_workspace_bytes(di_graph *g, int fluid) {
+    Carve c;
+    solve_layout(g, g->ws, fluid == DI_FLUID_F64 ? 8 : 4, [&](DevBuf &b, size_t n) { c.take(b, n); });
+    return c.used;
+}
+
+// Attaches a caller's workspace (NULL: back to library allocations). The library's own solve
+// buffers are freed at once, and the next solve lays its buffers out in the new memory.
+void solve_workspace_attach(di_graph *g, void *ext, size_t bytes) {
     Workspace &ws = g->ws;
+    ws.reset_graphs();   // the captured sweep graphs hold the old addresses
+    solve_layout(g, ws, 8, [&](DevBuf &b, size_t) { b.release(); });
+    ws.ext = ext;
+    ws.ext_bytes = ext ? bytes : 0;
+    ws.fluid = -1;
+    ws.cdf_d = -1.0;
+}
+
+template <class T>
+static void ensure_workspace(di_graph *g, Workspace &ws) {
     const int fl = sizeof(T) == 4 ? DI_FLUID_F32 : DI_FLUID_F64;
     if (ws.fluid == fl) return;
     ws.reset_graphs();
-    const size_t n = (size_t)g->n;
-    ws.F.ensure(sizeof(T) * (n + 8));   // padded: window flushes write four floats at a time
-    ws.chunks.ensure(sizeof(int4) * (n / kSelChunk + 2));
-    ws.H.ensure(sizeof(double) * n);
-    ws.B.ensure(sizeof(double) * n);
-    ws.front_id.ensure(sizeof(int32_t) * n);
-    ws.front_s.ensure(sizeof(T) * n);
-    ws.heavy_id.ensure(sizeof(int32_t) * (size_t)(g->n_heavy_out + 1));
-    ws.heavy_s.ensure(sizeof(T) * (size_t)(g->n_heavy_out + 1));
-    ws.heavy_cstart.ensure(sizeof(int32_t) * (size_t)(g->n_heavy_out + 1));
-    // a heavy node has at most out / kHeavyChunk + 1 chunks
-    ws.heavy_chunk.ensure(sizeof(int32_t) * (size_t)(g->L / kHeavyChunk + g->n_heavy_out + 1));
-    ws.partials.ensure(sizeof(double) * kReduceBlocks);
-    ws.ctl.ensure(sizeof(SolveCtl));
-    ws.y0.ensure(sizeof(float2) * n);
-    ws.y1.ensure(sizeof(float2) * n);
-    ws.Bdf.ensure(sizeof(float2) * n);
-    ws.cdf.ensure(sizeof(float2) * n);
+    if (ws.ext) {
+        const size_t need = solve_workspace_bytes(g, fl);
+        DI_REQUIRE(ws.ext_bytes >= need, DI_ERR_INVALID_ARG,
+                   "the attached solve workspace holds %zu bytes; %s fluid needs %zu (di_workspace_size)",
+                   ws.ext_bytes, fl == DI_FLUID_F64 ? "FP64" : "FP32", need);
+        Carve c{static_cast<char *>(ws.ext), ws.ext_bytes};
+        solve_layout(g, ws, sizeof(T), [&](DevBuf &b, size_t n) { c.take(b, n); });
+    } else {
+        solve_layout(g, ws, sizeof(T), [&](DevBuf &b, size_t n) { b.ensure(n); });
+    }
     ws.cdf_d = -1.0;
-    ws.Xdf.ensure(sizeof(float2) * n);
     if (!ws.capture_stream) DI_CHECK_CUDA(cudaStreamCreateWithFlags(&ws.capture_stream, cudaStreamNonBlocking));
     if (!ws.out_stream) {
         DI_CHECK_CUDA(cudaStreamCreateWithFlags(&ws.out_stream, cudaStreamNonBlocking));
@@ -1297,42 +1669,56 @@ static void ensure_workspace(di_graph *g) {
 }
 
 template <class T>
-static void launch_sweep_body(di_graph *g, const Launch &l, cudaStream_t s, cudaGraphConditionalHandle h, int set_cond,
-                              KernelClock *kc) {
-    Workspace &ws = g->ws;
+static void launch_sweep_body(di_graph *g, Workspace &ws, const Launch &l, cudaStream_t s, cudaGraphConditionalHandle h, int set_cond,
+                              KernelClock *kc, int parts) {
     SolveCtl *ctl = ws.ctl.as<SolveCtl>();
     KernelClock none(false, s);
     KernelClock &c = kc ? *kc : none;
-    c.run(KC_SELECT, 1, [&] {
-        k_select<T><<<l.sel_blocks, 256, 0, s>>>(ws.F.as<T>(), ws.H.as<double>(), g->out_info.as<int32_t>(), g->n,
-                                                  ctl, ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
-                                                  ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(),
-                                                  ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(),
-                                                  ws.chunks.as<int4>());
-    });
-    c.run(KC_PUSH, 1, [&] {
-        if (sizeof(T) == 4) {
-            k_push_win<<<l.win_blocks, 256, 0, s>>>(
-                ws.front_id.as<int32_t>(), ws.front_s.as<float>(), ws.heavy_id.as<int32_t>(), ws.heavy_s.as<float>(),
-                ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(), g->rp_out.as<int64_t>(),
-                g->col_push.as<int32_t>(), ws.chunks.as<int4>(), g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl);
-        } else {
-            k_push<T><<<l.push_blocks, 256, 0, s>>>(ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
-                                                    ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(),
-                                                    ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(),
-                                                    g->rp_out.as<int64_t>(), g->col_out.as<int32_t>(), ws.F.as<T>(),
-                                                    ctl);
-        }
-    });
-    c.run(KC_REDUCE, 1, [&] {
-        k_reduce<T><<<l.red_blocks, 256, 0, s>>>(ws.F.as<T>(), g->n, ws.partials.as<double>(), ctl, h, set_cond);
-    });
+    // a sweep is `parts` selections, each over a kSelChunk-aligned part of the node range with r
+    // taken again before it (one part: r once per sweep, the paper's rule)
+    const int64_t n = g->n;
+    const int64_t chunks = (n + kSelChunk - 1) / kSelChunk;
+    const int64_t per = (chunks + parts - 1) / parts;
+    const PushTune tune = g->tune_single;
+    for (int p = 0; p < parts; p++) {
+        const int64_t lo = std::min(n, p * per * kSelChunk), hi = std::min(n, (p + 1) * per * kSelChunk);
+        const bool last = p == parts - 1;
+        const int64_t want = (hi - lo + kSelChunk - 1) / kSelChunk;
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, l.sel_blocks));
+        c.run(KC_SELECT, 1, [&] {
+            k_select<T><<<blocks, 256, 0, s>>>(ws.F.as<T>(), ws.H.as<double>(), g->out_info.as<int32_t>(), g->n, ctl,
+                                               ws.front_id.as<int32_t>(), ws.front_s.as<T>(), ws.heavy_id.as<int32_t>(),
+                                               ws.heavy_s.as<T>(), ws.heavy_cstart.as<int32_t>(),
+                                               ws.heavy_chunk.as<int32_t>(), ws.chunks.as<int4>(),
+                                               g->win_qbits - kWinHeadBits, (int32_t)lo, (int32_t)hi, last ? 1 : 0,
+                                               tune.heavy, tune.chunk);
+        });
+        c.run(KC_PUSH, 1, [&] {
+            if (sizeof(T) == 4) {
+                k_push_win<<<l.win_blocks, 256, 0, s>>>(
+                    ws.front_id.as<int32_t>(), ws.front_s.as<float>(), ws.heavy_id.as<int32_t>(), ws.heavy_s.as<float>(),
+                    ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(), g->rp_out.as<int64_t>(),
+                    g->col_push.as<int32_t>(), ws.chunks.as<int4>(), g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl,
+                    1 << g->win_qbits, g->win_qbits - g->hub_qbits, 1 << g->hub_qbits, tune.row,
+                    tune.chunk);
+            } else {
+                k_push<T><<<l.push_blocks, 256, 0, s>>>(ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
+                                                        ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(),
+                                                        ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(),
+                                                        g->rp_out.as<int64_t>(), g->col_out.as<int32_t>(), ws.F.as<T>(),
+                                                        ctl, tune.chunk);
+            }
+        });
+        c.run(KC_REDUCE, 1, [&] {
+            k_reduce<T><<<l.red_blocks, 256, 0, s>>>(ws.F.as<T>(), g->n, ws.partials.as<double>(), ctl, h, set_cond,
+                                                     last ? 1 : 0);
+        });
+    }
 }
 
 // Graph: WHILE(cond, default 1 at every launch) { select; push; reduce -> cond }.
 template <class T>
-static void build_sweep_graph(di_graph *g, const Launch &l) {
-    Workspace &ws = g->ws;
+static void build_sweep_graph(di_graph *g, Workspace &ws, const Launch &l, int parts) {
     cudaGraph_t graph;
     DI_CHECK_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle h;
@@ -1346,36 +1732,56 @@ static void build_sweep_graph(di_graph *g, const Launch &l) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     DI_CHECK_CUDA(cudaStreamBeginCaptureToGraph(ws.capture_stream, body, nullptr, nullptr, 0,
                                                 cudaStreamCaptureModeThreadLocal));
-    launch_sweep_body<T>(g, l, ws.capture_stream, h, 1, nullptr);
+    launch_sweep_body<T>(g, ws, l, ws.capture_stream, h, 1, nullptr, parts);
     cudaGraph_t captured;
     DI_CHECK_CUDA(cudaStreamEndCapture(ws.capture_stream, &captured));
     DI_CHECK_CUDA(cudaGraphInstantiate(&ws.sweep_exec, graph, 0));
     DI_CHECK_CUDA(cudaGraphDestroy(graph));
+    ws.sweep_parts = parts;
+    ws.sweep_tune = g->tune_single;
 }
 
-template <class T>
-static void launch_pi_body(di_graph *g, const Launch &l, cudaStream_t s, cudaGraphConditionalHandle h, int set_cond) {
-    Workspace &ws = g->ws;
+// One power iteration: the heavy rows' chunk sums, then the pull. fp64: X_(k+1) = B + P X_k in
+// FP64; otherwise the FP32 increment form.
+static void launch_pi_body(di_graph *g, Workspace &ws, const Launch &l, cudaStream_t s, cudaGraphConditionalHandle h, int set_cond,
+                           bool fp64, KernelClock *kc) {
     SolveCtl *ctl = ws.ctl.as<SolveCtl>();
+    KernelClock none(false, s);
+    KernelClock &c = kc ? *kc : none;
     if (g->n_heavy_in_chunks > 0) {
         int blocks = (int)((g->n_heavy_in_chunks + 7) / 8);
         if (blocks > g->dev.sms * 8) blocks = g->dev.sms * 8;
-        k_pull_heavy<<<blocks, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(),
-                                            g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(),
-                                            g->heavy_in_chunk_row.as<int32_t>(), g->n_heavy_in_chunks,
-                                            ws.y0.as<float2>(), ws.y1.as<float2>(), ctl, 1,
-                                            g->heavy_in_partial.as<float2>());
+        c.run(KC_SELECT, 1, [&] {
+            if (fp64)
+                k_pull_heavy<AccF64><<<blocks, 256, 0, s>>>(
+                    g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), g->heavy_in_rows.as<int32_t>(),
+                    g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_chunk_row.as<int32_t>(), g->n_heavy_in_chunks,
+                    ws.y0.as<double>(), ws.y1.as<double>(), ctl, 1, g->heavy_in_partial.as<double>());
+            else
+                k_pull_heavy<AccF32><<<blocks, 256, 0, s>>>(
+                    g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), g->heavy_in_rows.as<int32_t>(),
+                    g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_chunk_row.as<int32_t>(), g->n_heavy_in_chunks,
+                    ws.y0.as<float>(), ws.y1.as<float>(), ctl, 1, g->heavy_in_partial.as<float2>());
+        });
     }
-    k_pull<PULL_PI, T><<<l.pull_blocks, 256, 0, s>>>(
-        g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<float2>(), ws.y1.as<float2>(), g->n,
-        g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<float2>(),
-        g->n_heavy_in, ws.B.as<double>(), ws.Bdf.as<float2>(), ws.cdf.as<float2>(), ws.Xdf.as<float2>(),
-        ws.H.as<double>(), (T *)nullptr, ws.partials.as<double>(), ctl, h, set_cond);
+    c.run(KC_PUSH, 1, [&] {
+        if (fp64)
+            k_pull<PULL_PI64, AccF64, double><<<l.pull_blocks, 256, 0, s>>>(
+                g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<double>(), ws.y1.as<double>(), g->n,
+                g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<double>(),
+                g->n_heavy_in, ws.B.as<double>(), ws.Bdf.p, ws.Xdf.p, nullptr, (double *)nullptr,
+                ws.partials.as<double>(), ctl, h, set_cond);
+        else
+            k_pull<PULL_INC, AccF32, float><<<l.pull_blocks, 256, 0, s>>>(
+                g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<float>(), ws.y1.as<float>(), g->n,
+                g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<float2>(),
+                g->n_heavy_in, ws.B.as<double>(), ws.Bdf.p, ws.H.p, nullptr, (float *)nullptr,
+                ws.partials.as<double>(), ctl, h, set_cond);
+    });
 }
 
-template <class T>
-static void build_pi_graph(di_graph *g, const Launch &l) {
-    Workspace &ws = g->ws;
+// Graph: WHILE(cond) { [heavy chunk sums;] pull -> cond }, one per mode.
+static void build_pi_graph(di_graph *g, Workspace &ws, const Launch &l, bool fp64) {
     cudaGraph_t graph;
     DI_CHECK_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle h;
@@ -1389,18 +1795,18 @@ static void build_pi_graph(di_graph *g, const Launch &l) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     DI_CHECK_CUDA(cudaStreamBeginCaptureToGraph(ws.capture_stream, body, nullptr, nullptr, 0,
                                                 cudaStreamCaptureModeThreadLocal));
-    launch_pi_body<T>(g, l, ws.capture_stream, h, 1);
+    launch_pi_body(g, ws, l, ws.capture_stream, h, 1, fp64, nullptr);
     cudaGraph_t captured;
     DI_CHECK_CUDA(cudaStreamEndCapture(ws.capture_stream, &captured));
     DI_CHECK_CUDA(cudaGraphInstantiate(&ws.pi_exec, graph, 0));
     DI_CHECK_CUDA(cudaGraphDestroy(graph));
+    ws.pi_fp64 = fp64 ? 1 : 0;
 }
 
 // F <- B + P.H - H (as T), ctl->r <- ||F*||_1 (exact residual of the history H: FP64 H and
 // B, double-float link sums). Launches 2 or 3 kernels.
 template <class T>
-static void launch_refine(di_graph *g, const Launch &l, double d, cudaStream_t s) {
-    Workspace &ws = g->ws;
+static void launch_refine(di_graph *g, Workspace &ws, const Launch &l, double d, cudaStream_t s) {
     SolveCtl *ctl = ws.ctl.as<SolveCtl>();
     if (ws.cdf_d != d) {   // d / out is formed once per damping factor
         k_link_weight<<<l.ew_blocks, 256, 0, s>>>(g->out_info.as<int32_t>(), g->n, d, ws.cdf.as<float2>());
@@ -1410,23 +1816,23 @@ static void launch_refine(di_graph *g, const Launch &l, double d, cudaStream_t s
     if (g->n_heavy_in_chunks > 0) {
         int blocks = (int)((g->n_heavy_in_chunks + 7) / 8);
         if (blocks > g->dev.sms * 8) blocks = g->dev.sms * 8;
-        k_pull_heavy<<<blocks, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(),
-                                            g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(),
-                                            g->heavy_in_chunk_row.as<int32_t>(), g->n_heavy_in_chunks,
-                                            ws.y0.as<float2>(), ws.y1.as<float2>(), ctl, 0,
-                                            g->heavy_in_partial.as<float2>());
+        k_pull_heavy<AccDF><<<blocks, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(),
+                                                   g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(),
+                                                   g->heavy_in_chunk_row.as<int32_t>(), g->n_heavy_in_chunks,
+                                                   ws.y0.as<float2>(), ws.y1.as<float2>(), ctl, 0,
+                                                   g->heavy_in_partial.as<float2>());
     }
-    k_pull<PULL_RESID, T><<<l.pull_blocks, 256, 0, s>>>(
+    k_pull<PULL_RESID, AccDF, T><<<l.pull_blocks, 256, 0, s>>>(
         g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<float2>(), ws.y1.as<float2>(), g->n,
         g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<float2>(),
-        g->n_heavy_in, ws.B.as<double>(), ws.Bdf.as<float2>(), ws.cdf.as<float2>(), ws.Xdf.as<float2>(),
-        ws.H.as<double>(), ws.F.as<T>(), ws.partials.as<double>(), ctl, cudaGraphConditionalHandle(0), 0);
+        g->n_heavy_in, ws.B.as<double>(), nullptr, nullptr, ws.H.as<double>(), ws.F.as<T>(), ws.partials.as<double>(),
+        ctl, cudaGraphConditionalHandle(0), 0);
     DI_CHECK_CUDA(cudaGetLastError());
 }
 
-static void write_ctl(di_graph *g, double d, double tol, int schedule, int max_sweeps, int plain_loops,
+static void write_ctl(di_graph *g, Workspace &ws, double d, double tol, int schedule, int max_sweeps, int plain_loops,
                       cudaStream_t s, int track = 0, int split = 0) {
-    SolveCtl &c = *g->ws.ctl_host;
+    SolveCtl &c = *ws.ctl_host;
     memset(&c, 0, sizeof(c));
     c.plain_loops = plain_loops;
     c.track = track;
@@ -1437,11 +1843,11 @@ static void write_ctl(di_graph *g, double d, double tol, int schedule, int max_s
     c.schedule = schedule;
     c.max_sweeps = max_sweeps;
     c.last_selected = -1;
-    DI_CHECK_CUDA(cudaMemcpyAsync(g->ws.ctl.p, &c, sizeof(SolveCtl), cudaMemcpyHostToDevice, s));
+    DI_CHECK_CUDA(cudaMemcpyAsync(ws.ctl.p, &c, sizeof(SolveCtl), cudaMemcpyHostToDevice, s));
 }
 
-static void read_ctl(di_graph *g, cudaStream_t s) {
-    DI_CHECK_CUDA(cudaMemcpyAsync(g->ws.ctl_host, g->ws.ctl.p, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
+static void read_ctl(di_graph *g, Workspace &ws, cudaStream_t s) {
+    DI_CHECK_CUDA(cudaMemcpyAsync(ws.ctl_host, ws.ctl.p, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
     DI_CHECK_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -1467,12 +1873,11 @@ static bool async_copy_target(const void *p) {
 static bool ctl_split_expected(bool fp32, int refine) { return fp32 && refine; }
 
 template <class T>
-static void solve_impl(di_graph *g, const double *B, double d, double tol, int schedule, int max_sweeps, int refine,
+static void solve_impl(di_graph *g, Workspace &ws, const double *B, double d, double tol, int schedule, int max_sweeps, int refine,
                        int host_loop, int profile, int e_prediffuse, int plain_loops, double *X_out,
                        double *residual_out, di_solve_info *info, cudaStream_t s, const double *H0 = nullptr,
-                       const double *F0 = nullptr, double *F_out = nullptr) {
-    ensure_workspace<T>(g);
-    Workspace &ws = g->ws;
+                       const double *F0 = nullptr, double *F_out = nullptr, int parts = 1, int exact_r = 0) {
+    ensure_workspace<T>(g, ws);
     const Launch l = launch_shape<T>(g);
     SolveCtl *ctl = ws.ctl.as<SolveCtl>();
     to_device(ws.B.p, B, sizeof(double) * (size_t)g->n, s);
@@ -1480,7 +1885,7 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
     // FP32 sweeps from (0, B), up to and after their halfway refinement (see k_reduce: that
     // refinement comes before the fluid's rounding has grown comparable to tol). A refined
     // solve's final residual is exact in any case.
-    write_ctl(g, d, tol, schedule, max_sweeps, plain_loops, s, (sizeof(T) == 4 && refine && !H0) ? 1 : 0,
+    write_ctl(g, ws, d, tol, schedule, max_sweeps, plain_loops, s, (sizeof(T) == 4 && refine && !H0 && !exact_r) ? 1 : 0,
               (sizeof(T) == 4 && refine) ? 1 : 0);
     if (profile) host_loop = 1;
     KernelClock kc(profile != 0, s);
@@ -1507,37 +1912,65 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
                 k_resume_init<T><<<l.ew_blocks, 256, 0, s>>>(ws.B.as<double>(), stage, g->n, ws.F.as<T>(),
                                                              ws.H.as<double>(), ctl);
             });
-            if (!F0) kc.run(KC_REFINE, g->n_heavy_in_chunks > 0 ? 3 : 2, [&] { launch_refine<T>(g, l, d, s); });
+            if (!F0) kc.run(KC_REFINE, g->n_heavy_in_chunks > 0 ? 3 : 2, [&] { launch_refine<T>(g, ws, l, d, s); });
         }
         if (e_prediffuse) {
+            const PushTune tune = g->tune_single;
             for (size_t lv = 0; lv + 1 < g->e_level_off.size(); lv++) {
                 const int64_t at = g->e_level_off[lv], cnt = g->e_level_off[lv + 1] - at;
-                const int64_t want = (cnt + 255) / 256, lim = (int64_t)g->dev.sms * 8;
-                const int blocks = (int)(want < lim ? want : lim);
-                kc.run(KC_REFINE, 1, [&] {
-                    k_e_visit<T><<<blocks, 256, 0, s>>>(g->e_order.as<int32_t>() + at, (int32_t)cnt,
-                                                        g->out_info.as<int32_t>(), g->rp_out.as<int64_t>(),
-                                                        g->col_push.as<int32_t>(), g->hub_ids.as<int32_t>(),
-                                                        ws.F.as<T>(), ws.H.as<double>(), ctl);
-                });
+                if (sizeof(T) == 4 && cnt >= kELevelSelectMin) {
+                    // a large level: select by id chunks, then the sweep's windowed push
+                    const int64_t nchunk = (g->n + kSelChunk - 1) / kSelChunk;
+                    const int blocks = (int)std::min<int64_t>(nchunk, (int64_t)g->dev.sms * 4);
+                    kc.run(KC_SELECT, 1, [&] {
+                        k_e_select<<<blocks, 256, 0, s>>>(
+                            g->e_order.as<int32_t>() + at, (int32_t)cnt, ws.F.as<float>(), ws.H.as<double>(),
+                            g->out_info.as<int32_t>(), g->n, ctl, ws.front_id.as<int32_t>(), ws.front_s.as<float>(),
+                            ws.heavy_id.as<int32_t>(), ws.heavy_s.as<float>(), ws.heavy_cstart.as<int32_t>(),
+                            ws.heavy_chunk.as<int32_t>(), ws.chunks.as<int4>(), g->win_qbits - kWinHeadBits,
+                            tune.heavy, tune.chunk);
+                    });
+                    kc.run(KC_PUSH, 1, [&] {
+                        k_push_win<<<l.win_blocks, 256, 0, s>>>(
+                            ws.front_id.as<int32_t>(), ws.front_s.as<float>(), ws.heavy_id.as<int32_t>(),
+                            ws.heavy_s.as<float>(), ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(),
+                            g->rp_out.as<int64_t>(), g->col_push.as<int32_t>(), ws.chunks.as<int4>(),
+                            g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl, 1 << g->win_qbits, g->win_qbits - g->hub_qbits, 1 << g->hub_qbits, tune.row,
+                    tune.chunk);
+                    });
+                    kc.run(KC_REFINE, 1, [&] { k_front_reset<<<1, 1, 0, s>>>(ctl); });
+                } else {
+                    const int64_t want = (cnt + 255) / 256, lim = (int64_t)g->dev.sms * 8;
+                    const int blocks = (int)(want < lim ? want : lim);
+                    kc.run(KC_REFINE, 1, [&] {
+                        k_e_visit<T><<<blocks, 256, 0, s>>>(g->e_order.as<int32_t>() + at, (int32_t)cnt,
+                                                            g->out_info.as<int32_t>(), g->rp_out.as<int64_t>(),
+                                                            g->col_push.as<int32_t>(), g->hub_ids.as<int32_t>(),
+                                                            ws.F.as<T>(), ws.H.as<double>(), ctl);
+                    });
+                }
             }
             DI_CHECK_CUDA(cudaGetLastError());
         }
         auto run_sweeps = [&]() {
+            // a new phase of sweeps: the reduction below decides again whether to stop
+            static const int32_t not_done = 0;
+            DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->done, &not_done, sizeof(int32_t), cudaMemcpyHostToDevice, s));
             kc.run(KC_REDUCE, 1, [&] {
                 k_reduce<T><<<l.red_blocks, 256, 0, s>>>(ws.F.as<T>(), g->n, ws.partials.as<double>(), ctl,
-                                                         cudaGraphConditionalHandle(0), 0);
+                                                         cudaGraphConditionalHandle(0), 0, 1);
             });
             DI_CHECK_CUDA(cudaGetLastError());
             if (host_loop) {
                 for (;;) {
-                    read_ctl(g, s);
+                    read_ctl(g, ws, s);
                     if (ws.ctl_host->done) break;
-                    launch_sweep_body<T>(g, l, s, cudaGraphConditionalHandle(0), 0, &kc);
+                    launch_sweep_body<T>(g, ws, l, s, cudaGraphConditionalHandle(0), 0, &kc, parts);
                     DI_CHECK_CUDA(cudaGetLastError());
                 }
             } else {
-                if (!ws.sweep_exec) build_sweep_graph<T>(g, l);
+                if (ws.sweep_exec && (ws.sweep_parts != parts || !(ws.sweep_tune == g->tune_single))) ws.reset_graphs();
+                if (!ws.sweep_exec) build_sweep_graph<T>(g, ws, l, parts);
                 DI_CHECK_CUDA(cudaGraphLaunch(ws.sweep_exec, s));
             }
         };
@@ -1557,8 +1990,8 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
                 from_device(X_out, ws.H.p, x_bytes, ws.out_stream);
                 DI_CHECK_CUDA(cudaEventRecord(ws.out_done, ws.out_stream));
             }
-            kc.run(KC_REFINE, g->n_heavy_in_chunks > 0 ? 3 : 2, [&] { launch_refine<T>(g, l, d, s); });
-            read_ctl(g, s);
+            kc.run(KC_REFINE, g->n_heavy_in_chunks > 0 ? 3 : 2, [&] { launch_refine<T>(g, ws, l, d, s); });
+            read_ctl(g, ws, s);
             rounds++;
             if (ws.ctl_host->status || ws.ctl_host->r <= tol || ws.ctl_host->sweeps >= max_sweeps || rounds >= 4) break;
             if (x_copied) {
@@ -1595,7 +2028,7 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
             DI_CHECK_CUDA(cudaGetLastError());
             from_device(F_out, stage, sizeof(double) * (size_t)g->n, s);
         }
-        read_ctl(g, s);
+        read_ctl(g, ws, s);
     } catch (...) {
         if (ws.out_stream) cudaStreamSynchronize(ws.out_stream);   // no copy outlives the call
         cudaEventDestroy(e0);
@@ -1617,7 +2050,7 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
         info->dangling_mass_e = c.e;
         info->paper_error = c.r / (1.0 - d - d * c.e);
         info->ms = ms;
-        info->kernel_launches = kc.host_launches + 3 * (int64_t)c.body_runs;
+        info->kernel_launches = kc.host_launches + 3 * (int64_t)parts * (int64_t)c.body_runs;
         info->frontier_entries = (int64_t)c.front_total;
         info->select_ms = kc.ms[KC_SELECT];
         info->push_ms = kc.ms[KC_PUSH];
@@ -1635,28 +2068,117 @@ static void solve_impl(di_graph *g, const double *B, double d, double tol, int s
                c.r, tol);
 }
 
+// ------------------------------------------------------------------------------------------
+// autotuning of the single right-hand-side push split (PushTune)
+// ------------------------------------------------------------------------------------------
+__global__ void k_fill(double *v, int32_t n, double x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) v[i] = x;
+}
+
+// Device time of a probe solve with split t: DI-SOP from B = (1 - d) / N, FP32 fluid without
+// refinement, to ||F||_1 <= 1e-3 (1 - d) (about 40% of a full solve's sweeps), median of 3 after
+// a warm-up. The caller holds the graph's lock.
+static double probe_single_ms(di_graph *g, Workspace &ws, double d, const PushTune &t, cudaStream_t s) {
+    ensure_workspace<float>(g, ws);
+    g->tune_single = t;
+    const Launch l = launch_shape<float>(g);
+    double *Bp = ws.Xdf.as<double>();       // neither buffer is used by a D-iteration solve
+    double *Xp = ws.Bdf.as<double>();
+    k_fill<<<l.ew_blocks, 256, 0, s>>>(Bp, g->n, (1.0 - d) / g->n);
+    DI_CHECK_CUDA(cudaGetLastError());
+    std::vector<double> ms;
+    for (int rep = 0; rep < 4; rep++) {
+        di_solve_info info;
+        solve_impl<float>(g, ws, Bp, d, 1e-3 * (1.0 - d), DI_SOP, 100000, 0, 0, 0, 0, 0, Xp, nullptr, &info, s);
+        if (rep) ms.push_back(info.ms);
+    }
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+}
+
+// Coordinate descent over the row cut-off, then the heavy cut-off, then the chunk length.
+PushTune autotune_single(di_graph *g, double d, cudaStream_t s, double *best_ms) {
+    Workspace &ws = g->ws;
+    PushTune best = g->tune_single;
+    double bms = probe_single_ms(g, ws, d, best, s);
+    auto try_one = [&](PushTune t) {
+        if (t.chunk > t.heavy) return;
+        const double ms = probe_single_ms(g, ws, d, t, s);
+        if (ms < bms) {
+            bms = ms;
+            best = t;
+        }
+    };
+    for (int row : {32, 64, 128, 256}) {
+        PushTune t = best;
+        t.row = row;
+        if (!(t == best)) try_one(t);
+    }
+    for (int heavy : {1024, 2048, 4096, 8192}) {
+        PushTune t = best;
+        t.heavy = heavy;
+        if (!(t == best)) try_one(t);
+    }
+    for (int chunk : {256, 512, 1024, 2048}) {
+        PushTune t = best;
+        t.chunk = chunk;
+        if (!(t == best)) try_one(t);
+    }
+    g->tune_single = best;
+    if (best_ms) *best_ms = bms;
+    return best;
+}
+
+// Parts of a DI-SOP sweep, each selecting with r taken again (opts.r_refresh; 1 = the paper's
+// r once per sweep). DI-CYC does not use r, so it always sweeps in one part.
+constexpr int kMaxSweepParts = 16;
+static int sweep_parts(const di_solve_opts &o) {
+    return (o.schedule == DI_SOP && o.r_refresh > 1) ? o.r_refresh : 1;
+}
+
+// Checks and dispatch shared by solve_single and solve_single_in; the caller owns ws.
+static void solve_single_body(di_graph *g, Workspace &ws, const double *B, double d, double tol,
+                              const di_solve_opts *opts, double *X_out, double *residual_out, di_solve_info *info,
+                              cudaStream_t s, bool lock) {
+    check_common(g, B, d, tol, X_out);
+    di_solve_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    DI_REQUIRE(o.schedule == DI_CYC || o.schedule == DI_SOP, DI_ERR_INVALID_ARG, "unknown schedule %d", o.schedule);
+    DI_REQUIRE(o.fluid == DI_FLUID_F32 || o.fluid == DI_FLUID_F64, DI_ERR_INVALID_ARG, "unknown fluid %d", o.fluid);
+    DI_REQUIRE(o.r_refresh >= 0 && o.r_refresh <= kMaxSweepParts, DI_ERR_INVALID_ARG,
+               "r_refresh must be in [0, %d] (got %d)", kMaxSweepParts, o.r_refresh);
+    int max_sweeps = o.max_sweeps <= 0 ? 100000 : (o.max_sweeps > 1000000 ? 1000000 : o.max_sweeps);
+    int refine = o.refine == 0 ? (o.fluid == DI_FLUID_F32) : (o.refine > 0);
+    std::unique_lock<std::mutex> lk(g->mu, std::defer_lock);
+    if (lock) {
+        lk.try_lock();
+        DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
+    }
+    DeviceGuard dg(g->dev.device);
+    if (o.fluid == DI_FLUID_F32)
+        solve_impl<float>(g, ws, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
+                          o.e_prediffuse != 0, 0, X_out, residual_out, info, s, nullptr, nullptr, nullptr,
+                          sweep_parts(o), o.exact_r != 0);
+    else
+        solve_impl<double>(g, ws, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
+                           o.e_prediffuse != 0, 0, X_out, residual_out, info, s, nullptr, nullptr, nullptr,
+                           sweep_parts(o), o.exact_r != 0);
+}
+
 di_status solve_single(di_graph *g, const double *B, double d, double tol, const di_solve_opts *opts, double *X_out,
                        double *residual_out, di_solve_info *info, cudaStream_t s) {
     return guarded([&] {
-        check_common(g, B, d, tol, X_out);
-        di_solve_opts o;
-        memset(&o, 0, sizeof(o));
-        if (opts) o = *opts;
-        DI_REQUIRE(o.schedule == DI_CYC || o.schedule == DI_SOP, DI_ERR_INVALID_ARG, "unknown schedule %d", o.schedule);
-        DI_REQUIRE(o.fluid == DI_FLUID_F32 || o.fluid == DI_FLUID_F64, DI_ERR_INVALID_ARG, "unknown fluid %d", o.fluid);
-        int max_sweeps = o.max_sweeps <= 0 ? 100000 : (o.max_sweeps > 1000000 ? 1000000 : o.max_sweeps);
-        int refine = o.refine == 0 ? (o.fluid == DI_FLUID_F32) : (o.refine > 0);
-        std::unique_lock<std::mutex> lk(g->mu, std::try_to_lock);
-        DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
-        DeviceGuard dg(g->dev.device);
-        if (o.fluid == DI_FLUID_F32)
-            solve_impl<float>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
-                              o.e_prediffuse != 0, 0, X_out,
-                              residual_out, info, s);
-        else
-            solve_impl<double>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
-                               o.e_prediffuse != 0, 0, X_out,
-                               residual_out, info, s);
+        DI_REQUIRE(g != nullptr, DI_ERR_INVALID_ARG, "graph is NULL");
+        solve_single_body(g, g->ws, B, d, tol, opts, X_out, residual_out, info, s, true);
+    });
+}
+
+di_status solve_single_in(di_graph *g, Workspace &ws, const double *B, double d, double tol, const di_solve_opts *opts,
+                          double *X_out, double *residual_out, di_solve_info *info, cudaStream_t s) {
+    return guarded([&] {
+        DI_REQUIRE(g != nullptr, DI_ERR_INVALID_ARG, "graph is NULL");
+        solve_single_body(g, ws, B, d, tol, opts, X_out, residual_out, info, s, false);
     });
 }
 
@@ -1677,17 +2199,22 @@ di_status solve_resume(di_graph *g, const double *B, const double *H0, const dou
         if (opts) o = *opts;
         DI_REQUIRE(o.schedule == DI_CYC || o.schedule == DI_SOP, DI_ERR_INVALID_ARG, "unknown schedule %d", o.schedule);
         DI_REQUIRE(o.fluid == DI_FLUID_F32 || o.fluid == DI_FLUID_F64, DI_ERR_INVALID_ARG, "unknown fluid %d", o.fluid);
+        DI_REQUIRE(o.r_refresh >= 0 && o.r_refresh <= kMaxSweepParts, DI_ERR_INVALID_ARG,
+                   "r_refresh must be in [0, %d] (got %d)", kMaxSweepParts, o.r_refresh);
         int max_sweeps = o.max_sweeps <= 0 ? 100000 : (o.max_sweeps > 1000000 ? 1000000 : o.max_sweeps);
         int refine = o.refine == 0 ? (o.fluid == DI_FLUID_F32) : (o.refine > 0);
         std::unique_lock<std::mutex> lk(g->mu, std::try_to_lock);
         DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
         DeviceGuard dg(g->dev.device);
+        Workspace &ws = g->ws;
         if (o.fluid == DI_FLUID_F32)
-            solve_impl<float>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
-                              o.e_prediffuse != 0, 0, X_out, residual_out, info, s, H0, F0, F_out);
+            solve_impl<float>(g, ws, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
+                              o.e_prediffuse != 0, 0, X_out, residual_out, info, s, H0, F0, F_out, sweep_parts(o),
+                              o.exact_r != 0);
         else
-            solve_impl<double>(g, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
-                               o.e_prediffuse != 0, 0, X_out, residual_out, info, s, H0, F0, F_out);
+            solve_impl<double>(g, ws, B, d, tol, o.schedule, max_sweeps, refine, o.host_loop, o.profile,
+                               o.e_prediffuse != 0, 0, X_out, residual_out, info, s, H0, F0, F_out, sweep_parts(o),
+                               o.exact_r != 0);
     });
 }
 
@@ -1700,61 +2227,158 @@ di_status power_iter_push(di_graph *g, const double *B, double d, double tol, in
         std::unique_lock<std::mutex> lk(g->mu, std::try_to_lock);
         DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
         DeviceGuard dg(g->dev.device);
+        Workspace &ws = g->ws;
         if (fluid == DI_FLUID_F32)
-            solve_impl<float>(g, B, d, tol, DI_CYC, mi, 1, 0, 0, 0, 1, X_out, residual_out, info, s);
+            solve_impl<float>(g, ws, B, d, tol, DI_CYC, mi, 1, 0, 0, 0, 1, X_out, residual_out, info, s);
         else
-            solve_impl<double>(g, B, d, tol, DI_CYC, mi, 0, 0, 0, 0, 1, X_out, residual_out, info, s);
+            solve_impl<double>(g, ws, B, d, tol, DI_CYC, mi, 0, 0, 0, 0, 1, X_out, residual_out, info, s);
+    });
+}
+
+// Power iteration (Jacobi on X = P.X + B, Section 2.5 "PI"), from X_0 = 0 until
+// ||X_(k+1) - X_k||_1 <= tol. fp64: FP64 throughout. Otherwise in increment form with FP32
+// increments: X_(k+1) - X_k = P (X_k - X_(k-1)), pulled over the in-links, X accumulated in
+// FP64 (in the history buffer, which the exact residual reads). The increments' FP32 rounding is relative to the increments, which shrink
+// geometrically; with refinement the iteration stops halfway (on a log scale) and at the end
+// to take the exact next increment B + P.X - X (double-float link sums, FP64 B and X), which
+// certifies the reported residual and, when above tol, restarts the increments from it.
+static void power_iter_impl(di_graph *g, Workspace &ws, const double *B, double d, double tol, int max_iters, bool fp64, bool refine,
+                            int profile, double *X_out, double *residual_out, di_solve_info *info, cudaStream_t s) {
+    using T = float;   // the single-solve workspace in its FP32 layout
+    ensure_workspace<T>(g, ws);
+    const Launch l = launch_shape<T>(g);
+    SolveCtl *ctl = ws.ctl.as<SolveCtl>();
+    to_device(ws.B.p, B, sizeof(double) * (size_t)g->n, s);
+    write_ctl(g, ws, d, tol, DI_CYC, max_iters, 0, s, 0, (!fp64 && refine) ? 1 : 0);
+    KernelClock kc(profile != 0, s);
+    cudaEvent_t e0, e1;
+    DI_CHECK_CUDA(cudaEventCreate(&e0));
+    DI_CHECK_CUDA(cudaEventCreate(&e1));
+    int rounds = 0;
+    try {
+        DI_CHECK_CUDA(cudaEventRecord(e0, s));
+        if (fp64) {
+            kc.run(KC_REFINE, 1, [&] {
+                k_pi64_init<<<l.ew_blocks, 256, 0, s>>>(g->out_info.as<int32_t>(), g->n, d, ws.Bdf.as<double>(),
+                                                        ws.Xdf.as<double>(), ws.y0.as<double>());
+            });
+        } else {
+            kc.run(KC_REFINE, 1, [&] {
+                // one iteration is done after the set-up, so the next pull reads y1 (see k_pull)
+                k_pi_inc_init<<<l.red_blocks, 256, 0, s>>>(ws.B.as<double>(), g->out_info.as<int32_t>(), g->n, d,
+                                                           ws.Bdf.as<float>(), ws.H.as<double>(), ws.y1.as<float>(),
+                                                           ws.partials.as<double>(), ctl);
+            });
+        }
+        DI_CHECK_CUDA(cudaGetLastError());
+        auto run_iters = [&]() {
+            if (profile) {
+                for (;;) {
+                    read_ctl(g, ws, s);
+                    if (ws.ctl_host->done) break;
+                    launch_pi_body(g, ws, l, s, cudaGraphConditionalHandle(0), 0, fp64, &kc);
+                    DI_CHECK_CUDA(cudaGetLastError());
+                }
+            } else {
+                if (ws.pi_exec && ws.pi_fp64 != (fp64 ? 1 : 0)) ws.reset_graphs();
+                if (!ws.pi_exec) build_pi_graph(g, ws, l, fp64);
+                DI_CHECK_CUDA(cudaGraphLaunch(ws.pi_exec, s));
+            }
+        };
+        // the set-up counts as the first iteration (X_1 = B), so the loop may already be done
+        read_ctl(g, ws, s);
+        if (!ws.ctl_host->done) run_iters();
+        if (fp64) {
+            kc.run(KC_REFINE, 1, [&] {
+                k_fluid_to_double<double><<<l.ew_blocks, 256, 0, s>>>(ws.Xdf.as<double>(), g->n, ws.H.as<double>());
+            });
+        }
+        while (!fp64 && refine) {
+            // the exact next increment of X (in ws.F as FP32, its norm in ctl->r)
+            kc.run(KC_REFINE, g->n_heavy_in_chunks > 0 ? 3 : 2, [&] { launch_refine<T>(g, ws, l, d, s); });
+            read_ctl(g, ws, s);
+            rounds++;
+            if (ws.ctl_host->r <= tol || ws.ctl_host->sweeps >= max_iters || rounds >= 4) break;
+            // continue the increments from it: after the halfway stop at tol itself (the exact
+            // check follows, and the fluid's rounding since that stop is far below tol), else at
+            // half of it
+            const bool after_split = ws.ctl_host->halfway != 0;
+            SolveCtl &c = *ws.ctl_host;
+            c.tol = (after_split ? 1.0 : 0.5) * tol;
+            c.halfway = 0;
+            c.done = 0;
+            DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->tol, &c.tol, sizeof(double), cudaMemcpyHostToDevice, s));
+            DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->halfway, &c.halfway, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->done, &c.done, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            kc.run(KC_REFINE, 1, [&] {
+                k_pi_inc_resume<<<l.ew_blocks, 256, 0, s>>>(ws.F.as<float>(), g->n, ws.Bdf.as<float>(),
+                                                            ws.H.as<double>(), ws.y0.as<float>(), ws.y1.as<float>(),
+                                                            ctl);
+            });
+            // applying the exact increment is one more iteration
+            c.sweeps += 1;
+            DI_CHECK_CUDA(cudaMemcpyAsync(&ctl->sweeps, &c.sweeps, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            if (c.sweeps < max_iters) run_iters();
+        }
+        DI_CHECK_CUDA(cudaGetLastError());
+        DI_CHECK_CUDA(cudaEventRecord(e1, s));
+        from_device(X_out, ws.H.p, sizeof(double) * (size_t)g->n, s);
+        read_ctl(g, ws, s);
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const SolveCtl &c = *ws.ctl_host;
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->sweeps = c.sweeps;
+        info->refine_rounds = rounds;
+        info->pushed_edges = (int64_t)c.sweeps * g->L;
+        info->visited_nodes = (int64_t)c.sweeps * g->n;
+        info->residual_l1 = c.r;
+        info->ms = ms;
+        const int per = g->n_heavy_in_chunks > 0 ? 2 : 1;
+        info->kernel_launches = kc.host_launches + (int64_t)c.body_runs * per;
+        info->select_ms = kc.ms[KC_SELECT];
+        info->push_ms = kc.ms[KC_PUSH];
+        info->refine_ms = kc.ms[KC_REFINE];
+        info->select_launches = kc.count[KC_SELECT];
+        info->push_launches = kc.count[KC_PUSH];
+        info->refine_launches = kc.count[KC_REFINE];
+    }
+    if (residual_out) *residual_out = c.r;
+    DI_REQUIRE(c.r <= tol, DI_ERR_NOT_CONVERGED, "PI not converged after %d iterations: %g > %g", c.sweeps, c.r, tol);
+}
+
+di_status power_iter_ex(di_graph *g, const double *B, double d, double tol, const di_solve_opts *opts, double *X_out,
+                        double *residual_out, di_solve_info *info, cudaStream_t s) {
+    return guarded([&] {
+        check_common(g, B, d, tol, X_out);
+        di_solve_opts o;
+        memset(&o, 0, sizeof(o));
+        if (opts) o = *opts;
+        DI_REQUIRE(o.fluid == DI_FLUID_F32 || o.fluid == DI_FLUID_F64, DI_ERR_INVALID_ARG, "unknown fluid %d", o.fluid);
+        const int mi = o.max_sweeps <= 0 ? 100000 : (o.max_sweeps > 1000000 ? 1000000 : o.max_sweeps);
+        const bool fp64 = o.fluid == DI_FLUID_F64;
+        const bool refine = o.refine >= 0;
+        std::unique_lock<std::mutex> lk(g->mu, std::try_to_lock);
+        DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
+        DeviceGuard dg(g->dev.device);
+        power_iter_impl(g, g->ws, B, d, tol, mi, fp64, refine, o.profile, X_out, residual_out, info, s);
     });
 }
 
 di_status power_iter(di_graph *g, const double *B, double d, double tol, int32_t max_iters, double *X_out,
                      double *residual_out, di_solve_info *info, cudaStream_t s) {
-    return guarded([&] {
-        check_common(g, B, d, tol, X_out);
-        int mi = max_iters <= 0 ? 100000 : (max_iters > 1000000 ? 1000000 : max_iters);
-        std::unique_lock<std::mutex> lk(g->mu, std::try_to_lock);
-        DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
-        DeviceGuard dg(g->dev.device);
-        using T = float;   // PI is FP64 throughout; the fluid buffers are unused
-        ensure_workspace<T>(g);
-        Workspace &ws = g->ws;
-        const Launch l = launch_shape<T>(g);
-        to_device(ws.B.p, B, sizeof(double) * (size_t)g->n, s);
-        write_ctl(g, d, tol, DI_CYC, mi, 0, s);
-        cudaEvent_t e0, e1;
-        DI_CHECK_CUDA(cudaEventCreate(&e0));
-        DI_CHECK_CUDA(cudaEventCreate(&e1));
-        DI_CHECK_CUDA(cudaEventRecord(e0, s));
-        // c = d / out, B and X_0 = 0 in double-float, y_0 = 0
-        k_pi_init<<<l.ew_blocks, 256, 0, s>>>(ws.B.as<double>(), g->out_info.as<int32_t>(), g->n, d,
-                                              ws.Bdf.as<float2>(), ws.cdf.as<float2>(), ws.Xdf.as<float2>(),
-                                              ws.y0.as<float2>());
-        ws.cdf_d = d;
-        if (!ws.pi_exec) build_pi_graph<T>(g, l);
-        DI_CHECK_CUDA(cudaGraphLaunch(ws.pi_exec, s));
-        k_df_to_double<<<l.ew_blocks, 256, 0, s>>>(ws.Xdf.as<float2>(), g->n, ws.H.as<double>());
-        DI_CHECK_CUDA(cudaGetLastError());
-        DI_CHECK_CUDA(cudaEventRecord(e1, s));
-        from_device(X_out, ws.H.p, sizeof(double) * (size_t)g->n, s);
-        read_ctl(g, s);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        const SolveCtl &c = *ws.ctl_host;
-        if (info) {
-            memset(info, 0, sizeof(*info));
-            info->sweeps = c.sweeps;
-            info->pushed_edges = (int64_t)c.sweeps * g->L;
-            info->visited_nodes = (int64_t)c.sweeps * g->n;
-            info->residual_l1 = c.r;
-            info->ms = ms;
-            info->kernel_launches = 2 + (int64_t)c.body_runs * (g->n_heavy_in_chunks > 0 ? 2 : 1);
-        }
-        if (residual_out) *residual_out = c.r;
-        DI_REQUIRE(c.r <= tol, DI_ERR_NOT_CONVERGED, "PI not converged after %d iterations: %g > %g", c.sweeps, c.r,
-                   tol);
-    });
+    di_solve_opts o;
+    memset(&o, 0, sizeof(o));
+    o.max_sweeps = max_iters;
+    return power_iter_ex(g, B, d, tol, &o, X_out, residual_out, info, s);
 }
 
 }  // namespace di
@@ -1790,6 +2414,11 @@ di_status di_power_iter_push(di_graph *g, const double *B, double d, double tol,
 di_status di_power_iter(di_graph *g, const double *B, double d, double tol, int32_t max_iters, double *X_out,
                         double *residual_out, di_solve_info *info, void *stream) {
     return di::power_iter(g, B, d, tol, max_iters, X_out, residual_out, info, (cudaStream_t)stream);
+}
+
+di_status di_power_iter_ex(di_graph *g, const double *B, double d, double tol, const di_solve_opts *opts,
+                           double *X_out, double *residual_out, di_solve_info *info, void *stream) {
+    return di::power_iter_ex(g, B, d, tol, opts, X_out, residual_out, info, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -39,12 +39,14 @@ struct BatchCtl {
     int32_t force_cyc;
     int32_t last_selected;
     int32_t front_count;
-    int32_t heavy_chunks;            // kHeavyChunk-link chunks of the entries with > kPushHeavy links
+    int32_t heavy_chunks;            // chunks of the entries with more than PushTune::heavy links
     int32_t batch_next;
     int32_t body_runs;
     uint32_t ticket;
-    int32_t split;                   // 1: the next stop test raises each active column's tol to
-                                     //    sqrt(tol * r), its first refinement point
+    uint32_t split_mask;             // columns whose next stop test raises their tol to
+                                     //    sqrt(tol * r), their first refinement point
+    int64_t seed_off[kMaxT + 1];     // seed sets of the tile's columns: column c holds the seeds
+                                     //    at positions [seed_off[c], seed_off[c+1]) of the list
 };
 
 // ------------------------------------------------------------------------------------------
@@ -62,23 +64,24 @@ __global__ void kb_load_B(const double *B, int32_t n, int c0, int ncols, double 
     }
 }
 
-// Bn[s*T + c] += (1 - d) / |S_c| for every seed s of column c (seeds of columns c0 .. c0+ncols)
+// Bn[s*T + c] += (1 - d) / |S_c| for every seed s of column c: seeds[e - e0] is the seed at list
+// position e, for e in [e0, e1), and ctl->seed_off holds the tile's column ranges
 template <int T>
-__global__ void kb_seed_B(const int64_t *off, const int32_t *seeds, int32_t n, int c0, int ncols, double d, double *Bn,
+__global__ void kb_seed_B(const int32_t *seeds, int64_t e0, int64_t e1, int32_t n, int ncols, double d, double *Bn,
                           BatchCtl *ctl) {
-    const int64_t e0 = off[c0], e1 = off[c0 + ncols];
+    const int64_t *off = ctl->seed_off;
     for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1; e += (int64_t)gridDim.x * blockDim.x) {
         int lo = 0, hi = ncols - 1;          // column whose range holds e
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (off[c0 + mid] <= e) lo = mid; else hi = mid - 1;
+            if (off[mid] <= e) lo = mid; else hi = mid - 1;
         }
-        const int32_t s = seeds[e];
+        const int32_t s = seeds[e - e0];
         if (s < 0 || s >= n) {
             ctl->status = 2;
             continue;
         }
-        const double cnt = (double)(off[c0 + lo + 1] - off[c0 + lo]);
+        const double cnt = (double)(off[lo + 1] - off[lo]);
         atomicAdd(&Bn[(int64_t)s * T + lo], (1.0 - d) / cnt);
     }
 }
@@ -146,12 +149,13 @@ __device__ __forceinline__ void column_l1(const V *v, int32_t n, double *partial
 
 // Column retirement and the stop test (thread 0 of the finishing block).
 static __device__ __forceinline__ void batch_stop_test(BatchCtl *ctl, cudaGraphConditionalHandle h, int set_cond) {
-    if (ctl->split) {
-        ctl->split = 0;
+    if (ctl->split_mask) {
         for (int c = 0; c < ctl->ncols; c++) {
             const double mid = sqrt(ctl->tol[c] * ctl->r[c]);
-            if (ctl->active[c] && mid > ctl->tol[c]) ctl->tol[c] = mid;
+            if ((ctl->split_mask >> c & 1u) && ctl->active[c] && ctl->tol[c] < kSplitBelow * ctl->r[c])
+                ctl->tol[c] = mid;
         }
+        ctl->split_mask = 0;
     }
     bool any = false;
     double rsum = 0.0;
@@ -182,13 +186,26 @@ __global__ void __launch_bounds__(256) kb_reduce(const float *F, int32_t n, doub
     column_l1<T>(F, n, partials, ctl, ctl->r, [&] { batch_stop_test(ctl, h, set_cond); });
 }
 
+// A column's DI-SOP test |F_ic| > (r_c / L) * out_i, decided as in FP64: FP32 unless the fluid
+// is within 2^-20 (relative) of the threshold, where the FP32 product's rounding (below 2^-22)
+// could matter, or r_c / L is too small for FP32's normal range.
+static __device__ __forceinline__ bool tile_sop_selects(float a, float o_f, double thr, float thr_f) {
+    const float p = thr_f * o_f;
+    if (thr_f >= 1e-30f) {
+        if (a > p * (1.f + 1.0f / (1 << 20))) return true;
+        if (a < p * (1.f - 1.0f / (1 << 20))) return false;
+    }
+    return (double)a > thr * (double)o_f;
+}
+
 // A block handles 256 consecutive nodes per iteration in T sub-steps of 256/T nodes (T lanes per
 // node, one lane per column); the pushed nodes of the 256 are compacted with one atomic, so the
 // frontier is id-sorted within each 256-node chunk.
 template <int T>
 __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int32_t *out_info, int32_t n,
                                                  BatchCtl *ctl, int32_t *front_id, float *front_s,
-                                                 int32_t *heavy_cstart, int32_t *heavy_chunk) {
+                                                 int32_t *heavy_cstart, int32_t *heavy_chunk, int heavy_cut,
+                                                 int heavy_len) {
     constexpr int kNodesPerStep = 256 / T;
     __shared__ double s_thr[T];
     __shared__ int s_act[T];
@@ -198,7 +215,7 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
     __shared__ int chunk_base;
     __shared__ float s_share[T][256];       // per sub-step share of every lane
     __shared__ unsigned s_lbs[T][8];        // per sub-step leader ballot of every warp
-    __shared__ int32_t s_hdeg[T][256 / T];  // per sub-step and node: out-degree if above kPushHeavy, else 0
+    __shared__ int32_t s_hdeg[T][256 / T];  // per sub-step and node: out-degree if above heavy_cut, else 0
     if (ctl->done) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool cyc = ctl->schedule == DI_CYC || ctl->force_cyc;
@@ -240,7 +257,8 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
             for (int q = 0; q < kGroup; q++) {
                 const int64_t i = base + (j0 + q) * kNodesPerStep + tid / T;
                 const float o_f = (float)(info[q] & 0x7fffffff);
-                if (i < n && act && (cyc ? (f[q] != 0.f) : (fabsf(f[q]) > thr_f * o_f))) selm |= 1u << q;
+                if (i < n && act && (cyc ? (f[q] != 0.f) : tile_sop_selects(fabsf(f[q]), o_f, s_thr[c], thr_f)))
+                    selm |= 1u << q;
             }
             double h[kGroup];
 #pragma unroll
@@ -278,7 +296,7 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
                     pushed += (unsigned long long)o;
                 }
                 const unsigned lb = __ballot_sync(kFull, leader && bpush != 0);
-                if (leader) s_hdeg[j][tid / T] = o > kPushHeavy ? o : 0;
+                if (leader) s_hdeg[j][tid / T] = o > heavy_cut ? o : 0;
                 s_share[j][tid] = share;
                 if (lane == 0) {
                     s_lbs[j][warp] = lb;
@@ -311,7 +329,7 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
                     // a node with many links is pushed in chunks over all warps (see kb_push)
                     const int32_t o = s_hdeg[j][tid / T];
                     if (o > 0) {
-                        const int nch = (o + kHeavyChunk - 1) / kHeavyChunk;
+                        const int nch = (o + heavy_len - 1) / heavy_len;
                         const int cs = atomicAdd(&ctl->heavy_chunks, nch);
                         heavy_cstart[pos] = cs;
                         for (int q = 0; q < nch; q++) heavy_chunk[cs + q] = pos;
@@ -349,6 +367,46 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
     }
 }
 
+// Slot kernels of a tile whose columns are refilled (the batched solver and the server):
+// scattering a request's seeds into a free column, loading a dense right-hand side into one,
+// and handing a finished column's history out while zeroing the column for its next request.
+template <int T>
+__global__ void kb_seed_col(const int32_t *seeds, int64_t cnt, int c, double share, int32_t n, float *F, double *Bn,
+                            BatchCtl *ctl) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = seeds[e];
+        if (s < 0 || s >= n) {
+            ctl->status = 2;
+            continue;
+        }
+        atomicAdd(&Bn[(int64_t)s * T + c], share);
+        atomicAdd(&F[(int64_t)s * T + c], (float)share);
+    }
+}
+
+template <int T>
+__global__ void kb_load_col(const double *B, int32_t n, int c, float *F, double *Bn, BatchCtl *ctl) {
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double b = B[i];
+        if (!(b >= 0.0) || isinf(b)) bad = true;
+        Bn[i * T + c] = b;
+        F[i * T + c] = (float)b;
+    }
+    if (bad) ctl->status = 1;
+}
+
+template <int T>
+__global__ void kb_col_retire(float *F, double *H, double *Bn, int32_t n, int c, double *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t idx = i * T + c;
+        out[i] = H[idx];
+        H[idx] = 0.0;
+        F[idx] = 0.f;
+        Bn[idx] = 0.0;
+    }
+}
+
 template <int T>
 __global__ void kb_fill(double *Bn, int64_t count, double v) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
@@ -367,7 +425,7 @@ __global__ void __launch_bounds__(256) kb_push(const int32_t *__restrict__ front
                                                const int32_t *__restrict__ heavy_cstart,
                                                const int32_t *__restrict__ heavy_chunk,
                                                const int64_t *__restrict__ rp_out, const int32_t *__restrict__ col_out,
-                                               float *F, BatchCtl *ctl) {
+                                               float *F, BatchCtl *ctl, int heavy_cut, int heavy_len) {
     if (ctl->done) return;
     constexpr int LPE = T / 4;          // lanes per link
     constexpr int EPI = 32 / LPE;       // links per warp step
@@ -385,7 +443,7 @@ __global__ void __launch_bounds__(256) kb_push(const int32_t *__restrict__ front
             const int32_t u = front_id[p];
             const int64_t beg = rp_out[u];
             const int deg = (int)(rp_out[u + 1] - beg);
-            if (deg > kPushHeavy) continue;   // pushed below, in chunks over all warps
+            if (deg > heavy_cut) continue;   // pushed below, in chunks over all warps
             const float4 s = reinterpret_cast<const float4 *>(front_s + (int64_t)p * T)[q];
             const bool any = (s.x != 0.f) || (s.y != 0.f) || (s.z != 0.f) || (s.w != 0.f);
             if (!any) continue;
@@ -399,7 +457,7 @@ __global__ void __launch_bounds__(256) kb_push(const int32_t *__restrict__ front
             }
         }
     }
-    // nodes with more than kPushHeavy links: kHeavyChunk-link chunks over all warps
+    // nodes with more than heavy_cut links: heavy_len-link chunks over all warps
     const int hch = ctl->heavy_chunks;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < hch; c += nwarps) {
@@ -407,8 +465,8 @@ __global__ void __launch_bounds__(256) kb_push(const int32_t *__restrict__ front
         const int32_t u = front_id[p];
         const float4 s = reinterpret_cast<const float4 *>(front_s + (int64_t)p * T)[q];
         const bool any = (s.x != 0.f) || (s.y != 0.f) || (s.z != 0.f) || (s.w != 0.f);
-        const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * kHeavyChunk;
-        const int64_t ce = min(cb + (int64_t)kHeavyChunk, rp_out[u + 1]);
+        const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * heavy_len;
+        const int64_t ce = min(cb + (int64_t)heavy_len, rp_out[u + 1]);
         if (!any) continue;
         for (int64_t e0 = cb + es; e0 < ce; e0 += EPI * 4) {
             int32_t j[4];   // four index loads in flight before the reductions
@@ -585,27 +643,51 @@ __global__ void kb_extract(const double *H, int32_t n, int ncols, double *X) {
 
 static int tile_index(int T) { return T == 4 ? 0 : T == 8 ? 1 : T == 16 ? 2 : 3; }
 
+// The batched workspace's buffers for tiles of up to T columns, in a fixed order; `take(buffer,
+// bytes)` allocates, binds or counts each.
+template <class Take>
+static void batch_layout(di_graph *g, BatchWorkspace &w, int T, Take &&take) {
+    const size_t n = (size_t)g->n, t = (size_t)T;
+    take(w.F, sizeof(float) * n * t);
+    take(w.H, sizeof(double) * n * t);
+    take(w.Bn, sizeof(double) * n * t);
+    take(w.front_id, sizeof(int32_t) * n);
+    take(w.heavy_cstart, sizeof(int32_t) * n);
+    // a heavy node has at most out / chunk + 1 chunks (chunk >= kHeavyChunkMin), and each node is
+    // one entry per sweep
+    take(w.heavy_chunk, sizeof(int32_t) * (size_t)(g->L / kHeavyChunkMin + g->n_heavy_out + 1));
+    take(w.front_s, sizeof(float) * n * t);
+    take(w.heavy_partial, sizeof(float2) * (size_t)(g->n_heavy_in_chunks + 1) * t);
+    take(w.y, sizeof(float2) * n * t);
+    take(w.partials, sizeof(double) * kReduceBlocks * kMaxT);
+    take(w.ctl, sizeof(BatchCtl));
+    take(w.stage, sizeof(double) * n * t);   // host <-> device staging of B, X and seed lists
+}
+
+static size_t batch_bytes(di_graph *g, int T) {
+    BatchWorkspace scratch;   // only counted, never allocated
+    Carve c;
+    batch_layout(g, scratch, T, [&](DevBuf &b, size_t n) { c.take(b, n); });
+    return c.used;
+}
+
 static void ensure_batch(di_graph *g, BatchWorkspace &w, int T) {
-    const size_t n = (size_t)g->n;
     if (w.T_alloc < T) {
         for (auto &e : w.exec)
             if (e) cudaGraphExecDestroy(e);
         for (auto &e : w.exec) e = nullptr;
-        w.F.ensure(sizeof(float) * n * T);
-        w.H.ensure(sizeof(double) * n * T);
-        w.Bn.ensure(sizeof(double) * n * T);
-        w.front_id.ensure(sizeof(int32_t) * n);
-        w.heavy_cstart.ensure(sizeof(int32_t) * n);
-        // a heavy node has at most out / kHeavyChunk + 1 chunks, and each node is one entry per sweep
-        w.heavy_chunk.ensure(sizeof(int32_t) * (size_t)(g->L / kHeavyChunk + g->n_heavy_out + 1));
-        w.front_s.ensure(sizeof(float) * n * T);
-        w.heavy_partial.ensure(sizeof(float2) * (size_t)(g->n_heavy_in_chunks + 1) * T);
-        w.y.ensure(sizeof(float2) * n * T);
+        if (w.ext) {
+            const size_t need = batch_bytes(g, T);
+            DI_REQUIRE(w.ext_bytes >= need, DI_ERR_INVALID_ARG,
+                       "the attached batch workspace holds %zu bytes; tiles of %d columns need %zu (di_workspace_size)",
+                       w.ext_bytes, T, need);
+            Carve c{static_cast<char *>(w.ext), w.ext_bytes};
+            batch_layout(g, w, T, [&](DevBuf &b, size_t n) { c.take(b, n); });
+        } else {
+            batch_layout(g, w, T, [&](DevBuf &b, size_t n) { b.ensure(n); });
+        }
         w.T_alloc = T;
     }
-    w.partials.ensure(sizeof(double) * kReduceBlocks * kMaxT);
-    w.ctl.ensure(sizeof(BatchCtl));
-    w.stage.ensure(sizeof(double) * n * T);
     if (!w.capture_stream) DI_CHECK_CUDA(cudaStreamCreateWithFlags(&w.capture_stream, cudaStreamNonBlocking));
     if (!w.ctl_host) DI_CHECK_CUDA(cudaMallocHost(&w.ctl_host, sizeof(BatchCtl)));
 }
@@ -635,19 +717,25 @@ template <int T>
 static void batch_body(di_graph *g, BatchWorkspace &w, const BLaunch &l, cudaStream_t s, cudaGraphConditionalHandle h,
                        int set_cond) {
     BatchCtl *ctl = w.ctl.as<BatchCtl>();
+    const PushTune tune = g->tune_batch;
     kb_select<T><<<l.sel, 256, 0, s>>>(w.F.as<float>(), w.H.as<double>(), g->out_info.as<int32_t>(), g->n, ctl,
                                        w.front_id.as<int32_t>(), w.front_s.as<float>(), w.heavy_cstart.as<int32_t>(),
-                                       w.heavy_chunk.as<int32_t>());
+                                       w.heavy_chunk.as<int32_t>(), tune.heavy, tune.chunk);
     kb_push<T><<<l.push, 256, 0, s>>>(w.front_id.as<int32_t>(), w.front_s.as<float>(), w.heavy_cstart.as<int32_t>(),
                                       w.heavy_chunk.as<int32_t>(), g->rp_out.as<int64_t>(), g->col_out.as<int32_t>(),
-                                      w.F.as<float>(), ctl);
+                                      w.F.as<float>(), ctl, tune.heavy, tune.chunk);
     kb_reduce<T><<<l.red, 256, 0, s>>>(w.F.as<float>(), g->n, w.partials.as<double>(), ctl, h, set_cond);
 }
 
 template <int T>
 static cudaGraphExec_t batch_graph(di_graph *g, BatchWorkspace &w, const BLaunch &l) {
     cudaGraphExec_t &ex = w.exec[tile_index(T)];
+    if (ex && !(w.exec_tune[tile_index(T)] == g->tune_batch)) {
+        cudaGraphExecDestroy(ex);
+        ex = nullptr;
+    }
     if (ex) return ex;
+    w.exec_tune[tile_index(T)] = g->tune_batch;
     cudaGraph_t graph;
     DI_CHECK_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle h;

@@ -127,3 +127,39 @@ def test_prediffusion_on_a_graph_where_E_dominates():
     assert i1["e_visits"] == st["E"]
     # the chains no longer feed the core one level per sweep
     assert i1["sweeps"] < i0["sweeps"]
+
+
+@pytest.mark.parametrize("fluid", [di.DI_FLUID_F64, di.DI_FLUID_F32])
+def test_large_levels_take_the_windowed_push(fluid):
+    # links only from [0, h) to [h, n): level 0 holds h = 30000 nodes, above the size from which
+    # a level is selected by id chunks and pushed through the sweep's windowed push (FP32 fluid)
+    lib()
+    n, h = 60000, 30000
+    u = workloads.u64(4300, 1, 2 * 8 * h)
+    src = (u[:8 * h] % np.uint64(h)).astype(np.int32)
+    dst = (h + (u[8 * h:] % np.uint64(n - h))).astype(np.int32)
+    g = di.di_graph_create(n, src, dst)
+    og = oracle.build(n, src, dst)
+    assert g.stats["E"] == n and g.stats["e_levels"] == 2
+    B = workloads.uniform(4301, 1, n) * (1 - D) / n
+    ref, _, oinfo, ok = oracle.di_e(og, B, D, 1e-300)
+    assert ok and oinfo["cycles"] == 0
+    X, info = di.di_solve_ex(g, B, D, 1e-12 * B.sum(), schedule=di.DI_SOP, fluid=fluid, e_prediffuse=1)
+    assert info["e_visits"] == n
+    assert rel_l1(X, ref) <= (1e-12 if fluid == di.DI_FLUID_F64 else 1e-6)
+
+
+def test_prediffusion_on_the_e_dominated_shape_at_1m_nodes():
+    # levels of about 40k nodes each: the chunked select and windowed push carry them
+    lib()
+    base = workloads.WORKLOADS["web_n10m_e"]["spec"]
+    spec = workloads.GraphSpec(**dict(base.as_dict(), n=1_000_000, seed=base.seed + 200))
+    n, src, dst = workloads.generate(spec)
+    g = di.di_graph_create(n, src, dst)
+    og = oracle.build(n, src, dst)
+    B = oracle.uniform_B(n, D)
+    ref, _, _, ok = oracle.di(og, B, D, 1e-12, oracle.SOP)
+    assert ok
+    for sched in (di.DI_SOP, di.DI_CYC):
+        X, info = di.di_solve_ex(g, B, D, 1e-9, schedule=sched, e_prediffuse=1)
+        assert rel_l1(X, ref) <= 1e-6 and info["e_visits"] == g.stats["E"]

@@ -1,7 +1,8 @@
 """Serving (continuously batched personalised PageRank over resident graphs) through the C ABI.
 
 Requests arrive while others are on the GPU; each one is admitted into a free slot of its
-graph's tile, retires at its own tolerance and is copied out. Every result must equal the same
+graph's tile (or, while few wait on an idle graph, solved alone on the single right-hand-side
+path), retires at its own tolerance and is copied out. Every result must equal the same
 request solved alone (and the oracle's solution) within its tolerance's error bound
 ||X - H||_1 <= tol / (1 - d), whatever was in the mix.
 """
@@ -31,9 +32,13 @@ def _graphs(sizes, seed):
     return out
 
 
-def test_served_results_match_solo_and_oracle():
+@pytest.mark.parametrize("tile_min_queue", [1, 0, 1000], ids=["tile", "mixed", "single"])
+def test_served_results_match_solo_and_oracle(tile_min_queue):
+    # tile_min_queue 1: every request shares the tile; 0 (default 4): requests run one by one on
+    # the single right-hand-side path until 4 wait on an idle graph; 1000: nearly always single
     graphs = _graphs((3000, 20000), seed=5151)
-    srv = di.di_server_create([g for g, _ in graphs], d=D, slots=8, sweeps_per_step=3)
+    srv = di.di_server_create([g for g, _ in graphs], d=D, slots=8, sweeps_per_step=3,
+                              tile_min_queue=tile_min_queue)
     rng = workloads.u64(99, 1, 400)
     reqs = []
     tols = (1e-4, 1e-6, 1e-8)
@@ -61,14 +66,14 @@ def test_served_results_match_solo_and_oracle():
         solo, sinfo = di.di_solve(g, B, D, tol)
         assert np.abs(solo - X).sum() <= 2 * bound           # against the same request alone
     srv.close()
-    # 40 requests over 2 x 8 slots: most of them waited for a slot while others were running
+    # 40 requests over 2 workers: some of them waited while others were running
     assert max(queue_ms) > 0.0
 
 
 def test_continuous_admission_under_a_request_stream():
     graphs = _graphs((20000,), seed=6161)
     g, og = graphs[0]
-    srv = di.di_server_create([g], d=D, slots=4, sweeps_per_step=2)
+    srv = di.di_server_create([g], d=D, slots=4, sweeps_per_step=2, tile_min_queue=1)
     done = []
     lock = threading.Lock()
 

@@ -130,17 +130,36 @@ def test_heavy_nodes_push_and_pull():
     assert rel_l1(X, ref) <= 1e-10
 
 
+@pytest.mark.parametrize("fluid", [di.DI_FLUID_F32, di.DI_FLUID_F64], ids=["f32inc", "f64"])
 @pytest.mark.parametrize("n,m,seed", [(1, 1, 11), (40, 100, 12), (5000, 20000, 13), (30000, 120000, 14)])
-def test_power_iteration_matches_oracle(n, m, seed):
+def test_power_iteration_matches_oracle(n, m, seed, fluid):
     n, src, dst = workloads.small_random_graph(n, m, seed=seed)
     g, og = gpu_graph(n, src, dst)
     B = workloads.uniform(seed, 22, n) * (1 - D) / n
-    X, info = di.di_power_iter(g, B, D, 1e-14)
+    X, info = di.di_power_iter_ex(g, B, D, 1e-14, fluid=fluid)
     Xo, oinfo, ok = oracle.pi(og, B, D, 1e-14)
     assert ok and rel_l1(X, Xo) <= 1e-12
-    # Jacobi from X_0 = 0: the same iterates up to summation order, so the same count (+-1 when
-    # the residual lands next to tol)
+    # Jacobi from X_0 = 0: the same iterates up to rounding, so the same count (+-1 when the
+    # residual lands next to tol)
     assert abs(info["sweeps"] - oinfo["iterations"]) <= 1
+    assert info["residual_l1"] <= 1e-14
+
+
+def test_power_iteration_residual_is_the_exact_next_increment():
+    # the FP32-increment path reports ||B + P.X - X||_1 of the X it returns (the oracle's residual
+    # of that X), which is PI's ||X_(k+1) - X_k||_1 taken exactly
+    n, src, dst = workloads.small_random_graph(20000, 90000, seed=15)
+    g, og = gpu_graph(n, src, dst)
+    B = workloads.uniform(15, 22, n) * (1 - D) / n
+    for tol in (1e-6, 1e-9, 1e-12):
+        X, info = di.di_power_iter(g, B, D, tol)
+        _, norm = oracle.residual(og, B, D, X)
+        assert info["residual_l1"] <= tol
+        assert abs(norm - info["residual_l1"]) <= 1e-6 * norm + 1e-15
+    # without the exact certification the residual is the last FP32 increment's norm
+    X, info = di.di_power_iter_ex(g, B, D, 1e-9, refine=-1)
+    Xo, _, _ = oracle.pi(og, B, D, 1e-14)
+    assert info["refine_rounds"] == 0 and rel_l1(X, Xo) <= 1e-6
 
 
 def test_history_never_exceeds_solution_and_error_bound():

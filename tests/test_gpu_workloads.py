@@ -9,7 +9,7 @@
   web_n10m_t, web_n10m_e, serve_4g: the bench legs' graphs at full size (transposed: DI-SOP and
             PI'; E-dominated: the pre-diffused DI-SOP; serving: one request per graph and
             tolerance), each against the oracle.
-  web_n10m: N=10M, ~141M links: bit-exact graph build; DI-SOP at d=0.85 against the oracle's
+  web_n10m: N=10M, ~150M links: bit-exact graph build; DI-SOP at d=0.85 against the oracle's
             DI-SOP fixed point; d=0.95 certified by the oracle's exact residual of the GPU
             history (||X - H||_1 <= ||B + P.H - H||_1 / (1 - d), a bound that holds at any size).
 """

@@ -2,7 +2,8 @@
 
 Each case plants one mistake in a copy of oracle/oracle.c (a dropped term, a wrong sign, a wrong
 index or operand), compiles the copy on the CPU and runs the whole pin suite
-(test_oracle_build.py, test_oracle_solve.py, test_oracle_e.py, test_oracle_resume.py) against it.
+(test_oracle_build.py, test_oracle_solve.py, test_oracle_e.py, test_oracle_resume.py,
+test_oracle_refresh.py) against it.
 Every mutant must fail at least one pin.
 """
 import os
@@ -66,6 +67,12 @@ MUTANTS = {
     "e_prepass_id_order": ("if (e_mask[i] && e_level[i] == l) {", "if (e_mask[i] && l == 0) {"),
     # E pre-diffusion skips the last level
     "e_prepass_short": ("for (int32_t l = 0; l < n_levels; l++)", "for (int32_t l = 0; l + 1 < n_levels; l++)"),
+    # refreshed DI-SOP: r taken again one node late
+    "refresh_late": ("if (r_every > 0 && i > 0 && i % r_every == 0) r_cycle = sum_fluid(n, F);",
+                     "if (r_every > 0 && i > 1 && i % r_every == 1) r_cycle = sum_fluid(n, F);"),
+    # refreshed DI-SOP: the refresh sums B instead of the current fluid (r never moves)
+    "refresh_stale": ("if (r_every > 0 && i > 0 && i % r_every == 0) r_cycle = sum_fluid(n, F);",
+                      "if (r_every > 0 && i > 0 && i % r_every == 0) r_cycle = r;"),
 }
 
 
@@ -86,7 +93,8 @@ def test_pins_catch_planted_mistake(name, tmp_path):
              os.path.join(ROOT, "tests", "test_oracle_build.py"),
              os.path.join(ROOT, "tests", "test_oracle_solve.py"),
              os.path.join(ROOT, "tests", "test_oracle_e.py"),
-             os.path.join(ROOT, "tests", "test_oracle_resume.py")],
+             os.path.join(ROOT, "tests", "test_oracle_resume.py"),
+             os.path.join(ROOT, "tests", "test_oracle_refresh.py")],
             cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
     except subprocess.TimeoutExpired:
         return  # a mutant that no longer converges within the cycle cap is caught too

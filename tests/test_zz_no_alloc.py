@@ -1,8 +1,8 @@
 """The zero-allocation residual entry point (di_residual_noalloc) agrees with the existing solve.
 
-Callers that cannot allocate (work recorded into a CUDA graph by stream capture, hosts whose
-own pool owns all device memory) use di_residual_noalloc, which keeps its scratch in a static
-device array. di_solve with refinement reports the exact residual ||B + P.H - H||_1 of the
+Callers that cannot allocate (hosts whose own pool owns all device memory, code that must not
+add the device-wide synchronisation cudaMalloc may cause) use di_residual_noalloc, which keeps
+its scratch in a static device array. di_solve with refinement reports the exact residual ||B + P.H - H||_1 of the
 history it returns; the zero-allocation call on the same H must report the same norm, on two
 calls in a row (the shared scratch must be left ready by the first call). This file is collected
 last so that a failure here comes after every other test has run.
@@ -71,3 +71,26 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(di.DiError) as e:
         di.di_residual_noalloc(n, rp_in, col_in, out_deg, B.cpu(), 0.85, B, norm)
     assert e.value.status == 1
+
+
+def test_noalloc_rejects_short_or_misplaced_arrays():
+    """The C call trusts n, so the binding checks every length against it before the call: a
+    history, right-hand side or output shorter than n, or row pointers of the wrong length,
+    raise DiError instead of reading or writing past the arrays."""
+    torch, n, src, dst, g, (rp_in, col_in, out_deg) = _setup()
+    B = torch.zeros(n, dtype=torch.float64, device="cuda")
+    H = torch.zeros(n, dtype=torch.float64, device="cuda")
+    norm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    bad = [dict(H=H[: n - 1]), dict(B=B[: n // 2]), dict(rp_in=rp_in[:n]), dict(out_deg=out_deg[:10]),
+           dict(norm_out=norm[:0]), dict(Fstar_out=torch.empty(n - 3, dtype=torch.float64, device="cuda"))]
+    for kw in bad:
+        args = dict(rp_in=rp_in, col_in=col_in, out_deg=out_deg, B=B, H=H, norm_out=norm)
+        args.update(kw)
+        with pytest.raises(di.DiError) as e:
+            di.di_residual_noalloc(n, args["rp_in"], args["col_in"], args["out_deg"], args["B"], 0.85, args["H"],
+                                   args["norm_out"], Fstar_out=args.get("Fstar_out"))
+        assert e.value.status == 1, kw
+    # the checked call still works afterwards on the shared scratch
+    di.di_residual_noalloc(n, rp_in, col_in, out_deg, B, 0.85, H, norm)
+    torch.cuda.synchronize()
+    assert float(norm.item()) == 0.0

@@ -106,12 +106,13 @@ WORKLOADS = {
     "web_n1m": dict(spec=GraphSpec(n=1_000_000, p_dangling=0.2, cap=5000, mean_out=10.0, p_local=0.7,
                                    chain_frac=0.1, seed=BASE_SEED + 1),
                     d=0.85, tol=1e-8, fluid="f32"),
-    # single solve, 10M nodes, ~150M links, same generator, d in {0.85, 0.95}
-    "web_n10m": dict(spec=GraphSpec(n=10_000_000, p_dangling=0.2, cap=5000, mean_out=18.75, p_local=0.7,
+    # single solve, 10M nodes, ~150M links after dedupe (150.5M), same generator, d in {0.85, 0.95}
+    "web_n10m": dict(spec=GraphSpec(n=10_000_000, p_dangling=0.2, cap=5000, mean_out=20.0, p_local=0.7,
                                     chain_frac=0.1, seed=BASE_SEED + 2),
                      d=0.85, tol=1e-8, fluid="f32"),
-    # batched personalised PageRank: 2M nodes, ~30M links, 256 seed sets of 1..1000 nodes
-    "ppr_n2m_k256": dict(spec=GraphSpec(n=2_000_000, p_dangling=0.2, cap=5000, mean_out=18.75, p_local=0.7,
+    # batched personalised PageRank: 2M nodes, ~30M links after dedupe (30.0M), 256 seed sets of
+    # 1..1000 nodes
+    "ppr_n2m_k256": dict(spec=GraphSpec(n=2_000_000, p_dangling=0.2, cap=5000, mean_out=20.0, p_local=0.7,
                                         chain_frac=0.1, seed=BASE_SEED + 3),
                          d=0.85, tol=1e-6, fluid="f32", k=256, max_seeds=1000),
     # the 1M- and 10M-node graphs with every link reversed (P transposed): the heavy-tailed
@@ -119,16 +120,16 @@ WORKLOADS = {
     "web_n1m_t": dict(spec=GraphSpec(n=1_000_000, p_dangling=0.2, cap=5000, mean_out=10.0, p_local=0.7,
                                      chain_frac=0.1, seed=BASE_SEED + 1, transpose=True),
                       d=0.85, tol=1e-8, fluid="f32"),
-    "web_n10m_t": dict(spec=GraphSpec(n=10_000_000, p_dangling=0.2, cap=5000, mean_out=18.75, p_local=0.7,
+    "web_n10m_t": dict(spec=GraphSpec(n=10_000_000, p_dangling=0.2, cap=5000, mean_out=20.0, p_local=0.7,
                                       chain_frac=0.1, seed=BASE_SEED + 2, transpose=True),
                        d=0.85, tol=1e-8, fluid="f32"),
     # a web-like graph where E dominates (E/N about 0.87, 22 levels; the paper's Dataset 2 has
     # E/N = 0.91): 87% of the nodes sit on zero-in-degree chains of 20 that feed a small core
-    "web_n10m_e": dict(spec=GraphSpec(n=10_000_000, p_dangling=0.02, cap=5000, mean_out=18.75, p_local=0.7,
+    "web_n10m_e": dict(spec=GraphSpec(n=10_000_000, p_dangling=0.02, cap=5000, mean_out=20.0, p_local=0.7,
                                       chain_frac=0.87, chain_min=20, chain_max=20, seed=BASE_SEED + 5),
                        d=0.85, tol=1e-8, fluid="f32"),
     # serving: four resident graphs
-    "serve_4g": dict(specs=[GraphSpec(n=n, p_dangling=0.2, cap=5000, mean_out=18.75, p_local=0.7,
+    "serve_4g": dict(specs=[GraphSpec(n=n, p_dangling=0.2, cap=5000, mean_out=20.0, p_local=0.7,
                                       chain_frac=0.1, seed=BASE_SEED + 4 + 1000 * i)
                             for i, n in enumerate((100_000, 500_000, 2_000_000, 5_000_000))],
                      d=0.85, tols=(1e-4, 1e-6, 1e-8), max_seeds=1000),
