@@ -351,7 +351,9 @@ typedef struct {
  * di_autotune — times short probe solves on graph g (damping d, uniform right-hand sides) and
  * keeps the fastest push split for later solves on g. what: bit 0 tunes the single right-hand
  * side push (row cut-off, heavy cut-off, chunk length; probe: a DI-SOP solve to 1e-3 ||B||_1,
- * median of 3), bit 1 the batched tile width and its push split (probes of 6 and 24 sweeps);
+ * median of 3), bit 1 the batched tile width and its push split (probes of 6 and 24 sweeps),
+ * bit 2 sets the single right-hand-side split to out's push_row, heavy_cut and heavy_chunk
+ * without probing (heavy_cut >= 1024, 256 <= heavy_chunk <= heavy_cut; to repeat a tuned setting);
  * 0 only reports the current values. Untuned graphs use 64 / 4096 / 1024; a graph's first
  * batched call with rhs_tile 0 tunes the batched setting itself. out (nullable) receives the
  * values in use. Errors: DI_ERR_INVALID_ARG, DI_ERR_BUSY, DI_ERR_OOM, DI_ERR_CUDA.

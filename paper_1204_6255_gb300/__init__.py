@@ -300,10 +300,14 @@ def di_graph_set_workspace(g: Graph, kind: int, workspace=None):
     g.workspaces[int(kind)] = workspace
 
 
-def di_autotune(g: Graph, d: float = 0.85, what: int = 3) -> dict:
+def di_autotune(g: Graph, d: float = 0.85, what: int = 3, set_split=None) -> dict:
     """Tune the push split on this graph (bit 0: single right-hand side, bit 1: batched; 0 only
-    reports). Returns the values in use."""
+    reports). set_split=(row, heavy_cut, heavy_chunk) sets the single right-hand-side split
+    without probing. Returns the values in use."""
     t = Tuning()
+    if set_split is not None:
+        t.push_row, t.heavy_cut, t.heavy_chunk = (int(x) for x in set_split)
+        what |= 4
     _check(load().di_autotune(g.handle, float(d), int(what), ctypes.byref(t), None))
     return t.as_dict()
 

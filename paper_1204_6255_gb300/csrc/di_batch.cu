@@ -530,12 +530,26 @@ di_status di_autotune(di_graph *g, double d, int32_t what, di_tuning *out, void 
     return guarded([&] {
         DI_REQUIRE(g != nullptr, DI_ERR_INVALID_ARG, "graph is NULL");
         DI_REQUIRE(d >= 0.0 && d < 1.0, DI_ERR_INVALID_ARG, "d must be in [0, 1) (got %g)", d);
-        DI_REQUIRE(what >= 0 && what <= 3, DI_ERR_INVALID_ARG, "what must be 0..3 (got %d)", what);
+        DI_REQUIRE(what >= 0 && what <= 7, DI_ERR_INVALID_ARG, "what must be 0..7 (got %d)", what);
+        if (what & 4) {
+            DI_REQUIRE(out != nullptr, DI_ERR_INVALID_ARG, "setting a split needs the values in out");
+            const bool row_ok = out->push_row >= 1 && out->push_row <= 1 << 20;
+            const bool heavy_ok = out->heavy_cut >= kPushHeavyMin && out->heavy_cut <= 1 << 30;
+            const bool chunk_ok = out->heavy_chunk >= kHeavyChunkMin && out->heavy_chunk <= out->heavy_cut;
+            DI_REQUIRE(row_ok && heavy_ok && chunk_ok, DI_ERR_INVALID_ARG,
+                       "push split out of range (row %d, heavy cut %d >= %d, chunk %d in [%d, heavy cut])",
+                       out->push_row, out->heavy_cut, kPushHeavyMin, out->heavy_chunk, kHeavyChunkMin);
+        }
         std::unique_lock<std::mutex> lk(g->mu, std::try_to_lock);
         DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
         DeviceGuard dg(g->dev.device);
         cudaStream_t s = (cudaStream_t)stream;
         double single_ms = 0.0;
+        if (what & 4) {
+            g->tune_single.row = out->push_row;
+            g->tune_single.heavy = out->heavy_cut;
+            g->tune_single.chunk = out->heavy_chunk;
+        }
         if (what & 1) autotune_single(g, d, s, &single_ms);
         if (what & 2) {
             if (g->bws) g->bws->tuned_T = 0;   // tune again

@@ -498,44 +498,6 @@ __global__ void k_window_reach(const int64_t *rp_in, const int32_t *col_in, int3
     atomicMax(max_cnt, best);
 }
 
-// Largest number of in-links that a hub receives from the sources of one kSelChunk-id segment
-// (the push's hub slots sum at most that many shares per segment before they are folded into
-// FP32). One warp per hub slot; its lanes walk the segments the hub's sorted in-row touches,
-// counting each by two binary searches.
-__global__ void k_hub_reach(const int64_t *rp_in, const int32_t *col_in, const int32_t *hub_ids, int chunk,
-                            unsigned int *max_cnt) {
-    const int lane = (int)lane_id();
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned int best = 0;
-    for (int64_t h = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; h < kHubSlots; h += nw) {
-        const int32_t v = hub_ids[h];
-        if (v < 0) continue;
-        const int64_t b = rp_in[v], e = rp_in[v + 1];
-        if (e <= b) continue;
-        const int32_t s0 = col_in[b] / chunk, s1 = col_in[e - 1] / chunk;
-        for (int32_t sg = s0 + lane; sg <= s1; sg += 32) {
-            int64_t lo = b, hi = e;
-            while (lo < hi) {   // first link from a source >= sg * chunk
-                const int64_t m = (lo + hi) >> 1;
-                if (col_in[m] < (int64_t)sg * chunk) lo = m + 1; else hi = m;
-            }
-            int64_t lo2 = lo, hi2 = e;
-            while (lo2 < hi2) {   // first link from a source >= (sg + 1) * chunk
-                const int64_t m = (lo2 + hi2) >> 1;
-                if (col_in[m] < (int64_t)(sg + 1) * chunk) lo2 = m + 1; else hi2 = m;
-            }
-            const unsigned int c = (unsigned int)(lo2 - lo);
-            best = c > best ? c : best;
-        }
-    }
-    best = max(best, __shfl_xor_sync(kFull, best, 16));
-    best = max(best, __shfl_xor_sync(kFull, best, 8));
-    best = max(best, __shfl_xor_sync(kFull, best, 4));
-    best = max(best, __shfl_xor_sync(kFull, best, 2));
-    best = max(best, __shfl_xor_sync(kFull, best, 1));
-    if (lane == 0 && best) atomicMax(max_cnt, best);
-}
-
 // (level << bits | id) keys of the nodes of E, and back to ids after sorting
 __global__ void k_e_keys(const int32_t *order, int64_t cnt, const int32_t *level, int bits, uint64_t *keys) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
@@ -716,18 +678,7 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
         int qb = 30;
         while (qb > 1 && (uint64_t)(rc ? rc : 1) * ((1ull << qb) - 1) > 0x7fffffffull) qb--;
         g->win_qbits = qb;
-        // the same for the hub slots: the most in-links of a hub from one segment's sources
-        DI_CHECK_CUDA(cudaMemsetAsync(reach_cnt, 0, sizeof(unsigned int), s));
-        k_hub_reach<<<(kHubSlots * 32 + 255) / 256, 256, 0, s>>>(g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(),
-                                                               g->hub_ids.as<int32_t>(), kSelChunkNodes, reach_cnt);
-        unsigned int hc = 0;
-        DI_CHECK_CUDA(cudaMemcpyAsync(&hc, reach_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
-        DI_CHECK_CUDA(cudaGetLastError());
-        DI_CHECK_CUDA(cudaStreamSynchronize(s));
-        g->hub_reach_max = (int32_t)hc;
-        int hb = 30;
-        while (hb > 1 && (uint64_t)(hc ? hc : 1) * ((1ull << hb) - 1) > 0x7fffffffull) hb--;
-        g->hub_qbits = hb < qb ? hb : qb;
+
     }
 
     // E by peeling; each level's frontier is appended to e_order, so e_order lists E grouped by
@@ -784,6 +735,16 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
         k_e_unkey<<<grid_for(e_total, 256, dev), 256, 0, s>>>(keys.as<uint64_t>(), e_total, bits, eo);
         DI_CHECK_CUDA(cudaGetLastError());
         DI_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    // the id span of each level (its first and last id, now that levels are sorted)
+    g->e_level_span.assign(g->e_level_off.size() > 0 ? g->e_level_off.size() - 1 : 0, 0);
+    for (size_t lv = 0; lv + 1 < g->e_level_off.size(); lv++) {
+        int32_t ends[2] = {0, 0};
+        DI_CHECK_CUDA(cudaMemcpyAsync(&ends[0], eo + g->e_level_off[lv], sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        DI_CHECK_CUDA(cudaMemcpyAsync(&ends[1], eo + g->e_level_off[lv + 1] - 1, sizeof(int32_t),
+                                      cudaMemcpyDeviceToHost, s));
+        DI_CHECK_CUDA(cudaStreamSynchronize(s));
+        g->e_level_span[lv] = (int64_t)ends[1] - ends[0] + 1;
     }
 
     // heavy in-CSR rows for the pull kernels

@@ -172,6 +172,8 @@ struct SolveCtl {
     unsigned long long front_total;  // frontier entries over all sweeps
     int32_t split;            // 1: the first reduction raises tol to sqrt(tol * r), the point of
                               //    the first refinement of a refined FP32 solve
+    int32_t big_segs;         // frontier segments of at least kBigSegment entries (latest selection)
+    int32_t small_segs;       // the other segments
     int32_t subs;             // selections so far (a sweep is r_refresh selections, one per
                               //    part of the node range)
     int32_t sweep_selected;   // nodes the parts of the current sweep selected so far
@@ -210,7 +212,6 @@ constexpr int kPullChunk = 4096;    // edges per heavy-row chunk of the pull
 constexpr int kReduceBlocks = 1024; // partial sums of the last-block-done reductions
 constexpr int kHubSlots = 2048;     // shared-memory hub cache of the push kernels
 constexpr int kWinReach = 4096;     // push window: every source-target pair it takes is closer
-constexpr int kSelChunkNodes = 2048;   // source nodes of a push segment (the selection's chunk)
 
 // Per-graph state for single-RHS solves and power iteration.
 struct Workspace {
@@ -269,6 +270,7 @@ struct di_graph {
     di::DevBuf e_level;            // int32
     di::DevBuf e_order;            // int32[N]: its first |E| entries list E grouped by level
     std::vector<int64_t> e_level_off;  // host: level l of E is e_order[off[l], off[l + 1])
+    std::vector<int64_t> e_level_span; // host: ids spanned by level l (last - first + 1)
     // heavy rows of the in-CSR (in-degree > kPullHeavy), for the pull kernels
     int32_t n_heavy_in = 0;
     int32_t n_heavy_in_chunks = 0;
@@ -282,8 +284,6 @@ struct di_graph {
     di::DevBuf hub_ids;            // int32[kHubSlots]: hub node per hash slot, -1 when empty
     int32_t win_reach_max = 0;     // most in-links of a non-hub node from sources < kWinReach ids away
     int32_t win_qbits = 20;        // push window: |fixed-point share| < 2^win_qbits (no int32 overflow)
-    int32_t hub_reach_max = 0;     // most in-links of a hub from the sources of one segment
-    int32_t hub_qbits = 20;        // push hub slots: the same bound (<= win_qbits)
     di::DevBuf col_push;           // int32[L]: col_out with bit 31 set on links into a hub
     std::mutex mu;                 // serialises use of the workspaces
     di::Workspace ws;

@@ -19,6 +19,7 @@
 // free up, so requests of different arrival times share sweeps, and the workers of different
 // graphs run concurrently on the device. Each column is an independent problem; batch-mates
 // only change which nodes a sweep visits, not the fixed point.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <condition_variable>
@@ -427,7 +428,15 @@ di_status di_server_create(di_graph *const *graphs, int32_t n_graphs, const di_s
             DeviceGuard dg(graphs[i]->dev.device);
             ensure_batch(graphs[i], w->w, T);
             w->col_out.ensure(sizeof(double) * (size_t)graphs[i]->n);
-            DI_CHECK_CUDA(cudaStreamCreateWithFlags(&w->s, cudaStreamNonBlocking));
+            // stream priority by graph size: the largest graph's kernels are scheduled first when
+            // workers overlap on the device, since its requests are the longest and make the
+            // latency tail; the others are short whatever their priority
+            int lo = 0, hi = 0;   // least and greatest priority (greatest is the smaller number)
+            DI_CHECK_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            int rank = 0;         // graphs larger than this one
+            for (int j = 0; j < n_graphs; j++) rank += graphs[j]->n > graphs[i]->n ? 1 : 0;
+            const int prio = std::max(hi, std::min(lo, hi + rank));
+            DI_CHECK_CUDA(cudaStreamCreateWithPriority(&w->s, cudaStreamNonBlocking, prio));
             srv->workers.push_back(std::move(w));
         }
         for (auto &w : srv->workers) {

@@ -169,6 +169,8 @@ __global__ void k_reduce(const T *F, int32_t n, double *partials, SolveCtl *ctl,
         ctl->last_selected = 0;
         ctl->front_total += (unsigned long long)(front_entries(ctl->front_chunks) + ctl->heavy_count);
         ctl->front_chunks = 0;
+        ctl->big_segs = 0;
+        ctl->small_segs = 0;
         ctl->heavy_count = 0;
         ctl->heavy_chunks = 0;
         ctl->chunk_next = 0;
@@ -340,6 +342,19 @@ __device__ __forceinline__ int window_exponent(float mean_abs, int mean_bits) {
 }
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }   // -126 <= k <= 127
 
+// Frontier segment records: the push takes segments in record order, so segments of at least
+// kBigSegment entries are written from the front of the record array and the others from its
+// back (index seg_cap - 1 downward); the push reads the front ones first, so the long segments
+// start early and the short ones fill the end of the kernel.
+constexpr int kBigSegment = 512;
+__device__ __forceinline__ int segment_slot(SolveCtl *ctl, int entries, int seg_cap) {
+    return entries >= kBigSegment ? atomicAdd(&ctl->big_segs, 1) : seg_cap - 1 - atomicAdd(&ctl->small_segs, 1);
+}
+__device__ __forceinline__ int segment_at(const SolveCtl *ctl, int ci, int seg_cap) {
+    const int big = ctl->big_segs;
+    return ci < big ? ci : seg_cap - 1 - (ci - big);
+}
+
 // Nodes are visited in chunks of kSelChunk consecutive ids per block iteration; warp w of the
 // block owns the kSelWarpNodes consecutive ids from base + w * kSelWarpNodes. The frontier
 // entries of a chunk are compacted with one atomic per chunk, so the frontier is id-sorted
@@ -350,7 +365,6 @@ constexpr int kTrackResync = 8;      // an exact reduction at least every kTrack
 constexpr double kTrackBand = 16.0;  // ... and at every sweep once r <= kTrackBand * tol
 constexpr int kSelWarpNodes = 32 * kSelItems;
 constexpr int kSelChunk = 8 * kSelWarpNodes;   // 256 threads
-static_assert(kSelChunk == kSelChunkNodes, "the build's hub bound counts sources per selection chunk");
 constexpr int kSelMinBlocks = 4;
 template <class T>
 constexpr int kSelBatch = sizeof(T) == 4 ? 4 : 2;   // packed rounds of 32 visits whose history loads fly together
@@ -361,7 +375,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                                                             int32_t *heavy_id, T *heavy_s, int32_t *heavy_cstart,
                                                             int32_t *heavy_chunk, int4 *chunks, int win_mean_bits,
                                                             int32_t node_lo, int32_t node_hi, int sweep_end,
-                                                            int heavy_cut, int heavy_len) {
+                                                            int heavy_cut, int heavy_len, int seg_cap) {
     __shared__ double scratch[32];
     __shared__ unsigned long long scratch_u[32];
     // Per warp, the selected nodes of its range packed in id order: fluid, degree word and
@@ -548,7 +562,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                 for (int w = 0; w < 8; w++) abs_tot += s_wabs[w];
                 const unsigned long long fc = atomicAdd(&ctl->front_chunks, (1ull << kFrontBits) | (unsigned)run);
                 s_chunk_base = front_entries(fc);
-                chunks[front_segments(fc)] =
+                chunks[segment_slot(ctl, run, seg_cap)] =
                     make_int4((int)base, s_chunk_base, run, window_exponent(abs_tot / (float)run, win_mean_bits));
             }
         }
@@ -695,7 +709,8 @@ __global__ void __launch_bounds__(256) k_e_select(const int32_t *nodes, int32_t 
                                                   const int32_t *out_info, int32_t n, SolveCtl *ctl,
                                                   int32_t *front_id, float *front_s, int32_t *heavy_id,
                                                   float *heavy_s, int32_t *heavy_cstart, int32_t *heavy_chunk,
-                                                  int4 *chunks, int win_mean_bits, int heavy_cut, int heavy_len) {
+                                                  int4 *chunks, int win_mean_bits, int heavy_cut, int heavy_len,
+                                                  int seg_cap) {
     constexpr int kPerWarp = kSelChunk / 8;   // a chunk holds at most kSelChunk nodes of a level
     __shared__ int32_t s_id[8][kPerWarp];
     __shared__ float s_sh[8][kPerWarp];
@@ -789,7 +804,7 @@ __global__ void __launch_bounds__(256) k_e_select(const int32_t *nodes, int32_t 
                 // one atomic reserves the chunk's frontier entries and its segment slot
                 const unsigned long long fc = atomicAdd(&ctl->front_chunks, (1ull << kFrontBits) | (unsigned)run);
                 s_base = front_entries(fc);
-                chunks[front_segments(fc)] = make_int4(c * kSelChunk, s_base, run,
+                chunks[segment_slot(ctl, run, seg_cap)] = make_int4(c * kSelChunk, s_base, run,
                                                        window_exponent(abs_tot / (float)run, win_mean_bits));
             }
         }
@@ -811,13 +826,16 @@ __global__ void __launch_bounds__(256) k_e_select(const int32_t *nodes, int32_t 
     }
 }
 
-constexpr int64_t kELevelSelectMin = 16384;   // levels of E at least this large take k_e_select
+constexpr int64_t kELevelSelectMin = 16384;   // levels of E at least this large ...
+constexpr int64_t kELevelDensity = 512;        // ... and this dense (nodes per kSelChunk ids) take k_e_select
 
 // Clears the frontier counters after a pre-diffusion level's push (the sweeps' reduction does
 // this after every sweep).
 __global__ void k_front_reset(SolveCtl *ctl) {
     ctl->front_total += (unsigned long long)(front_entries(ctl->front_chunks) + ctl->heavy_count);
     ctl->front_chunks = 0;
+    ctl->big_segs = 0;
+    ctl->small_segs = 0;
     ctl->heavy_count = 0;
     ctl->heavy_chunks = 0;
     ctl->chunk_next = 0;
@@ -922,6 +940,7 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
 // atomic per non-zero group, so a dense segment issues a fraction of the global atomics of a
 // link-by-link push. Shares too large for the segment's fixed point take the direct path, and
 // links into hubs always go to the hub cache (the window's overflow bound leaves hubs out).
+constexpr int kHubCopies = 1;   // copies of the push's shared-memory hub cache
 constexpr int kHalo = 1024;
 constexpr int kWin = kSelChunk + 2 * kHalo;     // 4096 int32 slots, 16 KB
 constexpr int kWinMinEntries = 24;              // sparser segments push link by link
@@ -933,11 +952,11 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                                                   const int64_t *__restrict__ rp_out,
                                                   const int32_t *__restrict__ col_push, const int4 *__restrict__ chunks,
                                                   const int32_t *__restrict__ hub_ids, float *F, SolveCtl *ctl,
-                                                  int win_qmax, int hub_shift, int hub_qmax, int push_row,
-                                                  int heavy_len) {
+                                                  int win_qmax, int push_row, int heavy_len, int seg_cap) {
     __shared__ __align__(16) int s_win[kWin];
-    __shared__ float s_hacc[kHubSlots];      // this block's pending additions to the hubs
-    __shared__ int s_hint[kHubSlots];        // ... from the current segment, in its hub fixed point
+    // this block's pending additions to the hubs, kHubCopies copies for alternating warps (the
+    // hubs are the hottest addresses, and FP32 shared atomics retry when another lane wrote first)
+    __shared__ float s_hacc[kHubCopies][kHubSlots];
     __shared__ int s_off[8][33];
     // per entry of a warp's batch: {row start - link offset, source id, share, fixed-point share}
     __shared__ int4 s_rec[8][32];
@@ -948,33 +967,18 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int q = tid; q < kHubSlots; q += 256) {
-        s_hacc[q] = 0.f;
-        s_hint[q] = 0;
-    }
+    for (int q = tid; q < kHubCopies * kHubSlots; q += 256) (&s_hacc[0][0])[q] = 0.f;
     __syncthreads();
+    float *my_hacc = s_hacc[w % kHubCopies];
     // a link to a far target (jr: target id with bit 31 set when the target is a hub): hubs
     // (high in-degree nodes) collect in shared memory, the rest goes to F directly
     auto far_add = [&](int32_t jr, float v) {
-        if (jr < 0) atomicAdd(&s_hacc[hub_slot(jr & 0x7fffffff)], v);
+        if (jr < 0) atomicAdd(&my_hacc[hub_slot(jr & 0x7fffffff)], v);
         else red_keep(&F[jr], v, keep);
     };
-    // the same within a segment: a hub slot takes at most hub_reach_max shares per segment (one
-    // per source; the graph build measures the bound), so it adds integers in the segment's hub
-    // fixed point (native shared atomics; FP32 ones are compare-and-swap loops) and is folded
-    // into the FP32 cache when the segment ends. A share that rounds to 0 or is too large for
-    // the fixed point takes the FP32 path.
-    float hub_scale = 1.f;
-    auto seg_far_add = [&](int32_t jr, float v) {
-        if (jr < 0) {
-            const int slot = hub_slot(jr & 0x7fffffff);
-            const int q = __float2int_rn(v * hub_scale);
-            if (q != 0 && q > -hub_qmax && q < hub_qmax) atomicAdd(&s_hint[slot], q);
-            else atomicAdd(&s_hacc[slot], v);
-        } else {
-            red_keep(&F[jr], v, keep);
-        }
-    };
+    // The hub cache stays FP32 (compare-and-swap atomics): integer hub slots, folded into FP32
+    // at every segment's end so that a per-segment bound keeps them from overflowing, were
+    // measured slower (the fold of every slot per segment costs more than the loops it saves).
 
     // nodes with more than the heavy cut-off of links: their chunks over all warps
     const int hch = ctl->heavy_chunks;
@@ -1003,13 +1007,10 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
         __syncthreads();
         const int ci = s_chunk;
         if (ci >= nchunks) break;
-        const int4 ch = chunks[ci];
+        const int4 ch = chunks[segment_at(ctl, ci, seg_cap)];
         const int cstart = ch.y, clen = ch.z;
         const bool use_win = clen >= kWinMinEntries;
         const float win_scale = pow2f(ch.w), win_unit = pow2f(-ch.w);   // fixed point <-> FP32
-        const int hub_k = max(-126, min(126, ch.w - hub_shift));
-        hub_scale = pow2f(hub_k);
-        const float hub_unit = pow2f(-hub_k);
         const int lo = max(0, ch.x - kHalo) & ~3;
         if (use_win) {
             for (int q = tid; q < kWin / 4; q += 256) reinterpret_cast<int4 *>(s_win)[q] = make_int4(0, 0, 0, 0);
@@ -1057,7 +1058,7 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                         if (k0 + 32 * v >= rd || (j == ru && !loops)) continue;
                         const unsigned off = (unsigned)(j - lo);
                         if (rq != 0 && jr[v] >= 0 && off < (unsigned)kWin) atomicAdd(&s_win[off], rq);
-                        else seg_far_add(jr[v], rs);
+                        else far_add(jr[v], rs);
                     }
                 }
             }
@@ -1114,20 +1115,12 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                     if (e0 + v >= total || (j == uu[v] && !loops)) continue;
                     const unsigned off = (unsigned)(j - lo);
                     if (qq[v] != 0 && jr[v] >= 0 && off < (unsigned)kWin) atomicAdd(&s_win[off], qq[v]);
-                    else seg_far_add(jr[v], ss[v]);
+                    else far_add(jr[v], ss[v]);
                 }
             }
             __syncwarp();
         }
         __syncthreads();
-        // the segment's hub integers into the FP32 hub cache (each slot by one thread)
-        for (int q = tid; q < kHubSlots; q += 256) {
-            const int v = s_hint[q];
-            if (v != 0) {
-                s_hacc[q] += (float)v * hub_unit;
-                s_hint[q] = 0;
-            }
-        }
         if (use_win) {
             for (int q = tid; q < kWin / 4; q += 256) {
                 const int4 v = reinterpret_cast<const int4 *>(s_win)[q];
@@ -1139,8 +1132,12 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
         }
     }
     // one atomic per hub that received something from this block
-    for (int q = tid; q < kHubSlots; q += 256)
-        if (s_hacc[q] != 0.f) red_keep(&F[__ldg(hub_ids + q)], s_hacc[q], keep);
+    for (int q = tid; q < kHubSlots; q += 256) {
+        float v = 0.f;
+#pragma unroll
+        for (int c = 0; c < kHubCopies; c++) v += s_hacc[c][q];
+        if (v != 0.f) red_keep(&F[__ldg(hub_ids + q)], v, keep);
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1285,7 +1282,12 @@ enum { PULL_RESID = 1, PULL_INC = 2, PULL_PI64 = 3 };
 // segmented prefix over them, and one segmented scan across the 32 lanes joins rows that span
 // lanes; a row's last link writes the row's sum, so no two lanes write the same row. A row
 // that runs past a round carries into the next.
-constexpr int kPullVT = 8;
+constexpr int kPullVT = 8;        // links per lane per round (double-float and FP64 values)
+constexpr int kPullVTF32 = 8;     // ... FP32 values (half the registers per value)
+template <class Acc>
+struct PullVT {
+    static constexpr int value = sizeof(typename Acc::V) == 4 ? kPullVTF32 : kPullVT;
+};
 
 template <int MODE, class Acc, class T>
 __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in, const int32_t *__restrict__ col_in,
@@ -1297,6 +1299,7 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
                                               cudaGraphConditionalHandle hcond, int set_cond) {
     using V = typename Acc::V;
     using W = typename Acc::Wide;
+    constexpr int kPullVT = PullVT<Acc>::value;
     __shared__ V acc_s[8][32];
     __shared__ int s_off[8][33];
     __shared__ int64_t s_beg[8][32];
@@ -1345,6 +1348,7 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
             int64_t base = s_beg[warp][k];          // reloaded only when the row changes
             int key[kPullVT];
             int32_t j[kPullVT];
+            unsigned ends = 0;                      // bit v: link v is its row's last
 #pragma unroll
             for (int v = 0; v < kPullVT; v++) {
                 const int e = first + v;
@@ -1355,6 +1359,7 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
                         base = s_beg[warp][k];
                     }
                     key[v] = k;
+                    if (e + 1 == next) ends |= 1u << v;
                     j[v] = ld_stream(col_in + base + e, stream);
                 }
             }
@@ -1382,10 +1387,9 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
             // finished rows: the row's last link writes its sum
 #pragma unroll
             for (int v = 0; v < kPullVT; v++) {
-                const int e = first + v;
                 if (key[v] >= 64) continue;
                 const V fin = (join && key[v] == key[0]) ? Acc::add(cin, val[v]) : val[v];
-                if (e + 1 == s_off[warp][key[v] + 1]) acc_s[warp][key[v]] = fin;
+                if (ends >> v & 1u) acc_s[warp][key[v]] = fin;
                 val[v] = fin;
             }
             // carry for the next round: the round's last link, when its row goes on
@@ -1599,13 +1603,16 @@ static Launch launch_shape(const di_graph *g) {
     return l;
 }
 
+// Records of frontier segments a selection can write (one per kSelChunk nodes, and one more).
+static int seg_capacity(const di_graph *g) { return (int)(g->n / kSelChunk + 2); }
+
 // The solve workspace's buffers in a fixed order, each with its size for a fluid of
 // `fb` bytes per value (4: FP32, 8: FP64); `take(buffer, bytes)` allocates, binds or counts it.
 template <class Take>
 static void solve_layout(di_graph *g, Workspace &ws, size_t fb, Take &&take) {
     const size_t n = (size_t)g->n, nh = (size_t)g->n_heavy_out + 1;
     take(ws.F, fb * (n + 8));   // padded: window flushes write four floats at a time
-    take(ws.chunks, sizeof(int4) * (n / kSelChunk + 2));
+    take(ws.chunks, sizeof(int4) * (size_t)seg_capacity(g));
     take(ws.H, sizeof(double) * n);
     take(ws.B, sizeof(double) * n);
     take(ws.front_id, sizeof(int32_t) * n);
@@ -1691,7 +1698,7 @@ static void launch_sweep_body(di_graph *g, Workspace &ws, const Launch &l, cudaS
                                                ws.heavy_s.as<T>(), ws.heavy_cstart.as<int32_t>(),
                                                ws.heavy_chunk.as<int32_t>(), ws.chunks.as<int4>(),
                                                g->win_qbits - kWinHeadBits, (int32_t)lo, (int32_t)hi, last ? 1 : 0,
-                                               tune.heavy, tune.chunk);
+                                               tune.heavy, tune.chunk, seg_capacity(g));
         });
         c.run(KC_PUSH, 1, [&] {
             if (sizeof(T) == 4) {
@@ -1699,8 +1706,7 @@ static void launch_sweep_body(di_graph *g, Workspace &ws, const Launch &l, cudaS
                     ws.front_id.as<int32_t>(), ws.front_s.as<float>(), ws.heavy_id.as<int32_t>(), ws.heavy_s.as<float>(),
                     ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(), g->rp_out.as<int64_t>(),
                     g->col_push.as<int32_t>(), ws.chunks.as<int4>(), g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl,
-                    1 << g->win_qbits, g->win_qbits - g->hub_qbits, 1 << g->hub_qbits, tune.row,
-                    tune.chunk);
+                    1 << g->win_qbits, tune.row, tune.chunk, seg_capacity(g));
             } else {
                 k_push<T><<<l.push_blocks, 256, 0, s>>>(ws.front_id.as<int32_t>(), ws.front_s.as<T>(),
                                                         ws.heavy_id.as<int32_t>(), ws.heavy_s.as<T>(),
@@ -1918,7 +1924,10 @@ static void solve_impl(di_graph *g, Workspace &ws, const double *B, double d, do
             const PushTune tune = g->tune_single;
             for (size_t lv = 0; lv + 1 < g->e_level_off.size(); lv++) {
                 const int64_t at = g->e_level_off[lv], cnt = g->e_level_off[lv + 1] - at;
-                if (sizeof(T) == 4 && cnt >= kELevelSelectMin) {
+                // (a level's ids span g->e_level_span[lv]: dense levels only, else the chunks
+                // would hold a few nodes each and the push's segments would be tiny)
+                if (sizeof(T) == 4 && cnt >= kELevelSelectMin &&
+                    cnt * kSelChunk >= kELevelDensity * g->e_level_span[lv]) {
                     // a large level: select by id chunks, then the sweep's windowed push
                     const int64_t nchunk = (g->n + kSelChunk - 1) / kSelChunk;
                     const int blocks = (int)std::min<int64_t>(nchunk, (int64_t)g->dev.sms * 4);
@@ -1928,15 +1937,14 @@ static void solve_impl(di_graph *g, Workspace &ws, const double *B, double d, do
                             g->out_info.as<int32_t>(), g->n, ctl, ws.front_id.as<int32_t>(), ws.front_s.as<float>(),
                             ws.heavy_id.as<int32_t>(), ws.heavy_s.as<float>(), ws.heavy_cstart.as<int32_t>(),
                             ws.heavy_chunk.as<int32_t>(), ws.chunks.as<int4>(), g->win_qbits - kWinHeadBits,
-                            tune.heavy, tune.chunk);
+                            tune.heavy, tune.chunk, seg_capacity(g));
                     });
                     kc.run(KC_PUSH, 1, [&] {
                         k_push_win<<<l.win_blocks, 256, 0, s>>>(
                             ws.front_id.as<int32_t>(), ws.front_s.as<float>(), ws.heavy_id.as<int32_t>(),
                             ws.heavy_s.as<float>(), ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(),
                             g->rp_out.as<int64_t>(), g->col_push.as<int32_t>(), ws.chunks.as<int4>(),
-                            g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl, 1 << g->win_qbits, g->win_qbits - g->hub_qbits, 1 << g->hub_qbits, tune.row,
-                    tune.chunk);
+                            g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl, 1 << g->win_qbits, tune.row, tune.chunk, seg_capacity(g));
                     });
                     kc.run(KC_REFINE, 1, [&] { k_front_reset<<<1, 1, 0, s>>>(ctl); });
                 } else {
