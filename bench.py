@@ -25,6 +25,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -429,17 +430,31 @@ def serving_leg(di, workloads, torch, n_req=1000, fracs=(0.25, 0.5, 0.75, 1.0, 1
             finish = max(arrive[i], finish) + service[i]
             lat_p[i] = 1e3 * (finish - arrive[i])
         plain_qps = n_req / finish
-        # served, in real time
+        # served, in real time; a client thread collects results while requests arrive, so the
+        # server's pinned result buffers are recycled as a serving front end would
         ids = [None] * n_req
+        infos = [None] * n_req
+        submitted = threading.Semaphore(0)
+
+        def collect():
+            for i in range(n_req):
+                submitted.acquire()
+                infos[i] = di.di_server_wait(srv, ids[i], timeout_ms=600000)[1]
+
+        waiter = threading.Thread(target=collect)
+        waiter.start()
         t0 = time.perf_counter()
         for i, (gi, seeds, tol) in enumerate(reqs):
             delay = arrive[i] - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
             ids[i] = di.di_server_submit(srv, int(gi), seeds, tol)
+            submitted.release()
+        waiter.join()
         lat, worst, lone, by_graph = [], 0.0, 0, {}
         for i in range(n_req):
-            _, info = di.di_server_wait(srv, ids[i], timeout_ms=600000)
+            info = infos[i]
+            assert info is not None, f"request {i} was not collected"
             lat.append(info["total_ms"])
             lone += info["slot"] < 0
             by_graph.setdefault(int(reqs[i][0]), []).append(info["total_ms"])
@@ -457,7 +472,7 @@ def serving_leg(di, workloads, torch, n_req=1000, fracs=(0.25, 0.5, 0.75, 1.0, 1
                        "worst_residual_over_tol": worst})
     srv.close()
     return {"requests_per_point": n_req, "graphs": [g.n for g in graphs], "slots": slots,
-            "sweeps_per_step": sweeps_per_step, "tile_min_queue": tile_min_queue or 4, "plain_capacity_qps": capacity,
+            "sweeps_per_step": sweeps_per_step, "tile_min_queue": tile_min_queue or 16, "plain_capacity_qps": capacity,
             "plain_service_ms_mean": 1e3 * float(service.mean()), "points": points}
 
 
@@ -580,6 +595,14 @@ def run_gpu(args):
     achieved = push_bytes / (push_ms * 1e-3) / 1e9
     kernel_total = prof["select_ms"] + prof["push_ms"] + prof["reduce_ms"] + prof["refine_ms"]
     traffic, traffic_src = push_traffic()
+    # the whole solve's algorithmic bytes, the same solve: per sweep the select reads every
+    # node's F and degree word (8 B); per visit it zeroes F_i (4 B), adds to H_i (16 B) and writes
+    # a frontier entry (8 B); the push as above; each exact residual pass reads a link index and
+    # gathers H_j (12 B per link) and per row its row start, B_i, H_i and writes F_i (28 B, 32 B
+    # with d/out); setup and output: B read, F and H initialised, X written (28 B per node)
+    solve_bytes = (8.0 * n * prof["sweeps"] + 28.0 * prof["visited_nodes"]
+                   + 12.0 * prof["pushed_edges"] + 16.0 * prof["frontier_entries"]
+                   + prof["refine_rounds"] * (12.0 * st["L"] + 32.0 * n) + 28.0 * n)
 
     legs = {}
     want = set(["solvers", "small_graphs", "transposed", "e_dominated", "ppr_batch", "serving"] if args.legs == "all"
@@ -682,6 +705,13 @@ def run_gpu(args):
                      "bytes_per_launch": push_bytes, "ms_per_launch": push_ms,
                      "kernel_share": prof["push_ms"] / kernel_total if kernel_total else None,
                      "profiled_solve_kernel_ms": {k: prof[k + "_ms"] for k in ("select", "push", "reduce", "refine")}},
+        "roofline_solve": {"bound": "hbm", "bytes_per_solve": solve_bytes,
+                           "ms_per_solve": statistics.median(step_ms),
+                           "achieved": solve_bytes / (statistics.median(step_ms) * 1e-3) / 1e9, "peak": peak,
+                           "unit": "GB/s",
+                           "frac": solve_bytes / (statistics.median(step_ms) * 1e-3) / 1e9 / peak,
+                           "peak_kind": peak_kind, "sweeps": prof["sweeps"],
+                           "refine_rounds": prof["refine_rounds"]},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "legs": legs,

@@ -379,7 +379,7 @@ typedef struct {
                                     ends with DI_ERR_NOT_CONVERGED; 0 means 100000 */
     int32_t tile_min_queue;      /* a graph whose tile is idle solves its queued requests one at a
                                     time on the single right-hand-side path until this many wait;
-                                    then they share the tile's sweeps. 0 means 4; 1 always tiles */
+                                    then they share the tile's sweeps. 0 means 16; 1 always tiles */
     int64_t mem_budget;          /* device bytes for request state over all graphs (24 bytes per
                                     node and slot); slots halve until it fits; 0 means no limit */
 } di_server_opts;
@@ -402,8 +402,9 @@ typedef struct {
  * GPU are admitted between sweep steps as slots free up, so their work overlaps; the workers of
  * different graphs run concurrently. A finished request's history is copied into a pinned host
  * buffer owned by the server (one per finished request not yet collected by di_server_wait, n
- * doubles each); the request is done when that copy has completed. The graphs must outlive the
- * server.
+ * doubles each; four per graph are made at creation and reused, more only while more results
+ * wait uncollected); the request is done when that copy has completed. The graphs must outlive
+ * the server.
  * Errors: DI_ERR_INVALID_ARG, DI_ERR_OOM (mem_budget below 4 slots per graph), DI_ERR_CUDA.
  */
 di_status di_server_create(di_graph *const *graphs, int32_t n_graphs, const di_server_opts *opts,

@@ -48,6 +48,8 @@ __global__ void ks_seed_dense(const int32_t *seeds, int cnt, double share, doubl
 // Requests with a tolerance below this get an exact FP64 residual before they retire.
 constexpr double kServeExactTol = 1e-6;
 
+constexpr int kPoolStart = 4;   // pinned result buffers per worker made at server creation
+
 struct Request {
     int64_t id = 0;
     int graph = 0;
@@ -74,7 +76,7 @@ struct di_server {
     double d = 0.85;
     int sweeps_per_step = 8;
     int max_request_sweeps = 100000;
-    int tile_min_queue = 4;              // requests waiting on an idle graph before the tile runs
+    int tile_min_queue = 16;             // requests waiting on an idle graph before the tile runs
     std::vector<std::unique_ptr<di::Worker>> workers;
     std::mutex mu;                       // requests map, completion signalling
     std::condition_variable done_cv;
@@ -417,7 +419,7 @@ di_status di_server_create(di_graph *const *graphs, int32_t n_graphs, const di_s
         srv->d = d;
         srv->sweeps_per_step = o.sweeps_per_step > 0 ? o.sweeps_per_step : 8;
         srv->max_request_sweeps = o.max_request_sweeps > 0 ? o.max_request_sweeps : 100000;
-        srv->tile_min_queue = o.tile_min_queue > 0 ? o.tile_min_queue : 4;
+        srv->tile_min_queue = o.tile_min_queue > 0 ? o.tile_min_queue : 16;
         for (int i = 0; i < n_graphs; i++) {
             DI_REQUIRE(graphs[i] != nullptr, DI_ERR_INVALID_ARG, "graph %d is NULL", i);
             std::unique_ptr<Worker> w(new Worker());
@@ -428,6 +430,13 @@ di_status di_server_create(di_graph *const *graphs, int32_t n_graphs, const di_s
             DeviceGuard dg(graphs[i]->dev.device);
             ensure_batch(graphs[i], w->w, T);
             w->col_out.ensure(sizeof(double) * (size_t)graphs[i]->n);
+            // pinned result buffers made up front: pinning host memory takes milliseconds for a
+            // large graph, which a request finishing on an empty pool would otherwise wait for
+            for (int b = 0; b < kPoolStart; b++) {
+                double *p = nullptr;
+                DI_CHECK_CUDA(cudaMallocHost(&p, sizeof(double) * (size_t)graphs[i]->n));
+                w->give_buffer(p);
+            }
             // stream priority by graph size: the largest graph's kernels are scheduled first when
             // workers overlap on the device, since its requests are the longest and make the
             // latency tail; the others are short whatever their priority

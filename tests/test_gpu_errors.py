@@ -4,8 +4,9 @@ For each method on the two oracle-sized workloads (pa_n10k: N=10k, FP64 workload
 web_n1m: N=1M web-like, tol 1e-8), the GPU result X is compared with the oracle's DI-SOP solved
 to 1e-14. The contraction of P (Section 2: ||P||_1 <= 1, so ||(I - dP)^-1||_1 <= 1/(1 - d))
 gives ||X - X*||_1 <= residual/(1 - d) for the exact residual the solver reports; each measured
-error must sit under that bound (plus the oracle's own 1e-14/(1 - d)). Run with `-s` to print
-the table: one line per method with the relative L1 error, the reported residual and the bound.
+error must sit under that bound (plus the oracle's own 1e-14/(1 - d) and the rounding of the
+reported residual). Run with `-s` to print the table: one line per method with the relative L1
+error, the reported residual and the bound.
 """
 import numpy as np
 import pytest
@@ -18,6 +19,8 @@ from gpu_util import lib, rel_l1
 pytestmark = pytest.mark.gpu
 
 ORACLE_TOL = 1e-14
+# the exact residual is itself summed in double-float (about 44 bits) over terms of size ||H||_1 = O(1)
+RESID_ABS = 1e-12
 
 
 def _methods(g, B, d, tol):
@@ -50,7 +53,7 @@ def test_errors_against_the_oracle(name):
     g = di.di_graph_create(n, src, dst)
     og = oracle.build(n, src, dst)
     d, tol = cfg["d"], cfg["tol"]
-    slack = ORACLE_TOL / (1 - d)
+    slack = (ORACLE_TOL + RESID_ABS) / (1 - d)
 
     B = oracle.uniform_B(n, d)
     ref, _, _, ok = oracle.di(og, B, d, ORACLE_TOL, oracle.SOP)
@@ -78,7 +81,7 @@ def test_errors_against_the_oracle(name):
         bound = (res_b[r] / (1 - d) + slack) / np.abs(refs[r]).sum()
         assert rel_l1(Xb[r], refs[r]) <= bound * (1 + 1e-9), r
     _line(name, "ppr_batch (worst of 8)", rel_l1(Xb[worst], refs[worst]), float(res_b[worst]),
-          (tol / (1 - d) + slack) / np.abs(refs[worst]).sum())
+          (res_b[worst] / (1 - d) + slack) / np.abs(refs[worst]).sum())
 
     srv = di.di_server_create([g], d=d, slots=8)
     try:

@@ -32,10 +32,11 @@ def _graphs(sizes, seed):
     return out
 
 
-@pytest.mark.parametrize("tile_min_queue", [1, 0, 1000], ids=["tile", "mixed", "single"])
+@pytest.mark.parametrize("tile_min_queue", [1, 4, 0, 1000], ids=["tile", "mixed", "default", "single"])
 def test_served_results_match_solo_and_oracle(tile_min_queue):
-    # tile_min_queue 1: every request shares the tile; 0 (default 4): requests run one by one on
-    # the single right-hand-side path until 4 wait on an idle graph; 1000: nearly always single
+    # tile_min_queue 1: every request shares the tile; 4: requests run one by one on the single
+    # right-hand-side path until 4 wait on an idle graph; 0 (default 16): the same with 16 (the 40
+    # requests submitted at once start on the tile); 1000: nearly always single
     graphs = _graphs((3000, 20000), seed=5151)
     srv = di.di_server_create([g for g, _ in graphs], d=D, slots=8, sweeps_per_step=3,
                               tile_min_queue=tile_min_queue)
