@@ -53,6 +53,8 @@ def parse():
                    help="row,heavy_cut,heavy_chunk: use this push split instead of tuning it (profiling runs)")
     p.add_argument("--one-solve", action="store_true",
                    help="build the graph, run one DI-SOP solve and exit (the command the ncu captures profile)")
+    p.add_argument("--one-pi", action="store_true",
+                   help="build the graph, run one power iteration solve and exit (profiles the pull)")
     return p.parse_args()
 
 
@@ -530,6 +532,11 @@ def run_gpu(args):
         return di.di_solve_ex(g, Bx, d, TOL, schedule=schedule, fluid=di.DI_FLUID_F32, max_sweeps=MAX_SWEEPS,
                               X_out=Xx, **kw)[1]
 
+    if args.one_pi:
+        info = di.di_power_iter_ex(g, B, D, TOL, max_iters=MAX_SWEEPS, profile=1, X_out=X)[1]
+        torch.cuda.synchronize()
+        print(json.dumps({"one_pi": {k: info[k] for k in ("sweeps", "refine_rounds", "kernel_launches", "ms")}}))
+        return
     if args.one_solve:
         info = step(profile=1)        # kernels launched one by one, so a profiler sees each
         torch.cuda.synchronize()

@@ -519,6 +519,13 @@ __global__ void k_mark_hub_links(const int32_t *col_out, int64_t L, const int32_
     }
 }
 
+// the push kernels' row bounds: rp_out narrowed to 32 bits (L < 2^31), so one 32-byte sector
+// holds eight nodes' bounds instead of four
+__global__ void k_narrow_rows(const int64_t *rp, int64_t count, int32_t *out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = (int32_t)rp[k];
+}
+
 static int ceil_log2(int64_t x) {
     int b = 0;
     while ((int64_t(1) << b) < x) b++;
@@ -664,6 +671,9 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
         if (L > 0)
             k_mark_hub_links<<<grid_for(L, 256, dev), 256, 0, s>>>(g->col_out.as<int32_t>(), L, g->hub_ids.as<int32_t>(),
                                                                  g->col_push.as<int32_t>());
+        g->rp_push.ensure(sizeof(int32_t) * (size_t)(n + 1));
+        k_narrow_rows<<<grid_for((int64_t)n + 1, 256, dev), 256, 0, s>>>(g->rp_out.as<int64_t>(), (int64_t)n + 1,
+                                                              g->rp_push.as<int32_t>());
         // fixed-point width of the push window: a slot sums at most `reach_cnt` shares per
         // segment, each below 2^win_qbits in magnitude, and the sum must stay an int32
         unsigned int *reach_cnt = reinterpret_cast<unsigned int *>(slots.as<char>());

@@ -949,7 +949,7 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                                                   const int32_t *__restrict__ heavy_id, const float *__restrict__ heavy_s,
                                                   const int32_t *__restrict__ heavy_cstart,
                                                   const int32_t *__restrict__ heavy_chunk,
-                                                  const int64_t *__restrict__ rp_out,
+                                                  const int32_t *__restrict__ rp_push,
                                                   const int32_t *__restrict__ col_push, const int4 *__restrict__ chunks,
                                                   const int32_t *__restrict__ hub_ids, float *F, SolveCtl *ctl,
                                                   int win_qmax, int push_row, int heavy_len, int seg_cap) {
@@ -986,8 +986,8 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
         const int p = heavy_chunk[c];
         const int32_t u = heavy_id[p];
         const float sh = heavy_s[p];
-        const int64_t cb = rp_out[u] + (int64_t)(c - heavy_cstart[p]) * heavy_len;
-        const int64_t ce = min(cb + (int64_t)heavy_len, rp_out[u + 1]);
+        const int64_t cb = __ldg(rp_push + u) + (int64_t)(c - heavy_cstart[p]) * heavy_len;
+        const int64_t ce = min(cb + (int64_t)heavy_len, (int64_t)__ldg(rp_push + u + 1));
         for (int64_t k0 = cb + lane; k0 < ce; k0 += 32 * kHeavyPushUnroll) {
             int32_t jr[kHeavyPushUnroll];
 #pragma unroll
@@ -1026,12 +1026,12 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
             int deg = 0;
             int32_t eu = 0;
             float es = 0.f;
-            int64_t ebeg = 0;
+            int ebeg = 0;   // links stay below 2^31
             if (b0 + lane < clen) {
                 eu = __ldcs(front_id + idx);
                 es = __ldcs(front_s + idx);
-                ebeg = __ldg(rp_out + eu);
-                deg = (int)(__ldg(rp_out + eu + 1) - ebeg);
+                ebeg = __ldg(rp_push + eu);
+                deg = __ldg(rp_push + eu + 1) - ebeg;
             }
             // the share in the segment's fixed point; 0 (never added to the window) when it
             // does not fit, so its local links go to F directly
@@ -1043,7 +1043,7 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
             const bool row = deg >= push_row;
             for (unsigned rows = __ballot_sync(kFull, row); rows; rows &= rows - 1) {
                 const int src = __ffs(rows) - 1;
-                const int rb = (int)__shfl_sync(kFull, ebeg, src);   // links stay below 2^31
+                const int rb = __shfl_sync(kFull, ebeg, src);
                 const int rd = __shfl_sync(kFull, deg, src);
                 const int32_t ru = __shfl_sync(kFull, eu, src);
                 const float rs = __shfl_sync(kFull, es, src);
@@ -1704,7 +1704,7 @@ static void launch_sweep_body(di_graph *g, Workspace &ws, const Launch &l, cudaS
             if (sizeof(T) == 4) {
                 k_push_win<<<l.win_blocks, 256, 0, s>>>(
                     ws.front_id.as<int32_t>(), ws.front_s.as<float>(), ws.heavy_id.as<int32_t>(), ws.heavy_s.as<float>(),
-                    ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(), g->rp_out.as<int64_t>(),
+                    ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(), g->rp_push.as<int32_t>(),
                     g->col_push.as<int32_t>(), ws.chunks.as<int4>(), g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl,
                     1 << g->win_qbits, tune.row, tune.chunk, seg_capacity(g));
             } else {
@@ -1943,7 +1943,7 @@ static void solve_impl(di_graph *g, Workspace &ws, const double *B, double d, do
                         k_push_win<<<l.win_blocks, 256, 0, s>>>(
                             ws.front_id.as<int32_t>(), ws.front_s.as<float>(), ws.heavy_id.as<int32_t>(),
                             ws.heavy_s.as<float>(), ws.heavy_cstart.as<int32_t>(), ws.heavy_chunk.as<int32_t>(),
-                            g->rp_out.as<int64_t>(), g->col_push.as<int32_t>(), ws.chunks.as<int4>(),
+                            g->rp_push.as<int32_t>(), g->col_push.as<int32_t>(), ws.chunks.as<int4>(),
                             g->hub_ids.as<int32_t>(), ws.F.as<float>(), ctl, 1 << g->win_qbits, tune.row, tune.chunk, seg_capacity(g));
                     });
                     kc.run(KC_REFINE, 1, [&] { k_front_reset<<<1, 1, 0, s>>>(ctl); });
