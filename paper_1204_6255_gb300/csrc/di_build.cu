@@ -620,7 +620,9 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
 
     // in-CSR: stable sort on the destination field keeps origins ascending within each row
     g->rp_in.ensure(sizeof(int64_t) * ((size_t)n + 1));
-    g->col_in.ensure(sizeof(int32_t) * (size_t)(L > 0 ? L : 1));
+    // padded by kColInPad: the pull reads whole 16-byte vectors of links around a group's range
+    g->col_in.ensure(sizeof(int32_t) * ((size_t)L + kColInPad));
+    DI_CHECK_CUDA(cudaMemsetAsync(g->col_in.as<int32_t>() + L, 0, sizeof(int32_t) * kColInPad, s));
     if (L > 0) {
         alt.ensure(sizeof(uint64_t) * (size_t)L);
         k_repack_in<<<grid_for(L, 256, dev), 256, 0, s>>>(keys.as<uint64_t>(), L, bits, alt.as<uint64_t>());

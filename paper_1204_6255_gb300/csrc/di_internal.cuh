@@ -209,6 +209,7 @@ constexpr double kAimAfterSplit = 0.9;
 constexpr double kSplitBelow = 1e-6;
 constexpr int kPullHeavy = 8192;    // in-degree above which a row's edges are split over warps
 constexpr int kPullChunk = 4096;    // edges per heavy-row chunk of the pull
+constexpr int kColInPad = 8;        // int32 slots allocated past col_in's L links (pull vector reads)
 constexpr int kReduceBlocks = 1024; // partial sums of the last-block-done reductions
 constexpr int kHubSlots = 2048;     // shared-memory hub cache of the push kernels
 constexpr int kWinReach = 4096;     // push window: every source-target pair it takes is closer

@@ -211,6 +211,14 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t *p, uint64_t pol) {
     asm volatile("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
     return v;
 }
+// four consecutive link indices from a 16-byte aligned address, same cache policy
+__device__ __forceinline__ int4 ld_stream4(const int32_t *p, uint64_t pol) {
+    int4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
 __device__ __forceinline__ void red_keep_v4(float *p, float4 v, uint64_t pol) {
     asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y),
                  "f"(v.z), "f"(v.w), "l"(pol)
@@ -1288,9 +1296,30 @@ template <class Acc>
 struct PullVT {
     static constexpr int value = sizeof(typename Acc::V) == 4 ? kPullVTF32 : kPullVT;
 };
+// Per accumulator: whether contiguous row groups read their link indices as 16-byte vectors, and
+// the resident blocks per SM the registers are capped for. Measured on GB300: vector reads speed
+// up the FP32 (PI increment) pull by 5 % and slow the double-float residual pull by 5 %; capping
+// the FP32 pull's registers for 5 or 6 blocks per SM, or at 64, was slower than the compiler's
+// own 53.
+template <class Acc>
+struct PullCfg {
+    static constexpr bool vec = false;
+    static constexpr int min_blocks = 4;   // double-float: the compiler's own choice fits 4 blocks
+};
+constexpr int kPullF32MinBlocks = 0;   // 0: the compiler's own register count (4 blocks; 5 and 6 were slower)
+template <>
+struct PullCfg<AccF32> {
+    static constexpr bool vec = true;
+    static constexpr int min_blocks = kPullF32MinBlocks;
+};
+template <>
+struct PullCfg<AccF64> {
+    static constexpr bool vec = false;
+    static constexpr int min_blocks = 3;
+};
 
 template <int MODE, class Acc, class T>
-__global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in, const int32_t *__restrict__ col_in,
+__global__ void __launch_bounds__(256, PullCfg<Acc>::min_blocks) k_pull(const int64_t *__restrict__ rp_in, const int32_t *__restrict__ col_in,
                                               const typename Acc::V *y0, typename Acc::V *y1, int32_t n,
                                               const int32_t *heavy_rows, const int32_t *heavy_chunk_off,
                                               const typename Acc::Wide::V *heavy_partial, int32_t n_heavy,
@@ -1300,6 +1329,7 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
     using V = typename Acc::V;
     using W = typename Acc::Wide;
     constexpr int kPullVT = PullVT<Acc>::value;
+    static_assert(kPullVT % 4 == 0, "a lane's links are read as 16-byte vectors");
     __shared__ V acc_s[8][32];
     __shared__ int s_off[8][33];
     __shared__ int64_t s_beg[8][32];
@@ -1338,29 +1368,46 @@ __global__ void __launch_bounds__(256) k_pull(const int64_t *__restrict__ rp_in,
         __syncwarp();
         V carry = Acc::zero();
         int carry_row = -1;
-        for (int e0 = 0; e0 < total; e0 += 32 * kPullVT) {
+        // Without a heavy row the group's links are contiguous (link e at gbase + e), so each
+        // lane reads its kPullVT links as 16-byte vectors: the rounds start pre = gbase mod 4
+        // links early, which aligns every lane's run; links before 0 or from total on are read
+        // (col_in is padded past L) but not used.
+        const bool contig = PullCfg<Acc>::vec && !__any_sync(kFull, heavy);
+        const int64_t gbase = __shfl_sync(kFull, beg, 0);
+        const int pre = contig && total > 0 ? (int)(gbase & 3) : 0;
+        for (int e0 = -pre; e0 < total; e0 += 32 * kPullVT) {
             const int first = e0 + lane * kPullVT;
             int k = 0;   // last row with s_off[k] <= first
 #pragma unroll
             for (int step = 16; step > 0; step >>= 1)
                 if (s_off[warp][k + step] <= first) k += step;
             int next = s_off[warp][k + 1];
-            int64_t base = s_beg[warp][k];          // reloaded only when the row changes
+            int64_t base = contig ? gbase : s_beg[warp][k];   // reloaded only when the row changes
             int key[kPullVT];
             int32_t j[kPullVT];
             unsigned ends = 0;                      // bit v: link v is its row's last
+            if (contig && first < total) {
+#pragma unroll
+                for (int q = 0; q < kPullVT / 4; q++) {
+                    const int4 jv = ld_stream4(col_in + gbase + first + 4 * q, stream);
+                    j[4 * q] = jv.x;
+                    j[4 * q + 1] = jv.y;
+                    j[4 * q + 2] = jv.z;
+                    j[4 * q + 3] = jv.w;
+                }
+            }
 #pragma unroll
             for (int v = 0; v < kPullVT; v++) {
                 const int e = first + v;
-                key[v] = 64 + lane;                 // past the end: a key no row uses
-                if (e < total) {
+                key[v] = 64 + lane;                 // outside [0, total): a key no row uses
+                if (e >= 0 && e < total) {
                     while (e >= next) {
                         next = s_off[warp][++k + 1];
-                        base = s_beg[warp][k];
+                        if (!contig) base = s_beg[warp][k];
                     }
                     key[v] = k;
                     if (e + 1 == next) ends |= 1u << v;
-                    j[v] = ld_stream(col_in + base + e, stream);
+                    if (!contig) j[v] = ld_stream(col_in + base + e, stream);
                 }
             }
             V val[kPullVT];
@@ -1539,7 +1586,7 @@ void Workspace::reset_graphs() {
 }
 
 struct Launch {
-    int sel_blocks, red_blocks, push_blocks, win_blocks, pull_blocks, ew_blocks;
+    int sel_blocks, red_blocks, push_blocks, win_blocks, pull_blocks, pi_blocks, pi64_blocks, ew_blocks;
 };
 
 // Counts the kernels a call launches from the host and, in profile mode, brackets each launch
@@ -1591,6 +1638,10 @@ static Launch launch_shape(const di_graph *g) {
     l.win_blocks = sms * (occ > 0 ? occ : 1);
     DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pull<PULL_RESID, AccDF, T>, 256, 0));
     l.pull_blocks = sms * (occ > 0 ? occ : 1);
+    DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pull<PULL_INC, AccF32, float>, 256, 0));
+    l.pi_blocks = sms * (occ > 0 ? occ : 1);
+    DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pull<PULL_PI64, AccF64, double>, 256, 0));
+    l.pi64_blocks = sms * (occ > 0 ? occ : 1);
     const int64_t n = g->n;
     auto cap = [&](int64_t want, int64_t lim) { return (int)(want < 1 ? 1 : (want < lim ? want : lim)); };
     DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select<T>, 256, 0));
@@ -1598,8 +1649,10 @@ static Launch launch_shape(const di_graph *g) {
     l.red_blocks = cap((n + 255) / 256, (int64_t)(kReduceBlocks < sms * 4 ? kReduceBlocks : sms * 4));
     l.ew_blocks = cap((n + 255) / 256, (int64_t)sms * 8);
     // a pull block never needs more row groups than exist
-    l.pull_blocks = cap(((n + 31) / 32 + 7) / 8, l.pull_blocks);
-    if (l.pull_blocks > kReduceBlocks) l.pull_blocks = kReduceBlocks;
+    for (int *b : {&l.pull_blocks, &l.pi_blocks, &l.pi64_blocks}) {
+        *b = cap(((n + 31) / 32 + 7) / 8, *b);
+        if (*b > kReduceBlocks) *b = kReduceBlocks;
+    }
     return l;
 }
 
@@ -1772,13 +1825,13 @@ static void launch_pi_body(di_graph *g, Workspace &ws, const Launch &l, cudaStre
     }
     c.run(KC_PUSH, 1, [&] {
         if (fp64)
-            k_pull<PULL_PI64, AccF64, double><<<l.pull_blocks, 256, 0, s>>>(
+            k_pull<PULL_PI64, AccF64, double><<<l.pi64_blocks, 256, 0, s>>>(
                 g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<double>(), ws.y1.as<double>(), g->n,
                 g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<double>(),
                 g->n_heavy_in, ws.B.as<double>(), ws.Bdf.p, ws.Xdf.p, nullptr, (double *)nullptr,
                 ws.partials.as<double>(), ctl, h, set_cond);
         else
-            k_pull<PULL_INC, AccF32, float><<<l.pull_blocks, 256, 0, s>>>(
+            k_pull<PULL_INC, AccF32, float><<<l.pi_blocks, 256, 0, s>>>(
                 g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<float>(), ws.y1.as<float>(), g->n,
                 g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<float2>(),
                 g->n_heavy_in, ws.B.as<double>(), ws.Bdf.p, ws.H.p, nullptr, (float *)nullptr,
@@ -2160,8 +2213,7 @@ static void solve_single_body(di_graph *g, Workspace &ws, const double *B, doubl
     int refine = o.refine == 0 ? (o.fluid == DI_FLUID_F32) : (o.refine > 0);
     std::unique_lock<std::mutex> lk(g->mu, std::defer_lock);
     if (lock) {
-        lk.try_lock();
-        DI_REQUIRE(lk.owns_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
+        DI_REQUIRE(lk.try_lock(), DI_ERR_BUSY, "graph workspace is in use by another call");
     }
     DeviceGuard dg(g->dev.device);
     if (o.fluid == DI_FLUID_F32)
