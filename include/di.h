@@ -457,7 +457,8 @@ di_status di_csr_validate(int32_t n, int64_t L, const int64_t *rp_out, const int
 /*
  * di_graph_validate — copies every array of a built graph to the host and runs di_csr_validate
  * on them. It also checks the push kernels' copy of the out-links, where bit 31 marks the links
- * into a hub, and |E| against the statistics. Same returns; DI_ERR_CUDA if a copy fails.
+ * into a hub and a loop node's self-link is swapped with the last link of its row, and |E|
+ * against the statistics. Same returns; DI_ERR_CUDA if a copy fails.
  */
 di_status di_graph_validate(const di_graph *g);
 

@@ -519,6 +519,24 @@ __global__ void k_mark_hub_links(const int32_t *col_out, int64_t L, const int32_
     }
 }
 
+// In the push kernels' copy, a loop node's self-link is swapped with the last link of its row, so
+// a push that diffuses the loop in closed form simply stops one link short of the row's end
+// instead of comparing every link with the source.
+__global__ void k_loop_last(const int64_t *rp, const uint8_t *loop, int32_t n, int32_t *col_push) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        if (!loop[u]) continue;
+        int64_t lo = rp[u], hi = rp[u + 1] - 1;   // rows are sorted, and the self-link is in the row
+        const int64_t last = hi;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((col_push[mid] & 0x7fffffff) < (int32_t)u) lo = mid + 1; else hi = mid;
+        }
+        const int32_t self = col_push[lo];
+        col_push[lo] = col_push[last];
+        col_push[last] = self;
+    }
+}
+
 // the push kernels' row bounds: rp_out narrowed to 32 bits (L < 2^31), so one 32-byte sector
 // holds eight nodes' bounds instead of four
 __global__ void k_narrow_rows(const int64_t *rp, int64_t count, int32_t *out) {
@@ -673,6 +691,9 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
         if (L > 0)
             k_mark_hub_links<<<grid_for(L, 256, dev), 256, 0, s>>>(g->col_out.as<int32_t>(), L, g->hub_ids.as<int32_t>(),
                                                                  g->col_push.as<int32_t>());
+        if (L > 0)
+            k_loop_last<<<grid_for(n, 256, dev), 256, 0, s>>>(g->rp_out.as<int64_t>(), g->loop.as<uint8_t>(), n,
+                                                            g->col_push.as<int32_t>());
         g->rp_push.ensure(sizeof(int32_t) * (size_t)(n + 1));
         k_narrow_rows<<<grid_for((int64_t)n + 1, 256, dev), 256, 0, s>>>(g->rp_out.as<int64_t>(), (int64_t)n + 1,
                                                               g->rp_push.as<int32_t>());

@@ -368,6 +368,8 @@ __device__ __forceinline__ int segment_at(const SolveCtl *ctl, int ci, int seg_c
 // entries of a chunk are compacted with one atomic per chunk, so the frontier is id-sorted
 // within each chunk (the push then walks neighbouring rows together). An entry is the node id
 // and its share (8 bytes); the push reads the row bounds itself, from neighbouring row pointers.
+// Bit 31 of the id marks a loop node whose self-link is diffused in closed form: the push's copy
+// of its row ends with the self-link (k_loop_last), so the push leaves the row's last link out.
 constexpr int kSelItems = 8;
 constexpr int kTrackResync = 8;      // an exact reduction at least every kTrackResync sweeps
 constexpr double kTrackBand = 16.0;  // ... and at every sweep once r <= kTrackBand * tol
@@ -499,11 +501,11 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
             for (int v = 0; v < kSelBatch<T>; v++) {
                 const int k = r0 + v * 32 + lane;
                 const uint32_t i = wb + poff[v];
-                bool light = false, heavy = false;
+                bool light = false, heavy = false, lp = false;
                 T share = (T)0;
                 const int32_t o = pinfo[v] & 0x7fffffff;
                 if (k < cnt) {
-                    const bool lp = !plain_loops && pinfo[v] < 0;
+                    lp = !plain_loops && pinfo[v] < 0;
                     st_keep(F + i, (T)0, keep);
                     T t;
                     visit_math(pf[v], o, lp, d, d_f, t, share);
@@ -525,6 +527,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                     const int p = nlight + __popc(bl & lt);
                     wf[p] = share;
                     woff[p] = (uint8_t)poff[v];
+                    winfo[p] = lp ? 1 : 0;
                     sh_abs += fabsf((float)share);
                 }
                 nlight += __popc(bl);
@@ -577,7 +580,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
         __syncthreads();
         const int cb = s_chunk_base + s_wbase[warp];
         for (int k = lane; k < nlight; k += 32) {
-            __stcs(front_id + cb + k, (int32_t)(wb + woff[k]));
+            __stcs(front_id + cb + k, (int32_t)((wb + woff[k]) | ((uint32_t)winfo[k] << 31)));
             __stcs(front_s + cb + k, wf[k]);
         }
         __syncwarp();   // the slots are reused: by the next chunk's copies or packing
@@ -898,7 +901,7 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
         const int64_t idx = b0 + lane;
         int deg = 0;
         if (idx < count) {
-            const int32_t u = __ldcs(front_id + idx);
+            const int32_t u = __ldcs(front_id + idx) & 0x7fffffff;   // bit 31: see k_select
             const int64_t rb = __ldg(rp_out + u);
             deg = (int)(__ldg(rp_out + u + 1) - rb);
             s_u[w][lane] = u;
@@ -952,8 +955,11 @@ constexpr int kHubCopies = 1;   // copies of the push's shared-memory hub cache
 constexpr int kHalo = 1024;
 constexpr int kWin = kSelChunk + 2 * kHalo;     // 4096 int32 slots, 16 KB
 constexpr int kWinMinEntries = 24;              // sparser segments push link by link
+// Resident blocks per SM the registers are capped for: measured on GB300, 7 blocks (32
+// registers) beat 6 and 5 (the kernel waits on memory and gains from more warps in flight).
+constexpr int kPushWinBlocks = 7;
 
-__global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__ front_id, const float *__restrict__ front_s,
+__global__ void __launch_bounds__(256, kPushWinBlocks) k_push_win(const int32_t *__restrict__ front_id, const float *__restrict__ front_s,
                                                   const int32_t *__restrict__ heavy_id, const float *__restrict__ heavy_s,
                                                   const int32_t *__restrict__ heavy_cstart,
                                                   const int32_t *__restrict__ heavy_chunk,
@@ -966,7 +972,7 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
     // hubs are the hottest addresses, and FP32 shared atomics retry when another lane wrote first)
     __shared__ float s_hacc[kHubCopies][kHubSlots];
     __shared__ int s_off[8][33];
-    // per entry of a warp's batch: {row start - link offset, source id, share, fixed-point share}
+    // per entry of a warp's batch: {row start - link offset, share, fixed-point share, unused}
     __shared__ int4 s_rec[8][32];
     __shared__ int s_chunk, s_batch;
     if (ctl->done) return;
@@ -1036,10 +1042,12 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
             float es = 0.f;
             int ebeg = 0;   // links stay below 2^31
             if (b0 + lane < clen) {
-                eu = __ldcs(front_id + idx);
+                // bit 31: a loop node diffused in closed form, whose row ends with the self-link
+                const int32_t raw = __ldcs(front_id + idx);
+                eu = raw & 0x7fffffff;
                 es = __ldcs(front_s + idx);
                 ebeg = __ldg(rp_push + eu);
-                deg = __ldg(rp_push + eu + 1) - ebeg;
+                deg = __ldg(rp_push + eu + 1) - ebeg - (int)((uint32_t)raw >> 31);
             }
             // the share in the segment's fixed point; 0 (never added to the window) when it
             // does not fit, so its local links go to F directly
@@ -1053,7 +1061,6 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                 const int src = __ffs(rows) - 1;
                 const int rb = __shfl_sync(kFull, ebeg, src);
                 const int rd = __shfl_sync(kFull, deg, src);
-                const int32_t ru = __shfl_sync(kFull, eu, src);
                 const float rs = __shfl_sync(kFull, es, src);
                 const int rq = __shfl_sync(kFull, eq, src);
                 for (int k0 = lane; k0 < rd; k0 += 32 * kPushVT) {
@@ -1062,9 +1069,8 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                     for (int v = 0; v < kPushVT; v++) jr[v] = k0 + 32 * v < rd ? ld_stream(col_push + rb + k0 + 32 * v, stream) : 0;
 #pragma unroll
                     for (int v = 0; v < kPushVT; v++) {
-                        const int32_t j = jr[v] & 0x7fffffff;
-                        if (k0 + 32 * v >= rd || (j == ru && !loops)) continue;
-                        const unsigned off = (unsigned)(j - lo);
+                        if (k0 + 32 * v >= rd) continue;
+                        const unsigned off = (unsigned)((jr[v] & 0x7fffffff) - lo);
                         if (rq != 0 && jr[v] >= 0 && off < (unsigned)kWin) atomicAdd(&s_win[off], rq);
                         else far_add(jr[v], rs);
                     }
@@ -1083,7 +1089,7 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
             if (dsm > 0) {
                 const int pos = __popc(small & lanemask_lt());
                 s_off[w][pos] = inc - dsm;
-                s_rec[w][pos] = make_int4(rbase, eu, __float_as_int(es), eq);
+                s_rec[w][pos] = make_int4(rbase, __float_as_int(es), eq, 0);
             }
             if (lane == 0) s_off[w][__popc(small)] = total;
             __syncwarp();
@@ -1096,13 +1102,12 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                 // to the next link crosses at most one entry boundary
                 int next = s_off[w][k + 1];
                 int4 rec = s_rec[w][k];
-                int32_t jr[kPushVT], uu[kPushVT], qq[kPushVT];
+                int32_t jr[kPushVT], qq[kPushVT];
                 float ss[kPushVT];
 #pragma unroll
                 for (int v = 0; v < kPushVT; v++) {
                     const int e = e0 + v;
                     jr[v] = 0;
-                    uu[v] = 0;
                     ss[v] = 0.f;
                     qq[v] = 0;
                     if (e < total) {
@@ -1112,16 +1117,14 @@ __global__ void __launch_bounds__(256, 5) k_push_win(const int32_t *__restrict__
                             rec = s_rec[w][k];
                         }
                         jr[v] = ld_stream(col_push + rec.x + e, stream);
-                        uu[v] = rec.y;
-                        ss[v] = __int_as_float(rec.z);
-                        qq[v] = rec.w;
+                        ss[v] = __int_as_float(rec.y);
+                        qq[v] = rec.z;
                     }
                 }
 #pragma unroll
                 for (int v = 0; v < kPushVT; v++) {
-                    const int32_t j = jr[v] & 0x7fffffff;
-                    if (e0 + v >= total || (j == uu[v] && !loops)) continue;
-                    const unsigned off = (unsigned)(j - lo);
+                    if (e0 + v >= total) continue;
+                    const unsigned off = (unsigned)((jr[v] & 0x7fffffff) - lo);
                     if (qq[v] != 0 && jr[v] >= 0 && off < (unsigned)kWin) atomicAdd(&s_win[off], qq[v]);
                     else far_add(jr[v], ss[v]);
                 }

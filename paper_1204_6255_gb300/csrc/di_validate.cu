@@ -108,12 +108,23 @@ extern "C" di_status di_graph_validate(const di_graph *g) {
         const di_status st = di_csr_validate(g->n, g->L, rp_out.data(), col_out.data(), rp_in.data(), col_in.data(),
                                              out_deg.data(), in_deg.data(), loop.data(), e_mask.data(), e_level.data());
         if (st != DI_OK) throw Fail{st};
-        for (size_t k = 0; k < L; k++) {
-            const int32_t j = col_out[k];
+        // the push's copy: col_out with bit 31 on links into a hub, and a loop node's self-link
+        // swapped with the last link of its row
+        auto marked = [&](int32_t j) {
             const int32_t slot = (int32_t)(((uint32_t)j * 0x9E3779B1u) >> 21);
-            const bool hub = hubs[slot] == j;
-            DI_REQUIRE(col_push[k] == (hub ? (int32_t)((uint32_t)j | 0x80000000u) : j), DI_ERR_CORRUPT,
-                       "hub-marked link copy differs at link %lld", (long long)k);
+            return hubs[slot] == j ? (int32_t)((uint32_t)j | 0x80000000u) : j;
+        };
+        for (size_t u = 0; u < n; u++) {
+            const int64_t b = rp_out[u], e = rp_out[u + 1];
+            int64_t self = -1;
+            if (loop[u])
+                for (int64_t k = b; k < e; k++)
+                    if (col_out[k] == (int32_t)u) self = k;
+            for (int64_t k = b; k < e; k++) {
+                const int64_t src = self < 0 ? k : (k == self ? e - 1 : (k == e - 1 ? self : k));
+                DI_REQUIRE(col_push[k] == marked(col_out[src]), DI_ERR_CORRUPT,
+                           "the push's link copy differs at link %lld", (long long)k);
+            }
         }
         int64_t e_count = 0;
         for (size_t i = 0; i < n; i++) e_count += e_mask[i] != 0;
