@@ -55,6 +55,10 @@ def parse():
                    help="build the graph, run one DI-SOP solve and exit (the command the ncu captures profile)")
     p.add_argument("--one-pi", action="store_true",
                    help="build the graph, run one power iteration solve and exit (profiles the pull)")
+    p.add_argument("--sweeps", default="",
+                   help="with --one-solve: A,B runs the same solve capped at A and then at B sweeps and prints "
+                        "the links and frontier entries that sweeps A+1..B push (scales a capture of those "
+                        "push launches to algorithmic bytes)")
     return p.parse_args()
 
 
@@ -140,13 +144,23 @@ PUSH_SRC = os.path.join(ROOT, "paper_1204_6255_gb300", "csrc", "di_solve.cu")
 PUSH_PROFILE = os.path.join(ROOT, "profiles", "k_push_win_web_n10m.md")
 
 
-def push_traffic():
-    """DRAM bytes per push launch from the committed ncu summary, or None when the kernel source
-    changed since that capture (the summary records the source's sha256)."""
+def push_source_sha():
+    """sha256 of the push kernel's source: the text from the comment that opens k_push_win's
+    section of di_solve.cu to the kernel's closing brace (its constants included)."""
     import hashlib
+    text = open(PUSH_SRC).read()
+    start = text.index("// Push with a shared-memory window (FP32 fluid).")
+    body = text.index("k_push_win(", start)
+    end = text.index("\n}\n", body) + 3
+    return hashlib.sha256(text[start:end].encode()).hexdigest()
+
+
+def push_traffic():
+    """DRAM bytes per push launch from the committed ncu summary, or None when the push kernel's
+    source changed since that capture (the summary records its sha256)."""
     if not os.path.exists(PUSH_PROFILE):
         return None, None
-    sha = hashlib.sha256(open(PUSH_SRC, "rb").read()).hexdigest()
+    sha = push_source_sha()
     fields = {}
     for line in open(PUSH_PROFILE):
         if line.startswith("- ") and ":" in line:
@@ -285,7 +299,23 @@ def ppr_batch_leg(di, workloads, torch):
         di.di_solve(g, B, d, tol, di.DI_SOP, MAX_SWEEPS, X_out=Xs)
         lat.append(1e3 * (time.perf_counter() - t))
     solo_s = time.perf_counter() - t0
+    # the batched push's roofline, from one more batched call with each kernel timed alone:
+    # per launch 4 B link index per link of a frontier node, 8 B read-modify-write of F per
+    # link and column with a non-zero share, and per frontier entry 4 B id + 8 B row bounds +
+    # 4 B share per column of the tile
+    _, _, pinfo = di.di_ppr_batch(g, off_d, seeds_d, d, tol, X_out=X, profile=1)
+    T = pinfo["rhs_tile"]
+    launches = max(pinfo["push_launches"], 1)
+    push_bytes = (4.0 * pinfo["pushed_edges"] + 8.0 * pinfo["column_links"]
+                  + (12.0 + 4.0 * T) * pinfo["frontier_entries"]) / launches
+    push_ms = pinfo["push_ms"] / launches
+    peak, peak_kind = peaks()
+    roof = {"kernel": f"kb_push<{T}>", "bound": "hbm", "bytes_per_launch": push_bytes, "ms_per_launch": push_ms,
+            "achieved": push_bytes / (push_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
+            "frac": push_bytes / (push_ms * 1e-3) / 1e9 / peak, "launches": pinfo["push_launches"],
+            "column_links": pinfo["column_links"], "select_ms_per_launch": pinfo["select_ms"] / max(pinfo["select_launches"], 1)}
     return {"requests": k, "graph": f"N={n}, L={g.stats['L']}", "tol": tol, "rhs_tile": info["rhs_tile"],
+            "push_split": di.di_autotune(g, d, what=0), "roofline": roof,
             "batched_qps": k / batch_s, "batched_ms": 1e3 * batch_s,
             "per_request_qps": sample / solo_s, "per_request_p50_ms": pct(lat, 50), "per_request_p99_ms": pct(lat, 99),
             "speedup": (k / batch_s) / (sample / solo_s), "max_residual": float(np.max(res))}
@@ -536,6 +566,20 @@ def run_gpu(args):
         info = di.di_power_iter_ex(g, B, D, TOL, max_iters=MAX_SWEEPS, profile=1, X_out=X)[1]
         torch.cuda.synchronize()
         print(json.dumps({"one_pi": {k: info[k] for k in ("sweeps", "refine_rounds", "kernel_launches", "ms")}}))
+        return
+    if args.one_solve and args.sweeps:
+        a, b = (int(x) for x in args.sweeps.split(","))
+        counts = []
+        for cap in (a, b):
+            try:
+                info = di.di_solve_ex(g, B, D, TOL, schedule=di.DI_SOP, fluid=di.DI_FLUID_F32, max_sweeps=cap,
+                                      X_out=X, profile=1)[1]
+            except di.DiError as e:           # capped before the tolerance: the counts still come back
+                info = e.info
+            counts.append(info)
+        print(json.dumps({"sweeps": [a + 1, b], "push_launches": counts[1]["push_launches"] - counts[0]["push_launches"],
+                          "pushed_edges": counts[1]["pushed_edges"] - counts[0]["pushed_edges"],
+                          "frontier_entries": counts[1]["frontier_entries"] - counts[0]["frontier_entries"]}))
         return
     if args.one_solve:
         info = step(profile=1)        # kernels launched one by one, so a profiler sees each

@@ -88,7 +88,7 @@ typedef struct {
     int32_t rhs_tile;    /* batched solves: RHS per tile, 4, 8, 16 or 32 (0: autotuned per graph) */
     int32_t profile;     /* 1: host-driven sweeps with CUDA events around every kernel launch;
                             fills the per-kernel times of di_solve_info (slower: one sync per
-                            sweep) */
+                            sweep). Batched solves time their select, push and reduce kernels */
     int32_t e_prediffuse;/* di_solve_ex only; 1: before the sweeps, visit every node of E once in
                             level order (Section 2.4: E converges in finitely many steps). Each
                             node of E then holds its exact value, up to rounding, and receives no
@@ -124,6 +124,9 @@ typedef struct {
     int32_t select_launches, push_launches, reduce_launches, refine_launches;
     int32_t rhs_tile;        /* batched solves: columns per tile that were used */
     int32_t e_visits;        /* visits of the E pre-diffusion (opts.e_prediffuse) */
+    int64_t column_links;    /* batched solves: link-column updates the push made (for every
+                                diffusion of a node in a column with a non-zero share, the
+                                node's pushed links); 0 for single solves */
 } di_solve_info;
 
 /* Which internal array di_graph_export copies. */

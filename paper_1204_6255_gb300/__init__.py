@@ -96,7 +96,8 @@ class SolveInfo(ctypes.Structure):
                 ("select_ms", ctypes.c_double), ("push_ms", ctypes.c_double), ("reduce_ms", ctypes.c_double),
                 ("refine_ms", ctypes.c_double), ("select_launches", ctypes.c_int32),
                 ("push_launches", ctypes.c_int32), ("reduce_launches", ctypes.c_int32),
-                ("refine_launches", ctypes.c_int32), ("rhs_tile", ctypes.c_int32), ("e_visits", ctypes.c_int32)]
+                ("refine_launches", ctypes.c_int32), ("rhs_tile", ctypes.c_int32), ("e_visits", ctypes.c_int32),
+                ("column_links", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -442,7 +443,7 @@ def di_solve_batch(g: Graph, B, d: float, tol, schedule: int = DI_SOP, max_sweep
 
 
 def di_ppr_batch(g: Graph, seed_offsets, seeds, d: float, tol, schedule: int = DI_SOP, max_sweeps: int = 0,
-                 rhs_tile: int = 0, refine: int = 0, host_loop: int = 0, X_out=None, res_out=None):
+                 rhs_tile: int = 0, refine: int = 0, host_loop: int = 0, profile: int = 0, X_out=None, res_out=None):
     """Personalised PageRank for k seed sets (seed_offsets int64[k+1], seeds int32): column r has
     B_r = (1-d)/|S_r| on its seeds. Returns (X (k, n), residuals (k,), info)."""
     k = int(seed_offsets.shape[0]) - 1
@@ -451,7 +452,8 @@ def di_ppr_batch(g: Graph, seed_offsets, seeds, d: float, tol, schedule: int = D
     res = res_out if res_out is not None else np.empty(k, dtype=np.float64)
     _need(k * g.n, X_out=X)
     _need(k, tol=tol, res_out=res)
-    o = SolveOpts(int(schedule), DI_FLUID_F32, int(max_sweeps), int(refine), int(host_loop), int(rhs_tile), 0, 0)
+    o = SolveOpts(int(schedule), DI_FLUID_F32, int(max_sweeps), int(refine), int(host_loop), int(rhs_tile),
+                  int(profile), 0)
     info = SolveInfo()
     _check(load().di_ppr_batch(g.handle, k, _ptr(seed_offsets, np.int64), _ptr(seeds, np.int32), float(d),
                                _ptr(tol, np.float64), ctypes.byref(o), _ptr(X, np.float64), _ptr(res, np.float64),

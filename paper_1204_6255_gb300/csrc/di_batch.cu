@@ -61,7 +61,7 @@ static void solve_tile(di_graph *g, int c0, int ncols, double d, const double *t
             for (;;) {
                 read_bctl(w, s);
                 if (hc.done) break;
-                batch_body<T>(g, w, l, s, cudaGraphConditionalHandle(0), 0);
+                batch_body<T>(g, w, l, s, cudaGraphConditionalHandle(0), 0, w.clock);
                 launches += 3;
             }
         } else {
@@ -112,6 +112,7 @@ static void solve_tile(di_graph *g, int c0, int ncols, double d, const double *t
     acc->pushed_edges += (int64_t)hc.pushed;
     acc->visited_nodes += (int64_t)hc.visited;
     acc->frontier_entries += (int64_t)hc.front_total;
+    acc->column_links += (int64_t)hc.col_pushed;
     acc->kernel_launches += launches + 3 * (int64_t)hc.body_runs;
     for (int c = 0; c < ncols; c++) acc->dangling_mass_e += hc.e[c];
 }
@@ -316,7 +317,7 @@ static void batch_refill(di_graph *g, int k, const double *B, bool B_dev, const 
             for (;;) {   // host-driven sweeps (one sync per sweep), for profiling kernels one by one
                 read_bctl(w, s);
                 if (hc.done) break;
-                batch_body<T>(g, w, l, s, cudaGraphConditionalHandle(0), 0);
+                batch_body<T>(g, w, l, s, cudaGraphConditionalHandle(0), 0, w.clock);
                 launches += 3;
             }
         } else {
@@ -373,6 +374,7 @@ static void batch_refill(di_graph *g, int k, const double *B, bool B_dev, const 
     acc->pushed_edges += (int64_t)hc.pushed;
     acc->visited_nodes += (int64_t)hc.visited;
     acc->frontier_entries += (int64_t)hc.front_total;
+    acc->column_links += (int64_t)hc.col_pushed;
     acc->kernel_launches += launches + 3 * (int64_t)hc.body_runs;
 }
 
@@ -416,7 +418,14 @@ static di_status batch_entry(di_graph *g, int32_t k, const double *B, const int6
         const bool seeds_dev = seeds && is_device_ptr(seeds);
         int T = o.rhs_tile ? o.rhs_tile : autotune(g, d, s);
         if (!g->bws) g->bws = new BatchWorkspace();
-        g->bws->host_loop = o.host_loop != 0;
+        g->bws->host_loop = o.host_loop != 0 || o.profile != 0;
+        // profile: host-driven sweeps with each select, push and reduce timed alone
+        KernelClock kc(o.profile != 0, s);
+        g->bws->clock = o.profile ? &kc : nullptr;
+        struct ClockReset {
+            BatchWorkspace *w;
+            ~ClockReset() { w->clock = nullptr; }
+        } clock_reset{g->bws};
         std::vector<double> res((size_t)k, 0.0);
         di_solve_info acc;
         memset(&acc, 0, sizeof(acc));
@@ -456,6 +465,14 @@ static di_status batch_entry(di_graph *g, int32_t k, const double *B, const int6
         for (int c = 0; c < k; c++) acc.residual_l1 = res[c] > acc.residual_l1 ? res[c] : acc.residual_l1;
         acc.paper_error = acc.residual_l1 / (1.0 - d);
         acc.rhs_tile = T;
+        if (o.profile) {
+            acc.select_ms = kc.ms[KC_SELECT];
+            acc.push_ms = kc.ms[KC_PUSH];
+            acc.reduce_ms = kc.ms[KC_REDUCE];
+            acc.select_launches = kc.count[KC_SELECT];
+            acc.push_launches = kc.count[KC_PUSH];
+            acc.reduce_launches = kc.count[KC_REDUCE];
+        }
         if (info) *info = acc;
         DI_REQUIRE(bad < 0, DI_ERR_NOT_CONVERGED, "column %d not converged: ||F||_1 = %g > tol = %g", bad, res[bad],
                    tol_h[bad]);

@@ -19,6 +19,7 @@ struct BatchWorkspace {
     cudaStream_t capture_stream = nullptr;
     void *ctl_host = nullptr;
     bool host_loop = false;          // drive the sweeps from the host instead of the graph
+    KernelClock *clock = nullptr;    // a profiled call's kernel timer (host-driven sweeps)
     ~BatchWorkspace();
 };
 

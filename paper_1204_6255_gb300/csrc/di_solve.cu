@@ -1592,44 +1592,6 @@ struct Launch {
     int sel_blocks, red_blocks, push_blocks, win_blocks, pull_blocks, pi_blocks, pi64_blocks, ew_blocks;
 };
 
-// Counts the kernels a call launches from the host and, in profile mode, brackets each launch
-// with CUDA events on the launching stream (synchronising after it) to time it alone.
-enum { KC_SELECT = 0, KC_PUSH = 1, KC_REDUCE = 2, KC_REFINE = 3 };
-struct KernelClock {
-    bool on = false;
-    cudaStream_t s = nullptr;
-    cudaEvent_t a = nullptr, b = nullptr;
-    double ms[4] = {0, 0, 0, 0};
-    int count[4] = {0, 0, 0, 0};
-    int64_t host_launches = 0;
-    KernelClock(bool profile, cudaStream_t st) : on(profile), s(st) {
-        if (on) {
-            DI_CHECK_CUDA(cudaEventCreate(&a));
-            DI_CHECK_CUDA(cudaEventCreate(&b));
-        }
-    }
-    ~KernelClock() {
-        if (a) cudaEventDestroy(a);
-        if (b) cudaEventDestroy(b);
-    }
-    template <class F>
-    void run(int slot, int launches, F &&launch) {
-        host_launches += launches;
-        if (!on) {
-            launch();
-            return;
-        }
-        DI_CHECK_CUDA(cudaEventRecord(a, s));
-        launch();
-        DI_CHECK_CUDA(cudaEventRecord(b, s));
-        DI_CHECK_CUDA(cudaEventSynchronize(b));
-        float t = 0.f;
-        DI_CHECK_CUDA(cudaEventElapsedTime(&t, a, b));
-        ms[slot] += t;
-        count[slot] += 1;
-    }
-};
-
 template <class T>
 static Launch launch_shape(const di_graph *g) {
     Launch l;

@@ -29,6 +29,8 @@ struct BatchCtl {
     unsigned long long pushed;       // sum of out_i over node visits (a node counted once per sweep)
     unsigned long long visited;      // node visits
     unsigned long long col_visits;   // (node, column) diffusions
+    unsigned long long col_pushed;   // links pushed per (node, column) diffusion with a share,
+                                     //    summed: the push's link-column updates
     unsigned long long front_total;
     int32_t ncols;
     int32_t schedule;
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
     __shared__ double s_thr[T];
     __shared__ int s_act[T];
     __shared__ double s_e[8][T];
-    __shared__ unsigned long long s_cnt[3][8];
+    __shared__ unsigned long long s_cnt[4][8];
     __shared__ int wcount[T][8];
     __shared__ int chunk_base;
     __shared__ float s_share[T][256];       // per sub-step share of every lane
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
     const float d_f = (float)d;
     const bool act = s_act[c] != 0;
     float e_run = 0.f;
-    unsigned long long pushed = 0, visited = 0, colv = 0;
+    unsigned long long pushed = 0, visited = 0, colv = 0, colp = 0;
     for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += (int64_t)gridDim.x * 256) {
         // sub-steps in groups of kGroup: the F and degree loads of a group are issued before any
         // of its stores, then H of the selected entries, so the loads of a group overlap
@@ -287,6 +289,7 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
                     else {
                         share = tf * d_f / of;
                         pushable = (o - (lp ? 1 : 0)) > 0;
+                        if (pushable && share != 0.f) colp += (unsigned long long)(o - (lp ? 1 : 0));
                     }
                 }
                 const unsigned bsel = __ballot_sync(kFull, sel) & gmask;
@@ -347,7 +350,8 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
     pushed = warp_sum(pushed);
     visited = warp_sum(visited);
     colv = warp_sum(colv);
-    if (lane == 0) { s_cnt[0][warp] = pushed; s_cnt[1][warp] = visited; s_cnt[2][warp] = colv; }
+    colp = warp_sum(colp);
+    if (lane == 0) { s_cnt[0][warp] = pushed; s_cnt[1][warp] = visited; s_cnt[2][warp] = colv; s_cnt[3][warp] = colp; }
     __syncthreads();
     if (tid < T) {
         double sum = 0.0;
@@ -355,14 +359,15 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
         if (sum != 0.0) atomicAdd(&ctl->e[tid], sum);
     }
     if (tid == 0) {
-        unsigned long long a = 0, b = 0, cc = 0;
-        for (int w = 0; w < 8; w++) { a += s_cnt[0][w]; b += s_cnt[1][w]; cc += s_cnt[2][w]; }
+        unsigned long long a = 0, b = 0, cc = 0, cp = 0;
+        for (int w = 0; w < 8; w++) { a += s_cnt[0][w]; b += s_cnt[1][w]; cc += s_cnt[2][w]; cp += s_cnt[3][w]; }
         if (a) atomicAdd(&ctl->pushed, a);
         if (b) {
             atomicAdd(&ctl->visited, b);
             atomicAdd(&ctl->last_selected, (int)b);
         }
         if (cc) atomicAdd(&ctl->col_visits, cc);
+        if (cp) atomicAdd(&ctl->col_pushed, cp);
         if (blockIdx.x == 0) atomicAdd(&ctl->sweeps, 1);
     }
 }
@@ -713,18 +718,28 @@ static BLaunch blaunch(const di_graph *g) {
     return l;
 }
 
+// One sweep of a tile: select, push, reduce. `kc` (host-driven sweeps only) times each kernel.
 template <int T>
 static void batch_body(di_graph *g, BatchWorkspace &w, const BLaunch &l, cudaStream_t s, cudaGraphConditionalHandle h,
-                       int set_cond) {
+                       int set_cond, KernelClock *kc = nullptr) {
     BatchCtl *ctl = w.ctl.as<BatchCtl>();
     const PushTune tune = g->tune_batch;
-    kb_select<T><<<l.sel, 256, 0, s>>>(w.F.as<float>(), w.H.as<double>(), g->out_info.as<int32_t>(), g->n, ctl,
-                                       w.front_id.as<int32_t>(), w.front_s.as<float>(), w.heavy_cstart.as<int32_t>(),
-                                       w.heavy_chunk.as<int32_t>(), tune.heavy, tune.chunk);
-    kb_push<T><<<l.push, 256, 0, s>>>(w.front_id.as<int32_t>(), w.front_s.as<float>(), w.heavy_cstart.as<int32_t>(),
-                                      w.heavy_chunk.as<int32_t>(), g->rp_out.as<int64_t>(), g->col_out.as<int32_t>(),
-                                      w.F.as<float>(), ctl, tune.heavy, tune.chunk);
-    kb_reduce<T><<<l.red, 256, 0, s>>>(w.F.as<float>(), g->n, w.partials.as<double>(), ctl, h, set_cond);
+    KernelClock none(false, s);
+    KernelClock &c = kc ? *kc : none;
+    c.run(KC_SELECT, 1, [&] {
+        kb_select<T><<<l.sel, 256, 0, s>>>(w.F.as<float>(), w.H.as<double>(), g->out_info.as<int32_t>(), g->n, ctl,
+                                           w.front_id.as<int32_t>(), w.front_s.as<float>(),
+                                           w.heavy_cstart.as<int32_t>(), w.heavy_chunk.as<int32_t>(), tune.heavy,
+                                           tune.chunk);
+    });
+    c.run(KC_PUSH, 1, [&] {
+        kb_push<T><<<l.push, 256, 0, s>>>(w.front_id.as<int32_t>(), w.front_s.as<float>(), w.heavy_cstart.as<int32_t>(),
+                                          w.heavy_chunk.as<int32_t>(), g->rp_out.as<int64_t>(),
+                                          g->col_out.as<int32_t>(), w.F.as<float>(), ctl, tune.heavy, tune.chunk);
+    });
+    c.run(KC_REDUCE, 1, [&] {
+        kb_reduce<T><<<l.red, 256, 0, s>>>(w.F.as<float>(), g->n, w.partials.as<double>(), ctl, h, set_cond);
+    });
 }
 
 template <int T>

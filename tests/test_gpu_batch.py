@@ -160,3 +160,22 @@ def test_batch_with_nodes_of_many_out_links(tile):
     for r in range(3):
         ref = _oracle_X(og, oracle.ppr_B(n, seeds[off[r]:off[r + 1]], D))
         assert rel_l1(X[r], ref) <= TOL_X, r
+
+
+def test_profiled_batch_times_its_kernels_and_counts_link_columns():
+    """opts.profile on a batched solve drives the sweeps from the host and times each select,
+    push and reduce; the results equal the oracle's as in graph mode, and the push's
+    link-column updates lie between the frontier's links (one column) and T times them."""
+    n, g, og = _graph(20000, 90000, seed=61)
+    off, seeds = workloads.seed_sets(n, 12, 300, seed=63)
+    tol = 1e-10
+    X, res, info = di.di_ppr_batch(g, off, seeds, D, tol, rhs_tile=8, profile=1)
+    assert np.all(res <= tol)
+    for r in range(12):
+        ref = _oracle_X(og, oracle.ppr_B(n, seeds[off[r]:off[r + 1]], D))
+        assert rel_l1(X[r], ref) <= TOL_X, r
+    assert info["push_launches"] > 0 and info["push_ms"] > 0.0
+    assert info["select_launches"] == info["push_launches"] == info["reduce_launches"]
+    assert 0 < info["column_links"] <= 8 * info["pushed_edges"]
+    _, _, plain = di.di_ppr_batch(g, off, seeds, D, tol, rhs_tile=8)
+    assert plain["push_launches"] == 0 and plain["column_links"] > 0
