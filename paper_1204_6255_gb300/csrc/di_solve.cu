@@ -1288,36 +1288,31 @@ enum { PULL_RESID = 1, PULL_INC = 2, PULL_PI64 = 3 };
 //               ctl->r (PI's ||X_(k+1) - X_k||_1), iteration count and the WHILE condition.
 //   PULL_PI64  (FP64): X'_i = B_i + acc_i, delta_i = |X'_i - X_i|, X_i = X'_i, y'_i = X'_i * c_i
 //               (c_i = d / out_i in FP64); sum delta -> ctl->r, iteration count, WHILE condition.
-// Segmented sum over the links of 32 consecutive rows per warp: each lane takes kPullVT
-// contiguous links per round (kPullVT index loads, then kPullVT gathers in flight), forms a
-// segmented prefix over them, and one segmented scan across the 32 lanes joins rows that span
-// lanes; a row's last link writes the row's sum, so no two lanes write the same row. A row
-// that runs past a round carries into the next.
-constexpr int kPullVT = 8;        // links per lane per round (double-float and FP64 values)
-constexpr int kPullVTF32 = 8;     // ... FP32 values (half the registers per value)
-template <class Acc>
-struct PullVT {
-    static constexpr int value = sizeof(typename Acc::V) == 4 ? kPullVTF32 : kPullVT;
-};
-// Per accumulator: whether contiguous row groups read their link indices as 16-byte vectors, and
-// the resident blocks per SM the registers are capped for. Measured on GB300: vector reads speed
-// up the FP32 (PI increment) pull by 5 % and slow the double-float residual pull by 5 %; capping
-// the FP32 pull's registers for 5 or 6 blocks per SM, or at 64, was slower than the compiler's
-// own 53.
+// Segmented sum over the links of 32 consecutive rows per warp. The rows' links are contiguous
+// in col_in (unless the group holds a heavy row, below), so a round gives each lane kPullVT
+// contiguous links, read as 16-byte vectors, with their kPullVT gathers in flight together:
+//   1. the rows that start in the round mark their first link in a per-lane bit mask;
+//   2. each lane forms the prefix sums of its links, restarting at every marked link;
+//   3. one segmented scan across the lanes gives each lane the sum of the row that runs into
+//      it from the left (and the round's carry into the next round);
+//   4. the lanes publish their prefix sums in shared memory, and each row's owner lane reads
+//      its sum at its own last link (adding the incoming sum when the row started before that
+//      lane).
+// A group holding a heavy row (summed apart in chunks) sums its other rows one at a time over
+// the whole warp.
+constexpr int kPullVT = 8;                // links per lane per round
+constexpr int kPullRound = 32 * kPullVT;  // links per warp per round
+// Resident blocks per SM the registers are capped for (0: the compiler's own count).
 template <class Acc>
 struct PullCfg {
-    static constexpr bool vec = false;
-    static constexpr int min_blocks = 4;   // double-float: the compiler's own choice fits 4 blocks
+    static constexpr int min_blocks = 4;
 };
-constexpr int kPullF32MinBlocks = 0;   // 0: the compiler's own register count (4 blocks; 5 and 6 were slower)
 template <>
 struct PullCfg<AccF32> {
-    static constexpr bool vec = true;
-    static constexpr int min_blocks = kPullF32MinBlocks;
+    static constexpr int min_blocks = 0;
 };
 template <>
 struct PullCfg<AccF64> {
-    static constexpr bool vec = false;
     static constexpr int min_blocks = 3;
 };
 
@@ -1331,11 +1326,11 @@ __global__ void __launch_bounds__(256, PullCfg<Acc>::min_blocks) k_pull(const in
                                               cudaGraphConditionalHandle hcond, int set_cond) {
     using V = typename Acc::V;
     using W = typename Acc::Wide;
-    constexpr int kPullVT = PullVT<Acc>::value;
-    static_assert(kPullVT % 4 == 0, "a lane's links are read as 16-byte vectors");
-    __shared__ V acc_s[8][32];
-    __shared__ int s_off[8][33];
-    __shared__ int64_t s_beg[8][32];
+    static_assert(kPullVT == 8, "a lane's links are two 16-byte vectors of indices");
+    __shared__ __align__(16) V s_pre[8][kPullRound];   // per link: prefix within its lane, from the row start
+    __shared__ V s_cin[8][32];                         // per lane: sum of the row entering it from the left
+    __shared__ int s_fs[8][32];                        // per lane: its first link that starts a row (kPullVT: none)
+    __shared__ unsigned s_bits[8][32];                 // per lane: bit v set when its link v starts a row
     __shared__ double scratch[32];
     const int lane = (int)lane_id(), warp = threadIdx.x >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1362,106 +1357,83 @@ __global__ void __launch_bounds__(256, PullCfg<Acc>::min_blocks) k_pull(const in
             heavy = dd > kPullHeavy;
             deg = heavy ? 0 : (int)dd;
         }
-        const int inc = warp_inclusive_scan(deg);
-        const int total = __shfl_sync(kFull, inc, 31);
-        s_off[warp][lane] = inc - deg;
-        if (lane == 31) s_off[warp][32] = total;
-        s_beg[warp][lane] = beg - (inc - deg);      // link e of row k sits at s_beg[k] + e
-        acc_s[warp][lane] = Acc::zero();
-        __syncwarp();
-        V carry = Acc::zero();
-        int carry_row = -1;
-        // Without a heavy row the group's links are contiguous (link e at gbase + e), so each
-        // lane reads its kPullVT links as 16-byte vectors: the rounds start pre = gbase mod 4
-        // links early, which aligns every lane's run; links before 0 or from total on are read
-        // (col_in is padded past L) but not used.
-        const bool contig = PullCfg<Acc>::vec && !__any_sync(kFull, heavy);
-        const int64_t gbase = __shfl_sync(kFull, beg, 0);
-        const int pre = contig && total > 0 ? (int)(gbase & 3) : 0;
-        for (int e0 = -pre; e0 < total; e0 += 32 * kPullVT) {
-            const int first = e0 + lane * kPullVT;
-            int k = 0;   // last row with s_off[k] <= first
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
-                if (s_off[warp][k + step] <= first) k += step;
-            int next = s_off[warp][k + 1];
-            int64_t base = contig ? gbase : s_beg[warp][k];   // reloaded only when the row changes
-            int key[kPullVT];
-            int32_t j[kPullVT];
-            unsigned ends = 0;                      // bit v: link v is its row's last
-            if (contig && first < total) {
-#pragma unroll
-                for (int q = 0; q < kPullVT / 4; q++) {
-                    const int4 jv = ld_stream4(col_in + gbase + first + 4 * q, stream);
-                    j[4 * q] = jv.x;
-                    j[4 * q + 1] = jv.y;
-                    j[4 * q + 2] = jv.z;
-                    j[4 * q + 3] = jv.w;
+        V a = Acc::zero();
+        if (!__any_sync(kFull, heavy)) {
+            const int inc = warp_inclusive_scan(deg);
+            const int total = __shfl_sync(kFull, inc, 31);
+            const int start = inc - deg, last = inc - 1;   // the row's first and last link in the group
+            // link e of the group sits at col_in[gbase + e]; rounds start pre links early so that
+            // every lane's run is 16-byte aligned (col_in is padded past L; links before 0 or
+            // from total on are read but not used)
+            const int64_t gbase = __shfl_sync(kFull, beg, 0);
+            const int pre = total > 0 ? (int)(gbase & 3) : 0;
+            V carry = Acc::zero();
+            for (int e0 = -pre; e0 < total; e0 += kPullRound) {
+                const int first = e0 + lane * kPullVT;
+                s_bits[warp][lane] = 0u;
+                __syncwarp();
+                if (deg > 0 && start >= e0 && start < e0 + kPullRound)
+                    atomicOr(&s_bits[warp][(start - e0) >> 3], 1u << ((start - e0) & 7));
+                int32_t j[kPullVT];
+                if (first < total) {
+                    const int4 j0 = ld_stream4(col_in + gbase + first, stream);
+                    const int4 j1 = ld_stream4(col_in + gbase + first + 4, stream);
+                    j[0] = j0.x; j[1] = j0.y; j[2] = j0.z; j[3] = j0.w;
+                    j[4] = j1.x; j[5] = j1.y; j[6] = j1.z; j[7] = j1.w;
                 }
-            }
+                V val[kPullVT];
 #pragma unroll
-            for (int v = 0; v < kPullVT; v++) {
-                const int e = first + v;
-                key[v] = 64 + lane;                 // outside [0, total): a key no row uses
-                if (e >= 0 && e < total) {
-                    while (e >= next) {
-                        next = s_off[warp][++k + 1];
-                        if (!contig) base = s_beg[warp][k];
+                for (int v = 0; v < kPullVT; v++)
+                    val[v] = (first + v >= 0 && first + v < total) ? y_in[j[v]] : Acc::zero();
+                __syncwarp();
+                const unsigned m = s_bits[warp][lane];
+                // prefix sums of the lane's links, restarting where a row starts
+#pragma unroll
+                for (int v = 1; v < kPullVT; v++)
+                    if (!(m >> v & 1u)) val[v] = Acc::add(val[v - 1], val[v]);
+                // segmented inclusive scan of the lanes' last prefixes: S = the open row's sum at
+                // the lane's end; f = some row starts in this lane or one to its left
+                V S = val[kPullVT - 1];
+                bool f = m != 0u;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const V o = Acc::shfl_up(S, off);
+                    const bool fo = __shfl_up_sync(kFull, f, off);
+                    if (lane >= off) {
+                        if (!f) S = Acc::add(o, S);
+                        f = f || fo;
                     }
-                    key[v] = k;
-                    if (e + 1 == next) ends |= 1u << v;
-                    if (!contig) j[v] = ld_stream(col_in + base + e, stream);
                 }
-            }
-            V val[kPullVT];
+                if (!f) S = Acc::add(carry, S);   // still the row carried in from the last round
+                V cin = Acc::shfl_up(S, 1);
+                if (lane == 0) cin = carry;
+                carry = Acc::shfl(S, 31);
 #pragma unroll
-            for (int v = 0; v < kPullVT; v++) val[v] = key[v] < 64 ? y_in[j[v]] : Acc::zero();
-            // the previous round's carry joins the first link of its row
-            if (lane == 0 && key[0] == carry_row) val[0] = Acc::add(val[0], carry);
-            // segmented prefix within the lane
-#pragma unroll
-            for (int v = 1; v < kPullVT; v++)
-                if (key[v] == key[v - 1]) val[v] = Acc::add(val[v - 1], val[v]);
-            // segmented scan of the lanes' last segments (keys never decrease across lanes)
-            V sv = val[kPullVT - 1];
-            const int sk = key[kPullVT - 1];
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const V ov = Acc::shfl_up(sv, off);
-                const int ok = __shfl_up_sync(kFull, sk, off);
-                if (lane >= off && ok == sk) sv = Acc::add(ov, sv);
-            }
-            const V cin = Acc::shfl_up(sv, 1);
-            const int ck = __shfl_up_sync(kFull, sk, 1);
-            const bool join = lane > 0 && ck == key[0];
-            // finished rows: the row's last link writes its sum
-#pragma unroll
-            for (int v = 0; v < kPullVT; v++) {
-                if (key[v] >= 64) continue;
-                const V fin = (join && key[v] == key[0]) ? Acc::add(cin, val[v]) : val[v];
-                if (ends >> v & 1u) acc_s[warp][key[v]] = fin;
-                val[v] = fin;
-            }
-            // carry for the next round: the round's last link, when its row goes on
-            const int last_e = min(e0 + 32 * kPullVT, total) - 1;
-            const int owner_lane = (last_e - e0) / kPullVT, owner_v = (last_e - e0) % kPullVT;
-            V cv = Acc::zero();
-            int crow = -1;
-#pragma unroll
-            for (int v = 0; v < kPullVT; v++)
-                if (v == owner_v) {
-                    cv = val[v];
-                    crow = key[v];
+                for (int v = 0; v < kPullVT; v++) s_pre[warp][lane * kPullVT + v] = val[v];
+                s_cin[warp][lane] = cin;
+                s_fs[warp][lane] = m ? __ffs(m) - 1 : kPullVT;
+                __syncwarp();
+                // the row whose last link is in this round takes its sum there
+                if (deg > 0 && last >= e0 && last < e0 + kPullRound) {
+                    const int p = last - e0, L = p >> 3;
+                    a = s_pre[warp][p];
+                    if ((p & 7) < s_fs[warp][L]) a = Acc::add(s_cin[warp][L], a);
                 }
-            cv = Acc::shfl(cv, owner_lane);
-            crow = __shfl_sync(kFull, crow, owner_lane);
-            const bool goes_on = crow < 64 && last_e + 1 < s_off[warp][crow + 1];
-            carry = goes_on ? cv : Acc::zero();
-            carry_row = goes_on ? crow : -1;
+                __syncwarp();
+            }
+        } else {
+            // a heavy row's links are not in the run: the other rows one at a time over the warp
+            for (unsigned rows = __ballot_sync(kFull, deg > 0); rows; rows &= rows - 1) {
+                const int k = __ffs(rows) - 1;
+                const int64_t b = __shfl_sync(kFull, beg, k);
+                const int dk = __shfl_sync(kFull, deg, k);
+                V s = Acc::zero();
+                for (int t = lane; t < dk; t += 32) s = Acc::add(s, y_in[ld_stream(col_in + b + t, stream)]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s = Acc::add(s, Acc::shfl_xor(s, o));
+                if (lane == k) a = s;
+            }
         }
-        __syncwarp();
-        V a = acc_s[warp][lane];
-        __syncwarp();
         if (heavy) {
             int lo = 0, hi = n_heavy - 1;
             while (lo < hi) {
