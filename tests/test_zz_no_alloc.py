@@ -50,8 +50,12 @@ def test_noalloc_residual_matches_solve_twice():
         X, info = di.di_solve_ex(g, Bt, d, tol, schedule=sched)
         norm = torch.zeros(1, dtype=torch.float64, device="cuda")
         Fs = torch.empty(n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        held, torch_held = di.di_device_bytes_held(), torch.cuda.memory_allocated()
         di.di_residual_noalloc(n, rp_in, col_in, out_deg, Bt, d, X, norm, Fstar_out=Fs)
         torch.cuda.synchronize()
+        # neither the library nor torch's allocator gained device memory during the call
+        assert di.di_device_bytes_held() == held and torch.cuda.memory_allocated() == torch_held
         got = float(norm.item())
         Xh = X.cpu().numpy()
         slack = _slack(B, Xh)
