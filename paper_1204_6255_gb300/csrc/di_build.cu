@@ -538,10 +538,11 @@ __global__ void k_loop_last(const int64_t *rp, const uint8_t *loop, int32_t n, i
 }
 
 // the push kernels' row bounds: rp_out narrowed to 32 bits (L < 2^31), so one 32-byte sector
-// holds eight nodes' bounds instead of four
-__global__ void k_narrow_rows(const int64_t *rp, int64_t count, int32_t *out) {
+// holds eight nodes' bounds instead of four. Bit 31 of a node's row end (the next node's entry)
+// marks a loop node, whose self-link k_loop_last moved to the row's last link.
+__global__ void k_narrow_rows(const int64_t *rp, const uint8_t *loop, int64_t count, int32_t *out) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
-        out[k] = (int32_t)rp[k];
+        out[k] = (int32_t)((uint32_t)rp[k] | (k > 0 && loop[k - 1] ? 0x80000000u : 0u));
 }
 
 static int ceil_log2(int64_t x) {
@@ -695,8 +696,8 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
             k_loop_last<<<grid_for(n, 256, dev), 256, 0, s>>>(g->rp_out.as<int64_t>(), g->loop.as<uint8_t>(), n,
                                                             g->col_push.as<int32_t>());
         g->rp_push.ensure(sizeof(int32_t) * (size_t)(n + 1));
-        k_narrow_rows<<<grid_for((int64_t)n + 1, 256, dev), 256, 0, s>>>(g->rp_out.as<int64_t>(), (int64_t)n + 1,
-                                                              g->rp_push.as<int32_t>());
+        k_narrow_rows<<<grid_for((int64_t)n + 1, 256, dev), 256, 0, s>>>(g->rp_out.as<int64_t>(), g->loop.as<uint8_t>(),
+                                                                       (int64_t)n + 1, g->rp_push.as<int32_t>());
         // fixed-point width of the push window: a slot sums at most `reach_cnt` shares per
         // segment, each below 2^win_qbits in magnitude, and the sum must stay an int32
         unsigned int *reach_cnt = reinterpret_cast<unsigned int *>(slots.as<char>());

@@ -324,7 +324,8 @@ struct di_graph {
     int32_t win_reach_max = 0;     // most in-links of a non-hub node from sources < kWinReach ids away
     int32_t win_qbits = 20;        // push window: |fixed-point share| < 2^win_qbits (no int32 overflow)
     di::DevBuf col_push;           // int32[L]: col_out with bit 31 set on links into a hub
-    di::DevBuf rp_push;            // int32[n+1]: rp_out narrowed (L < 2^31), the push's row bounds
+    di::DevBuf rp_push;            // int32[n+1]: rp_out narrowed (L < 2^31), the push's row bounds;
+                                   //   bit 31 of entry u + 1: node u has a self-link (last in its row)
     std::mutex mu;                 // serialises use of the workspaces
     di::Workspace ws;
     di::BatchWorkspace *bws = nullptr;   // batched solves (created on first use)

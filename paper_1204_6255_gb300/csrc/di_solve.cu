@@ -367,9 +367,8 @@ __device__ __forceinline__ int segment_at(const SolveCtl *ctl, int ci, int seg_c
 // block owns the kSelWarpNodes consecutive ids from base + w * kSelWarpNodes. The frontier
 // entries of a chunk are compacted with one atomic per chunk, so the frontier is id-sorted
 // within each chunk (the push then walks neighbouring rows together). An entry is the node id
-// and its share (8 bytes); the push reads the row bounds itself, from neighbouring row pointers.
-// Bit 31 of the id marks a loop node whose self-link is diffused in closed form: the push's copy
-// of its row ends with the self-link (k_loop_last), so the push leaves the row's last link out.
+// and its share (8 bytes); the push reads the row bounds itself, from neighbouring row pointers
+// (whose bit 31 marks a loop node, see k_push_win).
 constexpr int kSelItems = 8;
 constexpr int kTrackResync = 8;      // an exact reduction at least every kTrackResync sweeps
 constexpr double kTrackBand = 16.0;  // ... and at every sweep once r <= kTrackBand * tol
@@ -501,11 +500,11 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
             for (int v = 0; v < kSelBatch<T>; v++) {
                 const int k = r0 + v * 32 + lane;
                 const uint32_t i = wb + poff[v];
-                bool light = false, heavy = false, lp = false;
+                bool light = false, heavy = false;
                 T share = (T)0;
                 const int32_t o = pinfo[v] & 0x7fffffff;
                 if (k < cnt) {
-                    lp = !plain_loops && pinfo[v] < 0;
+                    const bool lp = !plain_loops && pinfo[v] < 0;
                     st_keep(F + i, (T)0, keep);
                     T t;
                     visit_math(pf[v], o, lp, d, d_f, t, share);
@@ -527,7 +526,6 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
                     const int p = nlight + __popc(bl & lt);
                     wf[p] = share;
                     woff[p] = (uint8_t)poff[v];
-                    winfo[p] = lp ? 1 : 0;
                     sh_abs += fabsf((float)share);
                 }
                 nlight += __popc(bl);
@@ -580,7 +578,7 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
         __syncthreads();
         const int cb = s_chunk_base + s_wbase[warp];
         for (int k = lane; k < nlight; k += 32) {
-            __stcs(front_id + cb + k, (int32_t)((wb + woff[k]) | ((uint32_t)winfo[k] << 31)));
+            __stcs(front_id + cb + k, (int32_t)(wb + woff[k]));
             __stcs(front_s + cb + k, wf[k]);
         }
         __syncwarp();   // the slots are reused: by the next chunk's copies or packing
@@ -901,7 +899,7 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
         const int64_t idx = b0 + lane;
         int deg = 0;
         if (idx < count) {
-            const int32_t u = __ldcs(front_id + idx) & 0x7fffffff;   // bit 31: see k_select
+            const int32_t u = __ldcs(front_id + idx);
             const int64_t rb = __ldg(rp_out + u);
             deg = (int)(__ldg(rp_out + u + 1) - rb);
             s_u[w][lane] = u;
@@ -1000,8 +998,8 @@ __global__ void __launch_bounds__(256, kPushWinBlocks) k_push_win(const int32_t 
         const int p = heavy_chunk[c];
         const int32_t u = heavy_id[p];
         const float sh = heavy_s[p];
-        const int64_t cb = __ldg(rp_push + u) + (int64_t)(c - heavy_cstart[p]) * heavy_len;
-        const int64_t ce = min(cb + (int64_t)heavy_len, (int64_t)__ldg(rp_push + u + 1));
+        const int64_t cb = (__ldg(rp_push + u) & 0x7fffffff) + (int64_t)(c - heavy_cstart[p]) * heavy_len;
+        const int64_t ce = min(cb + (int64_t)heavy_len, (int64_t)(__ldg(rp_push + u + 1) & 0x7fffffff));
         for (int64_t k0 = cb + lane; k0 < ce; k0 += 32 * kHeavyPushUnroll) {
             int32_t jr[kHeavyPushUnroll];
 #pragma unroll
@@ -1042,12 +1040,13 @@ __global__ void __launch_bounds__(256, kPushWinBlocks) k_push_win(const int32_t 
             float es = 0.f;
             int ebeg = 0;   // links stay below 2^31
             if (b0 + lane < clen) {
-                // bit 31: a loop node diffused in closed form, whose row ends with the self-link
-                const int32_t raw = __ldcs(front_id + idx);
-                eu = raw & 0x7fffffff;
+                eu = __ldcs(front_id + idx);
                 es = __ldcs(front_s + idx);
-                ebeg = __ldg(rp_push + eu);
-                deg = __ldg(rp_push + eu + 1) - ebeg - (int)((uint32_t)raw >> 31);
+                // bit 31 of the row end: a loop node, whose row ends with its self-link; diffused
+                // in closed form (the self-link is not a plain link), the row stops one link short
+                ebeg = __ldg(rp_push + eu) & 0x7fffffff;
+                const int32_t end = __ldg(rp_push + eu + 1);
+                deg = (end & 0x7fffffff) - ebeg - (loops ? 0 : (int)((uint32_t)end >> 31));
             }
             // the share in the segment's fixed point; 0 (never added to the window) when it
             // does not fit, so its local links go to F directly
@@ -1289,8 +1288,8 @@ enum { PULL_RESID = 1, PULL_INC = 2, PULL_PI64 = 3 };
 //   PULL_PI64  (FP64): X'_i = B_i + acc_i, delta_i = |X'_i - X_i|, X_i = X'_i, y'_i = X'_i * c_i
 //               (c_i = d / out_i in FP64); sum delta -> ctl->r, iteration count, WHILE condition.
 // Segmented sum over the links of 32 consecutive rows per warp. The rows' links are contiguous
-// in col_in (unless the group holds a heavy row, below), so a round gives each lane kPullVT
-// contiguous links, read as 16-byte vectors, with their kPullVT gathers in flight together:
+// in col_in (unless the group holds a heavy row, below), so a round gives each lane VT
+// contiguous links, read as 16-byte vectors, with their VT gathers in flight together:
 //   1. the rows that start in the round mark their first link in a per-lane bit mask;
 //   2. each lane forms the prefix sums of its links, restarting at every marked link;
 //   3. one segmented scan across the lanes gives each lane the sum of the row that runs into
@@ -1300,8 +1299,13 @@ enum { PULL_RESID = 1, PULL_INC = 2, PULL_PI64 = 3 };
 //      lane).
 // A group holding a heavy row (summed apart in chunks) sums its other rows one at a time over
 // the whole warp.
-constexpr int kPullVT = 8;                // links per lane per round
-constexpr int kPullRound = 32 * kPullVT;  // links per warp per round
+// Links per lane per round (a multiple of 4, at most 32), per accumulator.
+constexpr int kPullVT = 8;
+constexpr int kPullVTF32 = 8;
+template <class Acc>
+struct PullVT {
+    static constexpr int value = sizeof(typename Acc::V) == 4 ? kPullVTF32 : kPullVT;
+};
 // Resident blocks per SM the registers are capped for (0: the compiler's own count). Measured on
 // GB300: double-float 5 (a small spill) beats 4 by 1.4 %; FP32 at the compiler's 48 registers (5
 // blocks) beats a cap for 6 by 7 %.
@@ -1328,10 +1332,12 @@ __global__ void __launch_bounds__(256, PullCfg<Acc>::min_blocks) k_pull(const in
                                               cudaGraphConditionalHandle hcond, int set_cond) {
     using V = typename Acc::V;
     using W = typename Acc::Wide;
-    static_assert(kPullVT == 8, "a lane's links are two 16-byte vectors of indices");
-    __shared__ __align__(16) V s_pre[8][kPullRound];   // per link: prefix within its lane, from the row start
-    __shared__ V s_cin[8][32];                         // per lane: sum of the row entering it from the left
-    __shared__ int s_fs[8][32];                        // per lane: its first link that starts a row (kPullVT: none)
+    constexpr int VT = PullVT<Acc>::value;     // links per lane per round
+    constexpr int RL = 32 * VT;                // links per warp per round
+    static_assert(VT % 4 == 0 && VT <= 32, "a lane's links are 16-byte vectors of indices, its starts one word");
+    __shared__ __align__(16) V s_pre[8][RL];   // per link: prefix within its lane, from the row start
+    __shared__ V s_cin[8][32];                 // per lane: sum of the row entering it from the left
+    __shared__ int s_fs[8][32];                // per lane: its first link that starts a row (VT: none)
     __shared__ unsigned s_bits[8][32];                 // per lane: bit v set when its link v starts a row
     __shared__ double scratch[32];
     const int lane = (int)lane_id(), warp = threadIdx.x >> 5;
@@ -1370,32 +1376,36 @@ __global__ void __launch_bounds__(256, PullCfg<Acc>::min_blocks) k_pull(const in
             const int64_t gbase = __shfl_sync(kFull, beg, 0);
             const int pre = total > 0 ? (int)(gbase & 3) : 0;
             V carry = Acc::zero();
-            for (int e0 = -pre; e0 < total; e0 += kPullRound) {
-                const int first = e0 + lane * kPullVT;
+            for (int e0 = -pre; e0 < total; e0 += RL) {
+                const int first = e0 + lane * VT;
                 s_bits[warp][lane] = 0u;
                 __syncwarp();
-                if (deg > 0 && start >= e0 && start < e0 + kPullRound)
-                    atomicOr(&s_bits[warp][(start - e0) >> 3], 1u << ((start - e0) & 7));
-                int32_t j[kPullVT];
+                if (deg > 0 && start >= e0 && start < e0 + RL)
+                    atomicOr(&s_bits[warp][(start - e0) / VT], 1u << ((start - e0) % VT));
+                int32_t j[VT];
                 if (first < total) {
-                    const int4 j0 = ld_stream4(col_in + gbase + first, stream);
-                    const int4 j1 = ld_stream4(col_in + gbase + first + 4, stream);
-                    j[0] = j0.x; j[1] = j0.y; j[2] = j0.z; j[3] = j0.w;
-                    j[4] = j1.x; j[5] = j1.y; j[6] = j1.z; j[7] = j1.w;
-                }
-                V val[kPullVT];
 #pragma unroll
-                for (int v = 0; v < kPullVT; v++)
+                    for (int q = 0; q < VT / 4; q++) {
+                        const int4 jq = ld_stream4(col_in + gbase + first + 4 * q, stream);
+                        j[4 * q] = jq.x;
+                        j[4 * q + 1] = jq.y;
+                        j[4 * q + 2] = jq.z;
+                        j[4 * q + 3] = jq.w;
+                    }
+                }
+                V val[VT];
+#pragma unroll
+                for (int v = 0; v < VT; v++)
                     val[v] = (first + v >= 0 && first + v < total) ? y_in[j[v]] : Acc::zero();
                 __syncwarp();
                 const unsigned m = s_bits[warp][lane];
                 // prefix sums of the lane's links, restarting where a row starts
 #pragma unroll
-                for (int v = 1; v < kPullVT; v++)
+                for (int v = 1; v < VT; v++)
                     if (!(m >> v & 1u)) val[v] = Acc::add(val[v - 1], val[v]);
                 // segmented inclusive scan of the lanes' last prefixes: S = the open row's sum at
                 // the lane's end; f = some row starts in this lane or one to its left
-                V S = val[kPullVT - 1];
+                V S = val[VT - 1];
                 bool f = m != 0u;
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
@@ -1411,15 +1421,15 @@ __global__ void __launch_bounds__(256, PullCfg<Acc>::min_blocks) k_pull(const in
                 if (lane == 0) cin = carry;
                 carry = Acc::shfl(S, 31);
 #pragma unroll
-                for (int v = 0; v < kPullVT; v++) s_pre[warp][lane * kPullVT + v] = val[v];
+                for (int v = 0; v < VT; v++) s_pre[warp][lane * VT + v] = val[v];
                 s_cin[warp][lane] = cin;
-                s_fs[warp][lane] = m ? __ffs(m) - 1 : kPullVT;
+                s_fs[warp][lane] = m ? __ffs(m) - 1 : VT;
                 __syncwarp();
                 // the row whose last link is in this round takes its sum there
-                if (deg > 0 && last >= e0 && last < e0 + kPullRound) {
-                    const int p = last - e0, L = p >> 3;
+                if (deg > 0 && last >= e0 && last < e0 + RL) {
+                    const int p = last - e0, L = p / VT;
                     a = s_pre[warp][p];
-                    if ((p & 7) < s_fs[warp][L]) a = Acc::add(s_cin[warp][L], a);
+                    if (p % VT < s_fs[warp][L]) a = Acc::add(s_cin[warp][L], a);
                 }
                 __syncwarp();
             }
