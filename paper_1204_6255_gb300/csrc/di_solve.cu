@@ -626,10 +626,14 @@ __global__ void __launch_bounds__(256, kSelMinBlocks) k_select(T *F, double *H, 
 // in E at a lower level and was visited by an earlier launch, so the node's fluid is final, and
 // no two nodes of a level are linked. One lane per node visits it (E holds no loop node) and
 // pushes its share over at most kEWarpLinks out-links itself; the warp pushes the links of
-// nodes with more, one node at a time; both keep kEUnroll index loads in flight before their
-// additions. As in the push, links into hubs (bit 31 of col_push)
-// collect in a per-block shared-memory cache, flushed once per block.
+// nodes with up to kEBlockLinks, one node at a time; the whole block pushes the links of larger
+// nodes after its warps are done, so no single warp carries a long row at the kernel's tail.
+// All keep kEUnroll index loads in flight before their additions. As in the push, links into
+// hubs (bit 31 of col_push) collect in a per-block shared-memory cache, flushed once per block,
+// and the L2 keeps F (the additions' target) while the links and the history stream through it.
 constexpr int kEWarpLinks = 32;
+constexpr int kEBlockLinks = 256;
+constexpr int kEBlockRows = 256;   // large rows a block collects (more: the warp pushes them)
 constexpr int kEUnroll = 8;   // index loads in flight before their additions
 
 template <class T>
@@ -639,11 +643,17 @@ __global__ void __launch_bounds__(256) k_e_visit(const int32_t *nodes, int32_t c
     __shared__ double scratch[32];
     __shared__ unsigned long long scratch_u[32];
     __shared__ T s_hacc[kHubSlots];
+    __shared__ int64_t s_rb[kEBlockRows];   // the block's large rows: first link, links, share
+    __shared__ int32_t s_rd[kEBlockRows];
+    __shared__ T s_rs[kEBlockRows];
+    __shared__ int s_nrows;
     for (int q = threadIdx.x; q < kHubSlots; q += blockDim.x) s_hacc[q] = (T)0;
+    if (threadIdx.x == 0) s_nrows = 0;
     __syncthreads();
+    const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
     auto add = [&](int32_t jr, T v) {
         if (jr < 0) atomicAdd(&s_hacc[hub_slot(jr & 0x7fffffff)], v);
-        else atomicAdd(&F[jr], v);
+        else red_keep(&F[jr], v, keep);
     };
     const double d = ctl->d;
     const float d_f = (float)d;
@@ -658,13 +668,13 @@ __global__ void __launch_bounds__(256) k_e_visit(const int32_t *nodes, int32_t c
         T share = (T)0;
         if (idx < count) {
             u = nodes[idx];
-            const T f = F[u];
-            o = out_info[u] & 0x7fffffff;
-            b = rp_out[u];
+            const T f = ld_keep(F + u, keep);
+            o = __ldcs(out_info + u) & 0x7fffffff;
+            b = __ldcs(rp_out + u);
             T t;
             visit_math(f, o, false, d, d_f, t, share);
-            F[u] = (T)0;
-            H[u] += widen(t);
+            st_keep(F + u, (T)0, keep);
+            __stcs(H + u, __ldcs(H + u) + widen(t));
             if (o == 0) e_loc += widen(t);
             visited++;
             pushed += (unsigned long long)o;
@@ -672,13 +682,24 @@ __global__ void __launch_bounds__(256) k_e_visit(const int32_t *nodes, int32_t c
                 for (int64_t k0 = b; k0 < b + o; k0 += kEUnroll) {
                     int32_t jr[kEUnroll];
 #pragma unroll
-                    for (int v = 0; v < kEUnroll; v++) jr[v] = k0 + v < b + o ? col_push[k0 + v] : 0;
+                    for (int v = 0; v < kEUnroll; v++) jr[v] = k0 + v < b + o ? ld_stream(col_push + k0 + v, stream) : 0;
 #pragma unroll
                     for (int v = 0; v < kEUnroll; v++)
                         if (k0 + v < b + o) add(jr[v], share);
                 }
         }
-        unsigned big = __ballot_sync(kFull, idx < count && o > kEWarpLinks);
+        // rows above kEBlockLinks go to the block's list (while it has room)
+        bool later = false;
+        if (idx < count && o > kEBlockLinks) {
+            const int slot = atomicAdd(&s_nrows, 1);
+            if (slot < kEBlockRows) {
+                s_rb[slot] = b;
+                s_rd[slot] = o;
+                s_rs[slot] = share;
+                later = true;
+            }
+        }
+        unsigned big = __ballot_sync(kFull, idx < count && o > kEWarpLinks && !later);
         while (big) {
             const int src = __ffs(big) - 1;
             big &= big - 1;
@@ -688,7 +709,7 @@ __global__ void __launch_bounds__(256) k_e_visit(const int32_t *nodes, int32_t c
             for (int64_t k0 = bb + lane; k0 < bb + oo; k0 += 32 * kEUnroll) {
                 int32_t jr[kEUnroll];
 #pragma unroll
-                for (int v = 0; v < kEUnroll; v++) jr[v] = k0 + 32 * v < bb + oo ? col_push[k0 + 32 * v] : 0;
+                for (int v = 0; v < kEUnroll; v++) jr[v] = k0 + 32 * v < bb + oo ? ld_stream(col_push + k0 + 32 * v, stream) : 0;
 #pragma unroll
                 for (int v = 0; v < kEUnroll; v++)
                     if (k0 + 32 * v < bb + oo) add(jr[v], ss);
@@ -696,8 +717,25 @@ __global__ void __launch_bounds__(256) k_e_visit(const int32_t *nodes, int32_t c
         }
     }
     __syncthreads();
+    // the block's large rows, each over all of its threads
+    const int nrows = min(s_nrows, kEBlockRows);
+    for (int r = 0; r < nrows; r++) {
+        const int64_t bb = s_rb[r];
+        const int32_t oo = s_rd[r];
+        const T ss = s_rs[r];
+        for (int64_t k0 = bb + threadIdx.x; k0 < bb + oo; k0 += (int64_t)blockDim.x * kEUnroll) {
+            int32_t jr[kEUnroll];
+#pragma unroll
+            for (int v = 0; v < kEUnroll; v++)
+                jr[v] = k0 + (int64_t)blockDim.x * v < bb + oo ? ld_stream(col_push + k0 + blockDim.x * v, stream) : 0;
+#pragma unroll
+            for (int v = 0; v < kEUnroll; v++)
+                if (k0 + (int64_t)blockDim.x * v < bb + oo) add(jr[v], ss);
+        }
+    }
+    __syncthreads();
     for (int q = threadIdx.x; q < kHubSlots; q += blockDim.x)
-        if (s_hacc[q] != (T)0) atomicAdd(&F[__ldg(hub_ids + q)], s_hacc[q]);
+        if (s_hacc[q] != (T)0) red_keep(&F[__ldg(hub_ids + q)], s_hacc[q], keep);
     e_loc = block_sum(e_loc, scratch);
     pushed = block_sum(pushed, scratch_u);
     visited = block_sum(visited, scratch_u);
