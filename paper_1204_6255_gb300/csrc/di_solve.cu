@@ -988,12 +988,14 @@ __global__ void __launch_bounds__(256) k_push(const int32_t *__restrict__ front_
 // link-by-link push. Shares too large for the segment's fixed point take the direct path, and
 // links into hubs always go to the hub cache (the window's overflow bound leaves hubs out).
 constexpr int kHubCopies = 1;   // copies of the push's shared-memory hub cache
-constexpr int kHalo = 1024;
-constexpr int kWin = kSelChunk + 2 * kHalo;     // 4096 int32 slots, 16 KB
+constexpr int kHalo = 768;
+constexpr int kWin = kSelChunk + 2 * kHalo;     // 3584 int32 slots, 14 KB
 constexpr int kWinMinEntries = 24;              // sparser segments push link by link
-// Resident blocks per SM the registers are capped for: measured on GB300, 7 blocks (32
-// registers) beat 6 and 5 (the kernel waits on memory and gains from more warps in flight).
-constexpr int kPushWinBlocks = 7;
+// Resident blocks per SM the registers are capped for: the kernel waits on memory and gains from
+// more warps in flight. Measured on GB300: 7 blocks (32 registers) beat 6 and 5, and 8 blocks,
+// which the 14 KB window of a 768-id halo fits in shared memory, beat 7 with the 16 KB window of
+// a 1024-id halo (149.0 against 153.1 us per launch; the narrower halo misses few local links).
+constexpr int kPushWinBlocks = 8;
 
 __global__ void __launch_bounds__(256, kPushWinBlocks) k_push_win(const int32_t *__restrict__ front_id, const float *__restrict__ front_s,
                                                   const int32_t *__restrict__ heavy_id, const float *__restrict__ heavy_s,

@@ -163,3 +163,41 @@ def test_prediffusion_on_the_e_dominated_shape_at_1m_nodes():
     for sched in (di.DI_SOP, di.DI_CYC):
         X, info = di.di_solve_ex(g, B, D, 1e-9, schedule=sched, e_prediffuse=1)
         assert rel_l1(X, ref) <= 1e-6 and info["e_visits"] == g.stats["E"]
+
+
+@pytest.mark.parametrize("fluid", [di.DI_FLUID_F64, di.DI_FLUID_F32])
+def test_long_rows_of_a_level_are_pushed_by_the_block(fluid):
+    """Nodes of E with far more out-links than a warp takes alone (the block pushes rows above
+    256 links after its warps): a layered DAG whose layers hold a few sources of 300 to 6000
+    links each beside many short rows. The pre-pass alone must give the oracle's values."""
+    lib()
+    rng = workloads.u64(4300, 1, 1 << 20)
+    pos = [0]
+
+    def draw(k):
+        v = rng[pos[0]:pos[0] + k]
+        pos[0] += k
+        return v
+
+    layers, width = 4, 4000
+    n = layers * width
+    src, dst = [], []
+    for layer in range(layers - 1):
+        base, nxt = layer * width, (layer + 1) * width
+        for i in range(width):
+            deg = (300, 1200, 6000)[i % 3] if i < 9 else 1 + int(draw(1)[0] % np.uint64(12))
+            deg = min(deg, width)
+            t = nxt + (draw(deg) % np.uint64(width)).astype(np.int64)
+            src.append(np.full(deg, base + i, dtype=np.int32))
+            dst.append(t.astype(np.int32))
+    src, dst = np.concatenate(src), np.concatenate(dst)
+    g = di.di_graph_create(n, src, dst)
+    og = oracle.build(n, src, dst)
+    assert g.stats["E"] == n and g.stats["max_out"] > 256
+    B = workloads.uniform(4301, 1, n) * (1 - D) / n
+    ref, _, oinfo, ok = oracle.di_e(og, B, D, 1e-300)
+    assert ok and oinfo["cycles"] == 0
+    tol = 1e-12 * B.sum()
+    X, info = di.di_solve_ex(g, B, D, tol, schedule=di.DI_SOP, fluid=fluid, e_prediffuse=1)
+    assert info["e_visits"] == n
+    assert rel_l1(X, ref) <= (1e-12 if fluid == di.DI_FLUID_F64 else 1e-6)
