@@ -1334,9 +1334,9 @@ enum { PULL_RESID = 1, PULL_INC = 2, PULL_PI64 = 3 };
 //   2. each lane forms the prefix sums of its links, restarting at every marked link;
 //   3. one segmented scan across the lanes gives each lane the sum of the row that runs into
 //      it from the left (and the round's carry into the next round);
-//   4. the lanes publish their prefix sums in shared memory, and each row's owner lane reads
-//      its sum at its own last link (adding the incoming sum when the row started before that
-//      lane).
+//   4. the lane that holds a row's last link publishes that link's prefix (with the incoming sum
+//      added when the row started before the lane) in shared memory, where the row's owner lane
+//      reads it.
 // A group holding a heavy row (summed apart in chunks) sums its other rows one at a time over
 // the whole warp.
 // Links per lane per round (a multiple of 4, at most 32), per accumulator.
@@ -1375,9 +1375,7 @@ __global__ void __launch_bounds__(256, PullCfg<Acc>::min_blocks) k_pull(const in
     constexpr int VT = PullVT<Acc>::value;     // links per lane per round
     constexpr int RL = 32 * VT;                // links per warp per round
     static_assert(VT % 4 == 0 && VT <= 32, "a lane's links are 16-byte vectors of indices, its starts one word");
-    __shared__ __align__(16) V s_pre[8][RL];   // per link: prefix within its lane, from the row start
-    __shared__ V s_cin[8][32];                 // per lane: sum of the row entering it from the left
-    __shared__ int s_fs[8][32];                // per lane: its first link that starts a row (VT: none)
+    __shared__ __align__(16) V s_pre[8][RL];   // at a row's last link: the row's sum
     __shared__ unsigned s_bits[8][32];                 // per lane: bit v set when its link v starts a row
     __shared__ double scratch[32];
     const int lane = (int)lane_id(), warp = threadIdx.x >> 5;
@@ -1460,17 +1458,17 @@ __global__ void __launch_bounds__(256, PullCfg<Acc>::min_blocks) k_pull(const in
                 V cin = Acc::shfl_up(S, 1);
                 if (lane == 0) cin = carry;
                 carry = Acc::shfl(S, 31);
+                // a row ends before every start, at the group's last link, and possibly at the
+                // lane's last link: those positions publish the row's sum
+                unsigned ends = (m >> 1) | (1u << (VT - 1));
+                if (total - 1 >= first && total - 1 < first + VT) ends |= 1u << (total - 1 - first);
+                const int fs = m ? __ffs(m) - 1 : VT;   // links before it continue the row from the left
 #pragma unroll
-                for (int v = 0; v < VT; v++) s_pre[warp][lane * VT + v] = val[v];
-                s_cin[warp][lane] = cin;
-                s_fs[warp][lane] = m ? __ffs(m) - 1 : VT;
+                for (int v = 0; v < VT; v++)
+                    if (ends >> v & 1u) s_pre[warp][lane * VT + v] = v < fs ? Acc::add(cin, val[v]) : val[v];
                 __syncwarp();
                 // the row whose last link is in this round takes its sum there
-                if (deg > 0 && last >= e0 && last < e0 + RL) {
-                    const int p = last - e0, L = p / VT;
-                    a = s_pre[warp][p];
-                    if (p % VT < s_fs[warp][L]) a = Acc::add(s_cin[warp][L], a);
-                }
+                if (deg > 0 && last >= e0 && last < e0 + RL) a = s_pre[warp][last - e0];
                 __syncwarp();
             }
         } else {
