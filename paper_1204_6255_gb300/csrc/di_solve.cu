@@ -1347,8 +1347,8 @@ struct PullVT {
     static constexpr int value = sizeof(typename Acc::V) == 4 ? kPullVTF32 : kPullVT;
 };
 // Resident blocks per SM the registers are capped for (0: the compiler's own count). Measured on
-// GB300: double-float 5 (a small spill) beats 4 by 1.4 %; FP32 at the compiler's 48 registers (5
-// blocks) beats a cap for 6 by 7 %.
+// GB300: double-float 5 (a small spill) beats 4 by 1.4 %; FP32 at the compiler's own 64 registers
+// (4 blocks) beats caps for 5 (3.5 %) and 6.
 template <class Acc>
 struct PullCfg {
     static constexpr int min_blocks = 5;
@@ -1379,7 +1379,6 @@ __global__ void __launch_bounds__(256, PullCfg<Acc>::min_blocks) k_pull(const in
     __shared__ unsigned s_bits[8][32];                 // per lane: bit v set when its link v starts a row
     __shared__ double scratch[32];
     const int lane = (int)lane_id(), warp = threadIdx.x >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const bool odd = (MODE != PULL_RESID) && (ctl->sweeps & 1);
     const V *y_in = odd ? y1 : y0;
     V *y_out = odd ? const_cast<V *>(y0) : y1;
@@ -1387,13 +1386,17 @@ __global__ void __launch_bounds__(256, PullCfg<Acc>::min_blocks) k_pull(const in
     double sum = 0.0;
     float run = 0.f;
     int runs = 0;
-    // every warp runs the same number of row groups so the block stays converged
+    // Each block walks its own contiguous range of row groups, its warps side by side, so the
+    // gathers of nearby rows (most links stay near their source) find y in the SM's L1. Every
+    // warp runs the same number of row groups so the block stays converged.
     const int64_t groups = ((int64_t)n + 31) >> 5;
-    const int64_t rounds = (groups + nwarps - 1) / nwarps;
+    const int64_t per_block = (groups + gridDim.x - 1) / gridDim.x;
+    const int64_t g_lo = blockIdx.x * per_block, g_hi = min(groups, g_lo + per_block);
+    const int64_t rounds = (per_block + 7) / 8;
     for (int64_t rd = 0; rd < rounds; rd++) {
-        const int64_t grp = rd * nwarps + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+        const int64_t grp = g_lo + rd * 8 + warp;
         const int64_t row = grp * 32 + lane;
-        const bool valid = row < n;
+        const bool valid = grp < g_hi && row < n;
         int64_t beg = 0;
         int deg = 0;
         bool heavy = false;
