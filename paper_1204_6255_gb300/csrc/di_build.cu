@@ -414,6 +414,19 @@ __global__ void k_e_peel(const int32_t *frontier, const int32_t *count, const in
     }
 }
 
+// The pull's links per row (rows above kPullHeavy in-links count 0: they are summed apart), and
+// samples of their prefix at rows k * n / samples, k = 0..samples.
+__global__ void k_pull_links(const int32_t *in_deg, int32_t n, uint32_t *links) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = in_deg[v];
+        links[v] = d > kPullHeavy ? 0u : (uint32_t)d;
+    }
+}
+__global__ void k_sample_prefix(const uint32_t *prefix, int32_t n, int samples, int64_t *out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= samples; k += gridDim.x * blockDim.x)
+        out[k] = (int64_t)prefix[(int64_t)k * n / samples];
+}
+
 // Heavy rows of the in-CSR (in-degree > kPullHeavy) and their chunk lists.
 __global__ void k_heavy_in_flags(const int32_t *in_deg, int32_t n, uint32_t *flag, uint32_t *nchunks) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
@@ -811,6 +824,19 @@ static void build_graph(di_graph *g, const int32_t *src_in, const int32_t *dst_i
                                           cudaMemcpyHostToDevice, s));
             DI_CHECK_CUDA(cudaGetLastError());
         }
+        // the pull's link prefix, sampled, so a pull launch can judge whether contiguous stripes
+        // of rows carry even work (the links of the light rows stay below 2^32)
+        DevBuf smp;
+        smp.ensure(sizeof(int64_t) * (size_t)(kPullSamples + 1));
+        k_pull_links<<<grid_for(n, 256, dev), 256, 0, s>>>(g->in_deg.as<int32_t>(), n, flag.as<uint32_t>());
+        exclusive_scan_u32(flag.as<uint32_t>(), fpos.as<uint32_t>(), n, scan_tmp, s);
+        k_sample_prefix<<<(kPullSamples + 256) / 256, 256, 0, s>>>(fpos.as<uint32_t>(), n, kPullSamples,
+                                                                   smp.as<int64_t>());
+        g->pull_sample.assign((size_t)kPullSamples + 1, 0);
+        DI_CHECK_CUDA(cudaMemcpyAsync(g->pull_sample.data(), smp.p, sizeof(int64_t) * (size_t)(kPullSamples + 1),
+                                      cudaMemcpyDeviceToHost, s));
+        DI_CHECK_CUDA(cudaStreamSynchronize(s));
+        DI_CHECK_CUDA(cudaGetLastError());
     }
 
     BuildStats hst{};

@@ -209,6 +209,7 @@ constexpr double kAimAfterSplit = 0.9;
 constexpr double kSplitBelow = 1e-6;
 constexpr int kPullHeavy = 8192;    // in-degree above which a row's edges are split over warps
 constexpr int kPullChunk = 4096;    // edges per heavy-row chunk of the pull
+constexpr int kPullSamples = 4096;  // samples of the pull's link prefix (di_graph::pull_sample)
 constexpr int kColInPad = 8;        // int32 slots allocated past col_in's L links (pull vector reads)
 constexpr int kReduceBlocks = 1024; // partial sums of the last-block-done reductions
 constexpr int kHubSlots = 2048;     // shared-memory hub cache of the push kernels
@@ -313,6 +314,7 @@ struct di_graph {
     // heavy rows of the in-CSR (in-degree > kPullHeavy), for the pull kernels
     int32_t n_heavy_in = 0;
     int32_t n_heavy_in_chunks = 0;
+    std::vector<int64_t> pull_sample;  // host: light in-links of the rows below k * n / kPullSamples
     di::DevBuf heavy_in_rows;      // int32[n_heavy_in], ascending
     di::DevBuf heavy_in_chunk_off; // int32[n_heavy_in + 1]
     di::DevBuf heavy_in_chunk_row; // int32[n_heavy_in_chunks]: heavy index of each chunk

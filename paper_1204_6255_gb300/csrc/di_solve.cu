@@ -1369,7 +1369,7 @@ __global__ void __launch_bounds__(256, PullCfg<Acc>::min_blocks) k_pull(const in
                                               const typename Acc::Wide::V *heavy_partial, int32_t n_heavy,
                                               const double *__restrict__ B, const void *__restrict__ cvec, void *Xvec,
                                               const double *H, T *F, double *partials, SolveCtl *ctl,
-                                              cudaGraphConditionalHandle hcond, int set_cond) {
+                                              cudaGraphConditionalHandle hcond, int set_cond, int stripes) {
     using V = typename Acc::V;
     using W = typename Acc::Wide;
     constexpr int VT = PullVT<Acc>::value;     // links per lane per round
@@ -1386,15 +1386,19 @@ __global__ void __launch_bounds__(256, PullCfg<Acc>::min_blocks) k_pull(const in
     double sum = 0.0;
     float run = 0.f;
     int runs = 0;
-    // Each block walks its own contiguous range of row groups, its warps side by side, so the
-    // gathers of nearby rows (most links stay near their source) find y in the SM's L1. Every
-    // warp runs the same number of row groups so the block stays converged.
+    // stripes = 1: each block walks its own contiguous stripe of row groups, its warps side by
+    // side, so the gathers of nearby rows (most links stay near their source) find y in the SM's
+    // L1; the host picks this when the stripes carry even numbers of links. stripes = 0: the
+    // row groups are interleaved over the grid, which balances graphs whose links crowd into a
+    // few id ranges. Every warp runs the same number of row groups, so the block stays converged.
     const int64_t groups = ((int64_t)n + 31) >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * 8;
     const int64_t per_block = (groups + gridDim.x - 1) / gridDim.x;
-    const int64_t g_lo = blockIdx.x * per_block, g_hi = min(groups, g_lo + per_block);
-    const int64_t rounds = (per_block + 7) / 8;
+    const int64_t g_lo = stripes ? blockIdx.x * per_block : 0;
+    const int64_t g_hi = stripes ? min(groups, g_lo + per_block) : groups;
+    const int64_t rounds = stripes ? (per_block + 7) / 8 : (groups + nwarps - 1) / nwarps;
     for (int64_t rd = 0; rd < rounds; rd++) {
-        const int64_t grp = g_lo + rd * 8 + warp;
+        const int64_t grp = stripes ? g_lo + rd * 8 + warp : rd * nwarps + blockIdx.x * 8 + warp;
         const int64_t row = grp * 32 + lane;
         const bool valid = grp < g_hi && row < n;
         int64_t beg = 0;
@@ -1646,6 +1650,29 @@ static Launch launch_shape(const di_graph *g) {
     return l;
 }
 
+// 1 when `blocks` contiguous stripes of row groups carry even numbers of light in-links (the
+// busiest stripe within kPullStripeSlack of the mean, from the build's samples of the link
+// prefix), so each pull block may walk its own stripe; 0 keeps the groups interleaved.
+constexpr double kPullStripeSlack = 1.5;
+static int pull_stripes(const di_graph *g, int blocks) {
+    const int64_t n = g->n, groups = (n + 31) / 32;
+    const size_t S = g->pull_sample.size();
+    if (blocks < 2 || groups < 8 * (int64_t)blocks || S < 2) return 0;
+    const int64_t per = (groups + blocks - 1) / blocks;
+    auto links_below = [&](int64_t row) {   // nearest sample at or below the row
+        size_t k = (size_t)((double)row * (double)(S - 1) / (double)n);
+        return g->pull_sample[k < S - 1 ? k : S - 1];
+    };
+    const double total = (double)(g->pull_sample[S - 1] - g->pull_sample[0]);
+    if (total <= 0.0) return 0;
+    double busiest = 0.0;
+    for (int b = 0; b < blocks; b++) {
+        const int64_t r0 = std::min(n, (int64_t)b * per * 32), r1 = std::min(n, ((int64_t)b + 1) * per * 32);
+        busiest = std::max(busiest, (double)(links_below(r1) - links_below(r0)));
+    }
+    return busiest <= kPullStripeSlack * total / blocks ? 1 : 0;
+}
+
 // Records of frontier segments a selection can write (one per kSelChunk nodes, and one more).
 static int seg_capacity(const di_graph *g) { return (int)(g->n / kSelChunk + 2); }
 
@@ -1819,13 +1846,13 @@ static void launch_pi_body(di_graph *g, Workspace &ws, const Launch &l, cudaStre
                 g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<double>(), ws.y1.as<double>(), g->n,
                 g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<double>(),
                 g->n_heavy_in, ws.B.as<double>(), ws.Bdf.p, ws.Xdf.p, nullptr, (double *)nullptr,
-                ws.partials.as<double>(), ctl, h, set_cond);
+                ws.partials.as<double>(), ctl, h, set_cond, pull_stripes(g, l.pi64_blocks));
         else
             k_pull<PULL_INC, AccF32, float><<<l.pi_blocks, 256, 0, s>>>(
                 g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<float>(), ws.y1.as<float>(), g->n,
                 g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<float2>(),
                 g->n_heavy_in, ws.B.as<double>(), ws.Bdf.p, ws.H.p, nullptr, (float *)nullptr,
-                ws.partials.as<double>(), ctl, h, set_cond);
+                ws.partials.as<double>(), ctl, h, set_cond, pull_stripes(g, l.pi_blocks));
     });
 }
 
@@ -1875,7 +1902,7 @@ static void launch_refine(di_graph *g, Workspace &ws, const Launch &l, double d,
         g->rp_in.as<int64_t>(), g->col_in.as<int32_t>(), ws.y0.as<float2>(), ws.y1.as<float2>(), g->n,
         g->heavy_in_rows.as<int32_t>(), g->heavy_in_chunk_off.as<int32_t>(), g->heavy_in_partial.as<float2>(),
         g->n_heavy_in, ws.B.as<double>(), nullptr, nullptr, ws.H.as<double>(), ws.F.as<T>(), ws.partials.as<double>(),
-        ctl, cudaGraphConditionalHandle(0), 0);
+        ctl, cudaGraphConditionalHandle(0), 0, pull_stripes(g, l.pull_blocks));
     DI_CHECK_CUDA(cudaGetLastError());
 }
 
