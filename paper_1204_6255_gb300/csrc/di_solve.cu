@@ -1640,7 +1640,9 @@ static Launch launch_shape(const di_graph *g) {
     auto cap = [&](int64_t want, int64_t lim) { return (int)(want < 1 ? 1 : (want < lim ? want : lim)); };
     DI_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select<T>, 256, 0));
     l.sel_blocks = cap((n + kSelChunk - 1) / kSelChunk, (int64_t)sms * (occ > 0 ? occ : 1));
-    l.red_blocks = cap((n + 255) / 256, (int64_t)(kReduceBlocks < sms * 4 ? kReduceBlocks : sms * 4));
+    // two blocks per SM: most sweeps' reductions take r from the tracked sum, and a smaller grid
+    // costs less to launch (measured: 2 per SM beat 4 and 1)
+    l.red_blocks = cap((n + 255) / 256, (int64_t)(kReduceBlocks < sms * 2 ? kReduceBlocks : sms * 2));
     l.ew_blocks = cap((n + 255) / 256, (int64_t)sms * 8);
     // a pull block never needs more row groups than exist
     for (int *b : {&l.pull_blocks, &l.pi_blocks, &l.pi64_blocks}) {
