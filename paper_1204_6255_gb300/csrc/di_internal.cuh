@@ -414,6 +414,26 @@ __device__ __forceinline__ int warp_owner(int off, int q) {
     return pos;
 }
 
+// Exact FP32 -> FP64 widening on the integer units (IEEE 754 binary32 to binary64: the exponent
+// is rebiased from 127 to 1023 and the fraction extended with zeros; a subnormal is normalised
+// first; infinities and NaN keep the all-ones exponent).
+__device__ __forceinline__ double widen(float x) {
+    const uint32_t b = __float_as_uint(x);
+    uint32_t e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    if (e == 0xffu) {
+        e = 0x7ffu - 896u;
+    } else if (e == 0u) {
+        if (m == 0u) {
+            e = 0u - 896u;   // signed zero
+        } else {
+            const int s = __clz(m) - 8;   // moves the leading one to bit 23
+            m = (m << s) & 0x7fffffu;
+            e = 1u - (uint32_t)s;
+        }
+    }
+    const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
+    return __hiloint2double((int)hi, (int)(m << 29));
+}
 __device__ __forceinline__ void red_add(float *p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void red_add(double *p, double v) { atomicAdd(p, v); }
 }  // namespace di

@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(256) kb_select(float *F, double *H, const int3
                     // FP32 transit and share; FP64 only for H += transit
                     const float of = (float)o;
                     const float tf = lp ? f[q] * of / (of - d_f) : f[q];
-                    H[idx] = h[q] + (double)tf;
+                    H[idx] = h[q] + widen(tf);   // exact, on the integer units
                     colv++;
                     if (o == 0) e_run += tf;
                     else {
